@@ -1,0 +1,311 @@
+#!/usr/bin/env python3
+"""Benchmark: CGLS iterations/s and ray-voxel updates/s of A and A^T at 256^3.
+
+Workload (the 256^3 configuration): 256^3 FP32 volume of 1 mm voxels holding a
+seeded 40-ellipsoid phantom, 384 x 288 detector of 1 mm pixels, 360 views over
+360 degrees, SID 750 mm, SDD 1200 mm; b = A x_true.  One step = one ct_cgls
+call of ``--iters`` x updates (default 10, ERR = 0, x0 = 0), i.e. the whole
+hot path: A, A^T, the fused vector updates and the FP64 Krylov scalars.
+
+Prints ONE JSON line (rank 0).  ``value`` = CGLS iterations per second over
+all ranks (each rank solves its own replica: the path has no exchange step).
+``--impl reference`` times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CGLS iters/s and Gray-voxel/s (A, Aᵀ) at 256³; served p50/p99 latency"
+WORKLOAD = ("B256: 256^3 FP32 volume (1 mm voxels, 40 random ellipsoids, seed 1), 384x288 "
+            "detector (1 mm pixels), 360 views over 360 deg, SID 750 mm, SDD 1200 mm; "
+            "b = A x_true; one step = ct_cgls with ERR=0, x0=0")
+PEAK_FALLBACK_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--iters", type=int, default=10, help="CGLS x updates per step")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sample-views", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peak_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return PEAK_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[4 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2110_13526_gb300", "csrc", "projector.cu")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        ent = d.get(kernel)
+        if ent and ent.get("projector_sha256") == sha:
+            return float(ent["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def make_problem(ct, torch, synth, dev):
+    cfg = synth.CONFIGS["B256"]
+    g = ct.Geometry(**cfg)
+    lo, hi = synth.box_of(cfg)
+    x_true = torch.from_numpy(synth.voxelize(synth.random_ellipsoids(40, 1, lo, hi), cfg)).to(dev)
+    b = ct.project(g, x_true)
+    torch.cuda.synchronize()
+    return cfg, g, x_true, b
+
+
+def cpu_baseline(cfg, views_n, iters_per_step):
+    """The oracle (FP64 C, OpenMP) on a bounded sample: A and A^T on
+    ``views_n`` of the 360 views, extrapolated to one CGLS iteration."""
+    import numpy as np
+    import oracle
+    import synth
+    oracle.build()
+    og_full = oracle.OGeom(**cfg)
+    views = [int(round(k * cfg["nviews"] / views_n)) % cfg["nviews"] for k in range(views_n)]
+    og = og_full.subset(views)
+    lo, hi = synth.box_of(cfg)
+    x = synth.voxelize(synth.random_ellipsoids(40, 1, lo, hi), cfg).astype(np.float64)
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    p = oracle.project(og, x, threads)
+    t1 = time.perf_counter()
+    oracle.backproject(og, p, threads)
+    t2 = time.perf_counter()
+    scale = cfg["nviews"] / views_n
+    t_iter = (t2 - t0) * scale
+    return {"value": 1.0 / t_iter, "unit": "iters/s", "cores": threads, "kind": "oracle",
+            "sample": "A and A^T on %d of %d views (%.1f s + %.1f s), extrapolated x%.0f to "
+                      "one CGLS iteration (vector updates not counted)"
+                      % (views_n, cfg["nviews"], t1 - t0, t2 - t1, scale),
+            "seconds": t2 - t0}
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import synth
+    cfg = synth.CONFIGS["B256"]
+    vals = []
+    for _ in range(max(a.warmup, 0)):
+        cpu_baseline(cfg, a.cpu_sample_views, a.iters)
+    t_total = 0.0
+    last = None
+    for s in range(a.steps):
+        last = cpu_baseline(cfg, a.cpu_sample_views, a.iters)
+        vals.append(last["value"])
+        t_total += last["seconds"]
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "ms_per_step": 1000.0 * t_total / max(a.steps, 1),
+            "config": {"workload": WORKLOAD, "sample_views": a.cpu_sample_views},
+            "cpu_baseline": {"kind": "oracle", "cores": last["cores"], "sample": last["sample"],
+                             "value": value, "unit": "iters/s"},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2110_13526_gb300 as ct
+    import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    cfg, g, x_true, b = make_problem(ct, torch, synth, dev)
+    nnz = ct.count_nnz(g)
+    n_vox, n_rays = g.sizes()
+    K = a.iters
+
+    def step(timing=True):
+        return ct.cgls(g, b, max_iter=K, timing=timing)
+
+    for _ in range(max(a.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    l0 = ct.kernel_launches()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    ms_f = ms_b = 0.0
+    nf = nb = 0
+    for _ in range(a.steps):
+        _, rep = step()
+        ms_f += rep.ms_forward
+        ms_b += rep.ms_back
+        nf += rep.n_forward
+        nb += rep.n_back
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = (ct.kernel_launches() - l0) // max(a.steps, 1)
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    clk = clocks.stop()
+
+    # end to end through the public API with host buffers: pinned b in, x out
+    b_host = b.cpu().pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.e2e_steps):
+        xh, _ = ct.cgls(g, b_host, max_iter=K)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / a.e2e_steps
+    e2e_value = world * K / e2e_s
+
+    peak, peak_kind = measured_peak_gbs()
+    t_f = ms_f / max(nf, 1) * 1e-3           # s per launch of the forward kernel
+    t_b = ms_b / max(nb, 1) * 1e-3
+    bytes_f = 4.0 * nnz + 4.0 * n_rays        # one voxel load per ray-voxel pair + sinogram out
+    bytes_b = 4.0 * nnz + 4.0 * n_vox         # one voxel update per pair + volume out
+    dom = "forward" if ms_f >= ms_b else "backward"
+    t_dom, by_dom = (t_f, bytes_f) if dom == "forward" else (t_b, bytes_b)
+    achieved = by_dom / t_dom / 1e9
+    kname = "k_forward" if dom == "forward" else "k_backward"
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic_for(kname),
+            "kernel": kname, "peak_source": peak_kind,
+            "ms_per_launch": t_dom * 1e3,
+            "algorithmic_bytes_per_launch": by_dom}
+    value = world * a.steps * K / (ms * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cgls_iters_per_step": K,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (sinogram 159 MB; working set ~0.8 GB)",
+                       "nnz": nnz},
+            "gray_voxel_per_s": {"A": nnz / t_f / 1e9, "AT": nnz / t_b / 1e9},
+            "ms_per_op": {"A": t_f * 1e3, "AT": t_b * 1e3},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": "iters/s",
+                    "h2d_bytes_per_step": 4 * n_rays, "d2h_bytes_per_step": 4 * n_vox},
+            "gpu_launches": int(launches) * a.steps,
+            "clocks": clk}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cb = cpu_baseline(cfg, a.cpu_sample_views, K)
+        cb.pop("seconds", None)
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

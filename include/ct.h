@@ -1,0 +1,189 @@
+/*
+ * ct.h -- C ABI of the GB300 (sm_103a) cone-beam CT operator and Krylov solvers.
+ *
+ * The operator is the sparse CBCT system matrix A of Materials and Methods
+ * (Eq. 1, b = A x), never stored: A_ij is the length in mm of ray i inside
+ * voxel j (the Siddon ray-caster named in the Software section).  The
+ * solvers are CGLS with delayed residual computation (Algorithm 1) and LSQR
+ * (Paige & Saunders 1982, cited in Materials and Methods), with the diagonal
+ * preconditioners of the Software and Discussion sections.
+ *
+ * Conventions (the paper fixes none of them; every call uses these):
+ *   lengths in mm, angles in radians;
+ *   circular orbit about +z: source s = SID (cos th, sin th, 0);
+ *   flat detector centred at -(SDD - SID) (cos th, sin th, 0) with axes
+ *   e_u = (-sin th, cos th, 0) and e_v = (0, 0, 1);
+ *   pixel (u, v) centre = centre + ((u - (nu-1)/2) du + det_off_u) e_u
+ *                                + ((v - (nv-1)/2) dv + det_off_v) e_v;
+ *   one ray per pixel, from the source to the pixel centre;
+ *   volume box = [-n h / 2 + off, +n h / 2 + off] per axis (off-centre
+ *   reconstruction, Software section);
+ *   volume  float32 [nz][ny][nx], x fastest;
+ *   sinogram float32 [nviews][nv][nu], u fastest.
+ *
+ * Memory: every vector argument named d_* is a DEVICE pointer on the device
+ * that was current when the geometry was created; the caller owns it.  The
+ * library owns the geometry and any workspace it allocates (stream-ordered,
+ * cudaMallocAsync / cudaFreeAsync on the call's stream).
+ *
+ * Streams: ``stream`` is a cudaStream_t passed as void* (NULL = the legacy
+ * default stream).  ct_project / ct_backproject / ct_project_norm2 only
+ * enqueue work and return; ct_count_nnz, ct_precond_weights, ct_cgls and
+ * ct_lsqr return after the stream has completed their work.
+ *
+ * Errors: every call validates its arguments and returns a ct_status; it
+ * never aborts.  ct_last_error() gives a message for the calling thread's
+ * last failure.  A CT_ERR_CUDA status leaves the CUDA error in the message.
+ */
+#ifndef CT_H
+#define CT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CT_OK = 0,
+    CT_ERR_INVALID_ARG = 1, /* NULL pointer, bad size, unsupported option   */
+    CT_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed  */
+    CT_ERR_OOM = 3,         /* device workspace allocation failed           */
+    CT_ERR_TIMEOUT = 4,     /* reserved: a bounded device wait gave up      */
+    CT_ERR_INTERNAL = 5     /* a device-side consistency check failed       */
+} ct_status;
+
+/* Opaque geometry: per-view ray constants on the device, library-owned. */
+typedef struct ct_geometry ct_geometry;
+
+/* Caller-owned description of the scan (Results section: a C-arm-like
+ * circular cone-beam orbit).  angles_rad may be NULL: views are then
+ * 2 pi k / nviews, k = 0 .. nviews-1 (uniform over 360 degrees, endpoint
+ * excluded).  Otherwise it points to nviews host doubles, copied at create. */
+typedef struct {
+    int32_t nx, ny, nz;          /* volume size in voxels                    */
+    double vx, vy, vz;           /* voxel pitch, mm                          */
+    double off_x, off_y, off_z;  /* volume centre, mm (off-centre recon)     */
+    int32_t nu, nv;              /* detector size in pixels                  */
+    double du, dv;               /* pixel pitch, mm                          */
+    double det_off_u, det_off_v; /* detector shift along e_u / e_v, mm       */
+    double sid, sdd;             /* source-isocentre, source-detector, mm    */
+    int32_t nviews;              /* number of views                          */
+    const double *angles_rad;    /* NULL or nviews view angles               */
+} ct_geometry_desc;
+
+/* Create a geometry on the current CUDA device.  Requires nx, ny, nz >= 1,
+ * nu, nv, nviews >= 0, positive pitches, 0 < sid < sdd, fewer than 2^31
+ * voxels and fewer than 2^31 rays per view block.  *out receives the handle. */
+ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out);
+
+/* Free the geometry (NULL is a no-op).  No call using it may be in flight. */
+void ct_geometry_destroy(ct_geometry *g);
+
+/* Sizes of the geometry: voxels (n = nx ny nz) and rays (m = nviews nv nu). */
+ct_status ct_geometry_sizes(const ct_geometry *g, int64_t *n_vox, int64_t *n_rays);
+
+/* Forward projection (Eq. 1; Algorithm 1 steps p_b = A x and p_b = A d_x):
+ *   d_sino = alpha * (A d_vol) + beta * d_sino.
+ * With beta == 0, d_sino is not read (it may hold anything).  d_vol and
+ * d_sino must not overlap. */
+ct_status ct_project(const ct_geometry *g, const float *d_vol, float *d_sino, float alpha,
+                     float beta, void *stream);
+
+/* Backprojection, the exact transpose of ct_project (Algorithm 1 step
+ * r_x = A^T e_b):   d_vol = alpha * (A^T d_sino) + beta * d_vol.
+ * With beta == 0, d_vol is not read.  Sums are accumulated with float
+ * atomics, so the last bits may differ between runs. */
+ct_status ct_backproject(const ct_geometry *g, const float *d_sino, float *d_vol, float alpha,
+                         float beta, void *stream);
+
+/* ct_project plus the squared norm of the result (Algorithm 1 step
+ * NP2 = ||p_b||_2^2), accumulated in FP64 in a fixed order (deterministic):
+ *   d_sino = alpha * (A d_vol) + beta * d_sino;  *d_norm2 = ||d_sino||^2.
+ * d_norm2 is a DEVICE pointer to one double.  Uses a stream-ordered
+ * device workspace of 8 bytes per 256 rays. */
+ct_status ct_project_norm2(const ct_geometry *g, const float *d_vol, float *d_sino, float alpha,
+                           float beta, double *d_norm2, void *stream);
+
+/* Number of (ray, voxel) pairs with positive intersection length, i.e. the
+ * nonzeros of A (the unit of the ray-voxel update rate).  *out is a HOST
+ * int64.  Blocks until done. */
+ct_status ct_count_nnz(const ct_geometry *g, int64_t *out, void *stream);
+
+typedef enum {
+    CT_PRECOND_NONE = 0,
+    /* Jacobi (Software and Discussion sections): the normal-equation
+     * matrix A^T A approximated by its diagonal; x = D^-1/2 y. */
+    CT_PRECOND_JACOBI = 1,
+    /* Diagonal row/column sums: min || R^-1/2 (A C^-1/2 y - b) ||, x = C^-1/2 y,
+     * R = A 1 (row sums), C = A^T 1 (column sums).  Left scaling changes the
+     * least-squares solution when b is inconsistent (it weights the rays). */
+    CT_PRECOND_ROWCOL = 2
+} ct_precond;
+
+/* Preconditioner weights.  JACOBI: d_vol_w = diag(A^T A)^-1/2 (d_sino_w
+ * unused, may be NULL).  ROWCOL: d_sino_w = (A 1)^-1/2, d_vol_w = (A^T 1)^-1/2.
+ * Entries whose sum is <= 1e-6 times the largest are set to 0: those voxels
+ * or rays carry no data (the tiny cone-boundary values of the Discussion).
+ * Blocks until done. */
+ct_status ct_precond_weights(const ct_geometry *g, int32_t kind, float *d_vol_w, float *d_sino_w,
+                             void *stream);
+
+/* Solver options (Algorithm 1 input: x0, ERR, K; Software section:
+ * preconditioning; Discussion: periodic recomputation of the discrepancy). */
+typedef struct {
+    int32_t max_iter;        /* K >= 1: number of x updates at most            */
+    double err_tol;          /* ERR >= 0: stop once NB / NB0 <= ERR            */
+    int32_t precond;         /* a ct_precond value                            */
+    double tikhonov_lambda;  /* must be 0 (Tikhonov regularisation: not built) */
+    int32_t recompute_every; /* k > 0: e_b = b - A x every k updates (CGLS)    */
+    int32_t timing;          /* nonzero: time every A and A^T with CUDA events */
+} ct_solver_opts;
+
+/* Solver report, filled on return.  history_nb (HOST, caller-owned, may be
+ * NULL) receives NB / NB0 after each x update, up to history_cap entries.
+ * For LSQR, NB is the recurrence estimate phi_bar of the discrepancy.  With
+ * preconditioning the discrepancy is the weighted one, || R^-1/2 (b - A x) ||
+ * for ROWCOL. */
+typedef struct {
+    int32_t iterations;   /* i of Algorithm 1: x updates done               */
+    double nb0, nb;       /* NB0 = ||b|| and the final NB                   */
+    double *history_nb;   /* in: host array or NULL                         */
+    int32_t history_cap;  /* in: its length                                 */
+    int32_t n_forward;    /* operator calls made: A                         */
+    int32_t n_back;       /* operator calls made: A^T                       */
+    double ms_forward;    /* with opts.timing: total device time in A, ms   */
+    double ms_back;       /* with opts.timing: total device time in A^T, ms */
+} ct_solver_report;
+
+/* CGLS with delayed residual computation (Algorithm 1, with the direction
+ * update read as d_x = r_x + beta d_x).  d_b: sinogram (device, read only);
+ * d_x: in = x0, out = x (device).  A zero x0 skips the A x0 call, so K updates
+ * cost 2K operator calls (2K + 1 with a nonzero x0).  Device workspace:
+ * 3 volumes + 2 sinograms (+ weights).  Blocks until done. */
+ct_status ct_cgls(const ct_geometry *g, const float *d_b, float *d_x, const ct_solver_opts *opts,
+                  ct_solver_report *report, void *stream);
+
+/* LSQR (Paige & Saunders 1982) on the same operator; K iterations cost
+ * 2K + 1 operator calls (+1 with a nonzero x0).  Same arguments as ct_cgls;
+ * recompute_every is ignored.  Blocks until done. */
+ct_status ct_lsqr(const ct_geometry *g, const float *d_b, float *d_x, const ct_solver_opts *opts,
+                  ct_solver_report *report, void *stream);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *ct_last_error(void);
+
+/* Library version string. */
+const char *ct_version(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all threads, all devices).  A profiling counter; memsets and copies are
+ * not kernels and are not counted. */
+int64_t ct_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CT_H */

@@ -1,0 +1,308 @@
+"""Python binding of the GB300 (sm_103a) cone-beam CT library (``include/ct.h``).
+
+Argument marshalling only: every step of the operator and of the solvers runs
+in the CUDA library ``_build/libct_gb300.so``; PyTorch supplies device
+memory and streams.  There is no CPU fallback: without the built library, or
+without a CUDA device, every call raises.
+
+    import paper_2110_13526_gb300 as ct
+    g = ct.Geometry(nx=256, ny=256, nz=256, vx=1, vy=1, vz=1, nu=384, nv=288,
+                    du=1, dv=1, sid=750, sdd=1200, nviews=360)
+    sino = ct.project(g, vol)                 # A x      (vol: cuda float32 [nz, ny, nx])
+    back = ct.backproject(g, sino)            # A^T b
+    x, rep = ct.cgls(g, b, max_iter=50)       # Algorithm 1 (CGLS)
+    x, rep = ct.lsqr(g, b, max_iter=50)       # LSQR
+
+CPU tensors passed to ``cgls`` / ``lsqr`` / ``project`` / ``backproject`` are
+copied to the device and the result is copied back (the end-to-end path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libct_gb300.so")
+
+CT_OK = 0
+CT_PRECOND_NONE, CT_PRECOND_JACOBI, CT_PRECOND_ROWCOL = 0, 1, 2
+_PRECOND = {"none": 0, None: 0, "jacobi": 1, "rowcol": 2, 0: 0, 1: 1, 2: 2}
+_STATUS = {0: "CT_OK", 1: "CT_ERR_INVALID_ARG", 2: "CT_ERR_CUDA", 3: "CT_ERR_OOM",
+           4: "CT_ERR_TIMEOUT", 5: "CT_ERR_INTERNAL"}
+
+# Every symbol include/ct.h declares (checked by the CPU tests).
+EXPORTS = ("ct_geometry_create", "ct_geometry_destroy", "ct_geometry_sizes", "ct_project",
+           "ct_backproject", "ct_project_norm2", "ct_count_nnz", "ct_precond_weights",
+           "ct_cgls", "ct_lsqr", "ct_last_error", "ct_version", "ct_kernel_launches")
+
+
+class CTError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (_STATUS.get(status, str(status)), msg))
+        self.status = status
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("vx", ctypes.c_double), ("vy", ctypes.c_double), ("vz", ctypes.c_double),
+                ("off_x", ctypes.c_double), ("off_y", ctypes.c_double),
+                ("off_z", ctypes.c_double),
+                ("nu", ctypes.c_int32), ("nv", ctypes.c_int32),
+                ("du", ctypes.c_double), ("dv", ctypes.c_double),
+                ("det_off_u", ctypes.c_double), ("det_off_v", ctypes.c_double),
+                ("sid", ctypes.c_double), ("sdd", ctypes.c_double),
+                ("nviews", ctypes.c_int32),
+                ("angles_rad", ctypes.POINTER(ctypes.c_double))]
+
+
+class SolverOpts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("err_tol", ctypes.c_double),
+                ("precond", ctypes.c_int32), ("tikhonov_lambda", ctypes.c_double),
+                ("recompute_every", ctypes.c_int32), ("timing", ctypes.c_int32)]
+
+
+class _Report(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("nb0", ctypes.c_double),
+                ("nb", ctypes.c_double), ("history_nb", ctypes.POINTER(ctypes.c_double)),
+                ("history_cap", ctypes.c_int32), ("n_forward", ctypes.c_int32),
+                ("n_back", ctypes.c_int32), ("ms_forward", ctypes.c_double),
+                ("ms_back", ctypes.c_double)]
+
+
+@dataclass
+class SolveReport:
+    iterations: int
+    nb0: float
+    nb: float
+    history: list          # NB / NB0 after each x update
+    n_forward: int
+    n_back: int
+    ms_forward: float
+    ms_back: float
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("CUDA library %s is not built; run __graft_entry__.build() or "
+                               "python -m paper_2110_13526_gb300.build" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P, vp = ctypes.POINTER, ctypes.c_void_p
+        sig = {
+            "ct_geometry_create": ([P(_Desc), P(vp)], ctypes.c_int),
+            "ct_geometry_destroy": ([vp], None),
+            "ct_geometry_sizes": ([vp, P(ctypes.c_int64), P(ctypes.c_int64)], ctypes.c_int),
+            "ct_project": ([vp, vp, vp, ctypes.c_float, ctypes.c_float, vp], ctypes.c_int),
+            "ct_backproject": ([vp, vp, vp, ctypes.c_float, ctypes.c_float, vp], ctypes.c_int),
+            "ct_project_norm2": ([vp, vp, vp, ctypes.c_float, ctypes.c_float, vp, vp],
+                                 ctypes.c_int),
+            "ct_count_nnz": ([vp, P(ctypes.c_int64), vp], ctypes.c_int),
+            "ct_precond_weights": ([vp, ctypes.c_int32, vp, vp, vp], ctypes.c_int),
+            "ct_cgls": ([vp, vp, vp, P(SolverOpts), P(_Report), vp], ctypes.c_int),
+            "ct_lsqr": ([vp, vp, vp, P(SolverOpts), P(_Report), vp], ctypes.c_int),
+            "ct_last_error": ([], ctypes.c_char_p),
+            "ct_version": ([], ctypes.c_char_p),
+            "ct_kernel_launches": ([], ctypes.c_int64),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != CT_OK:
+        raise CTError(status, lib().ct_last_error().decode("utf-8", "replace"))
+
+
+def version() -> str:
+    return lib().ct_version().decode()
+
+
+def kernel_launches() -> int:
+    """Kernels this library has launched in this process so far."""
+    return int(lib().ct_kernel_launches())
+
+
+class Geometry:
+    """Circular cone-beam scan geometry on the current CUDA device (ct_geometry).
+
+    Lengths in mm.  ``angles`` (radians) defaults to 2 pi k / nviews.
+    Volume tensors are float32 [nz, ny, nx]; sinograms float32 [nviews, nv, nu].
+    """
+
+    def __init__(self, nx, ny, nz, vx, vy, vz, nu, nv, du, dv, sid, sdd, nviews,
+                 ox=0.0, oy=0.0, oz=0.0, det_off_u=0.0, det_off_v=0.0,
+                 angles: Optional[Sequence[float]] = None, device=None):
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.nu, self.nv, self.nviews = int(nu), int(nv), int(nviews)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        ang = None
+        if angles is not None:
+            arr = (ctypes.c_double * int(nviews))(*[float(a) for a in angles])
+            ang = ctypes.cast(arr, ctypes.POINTER(ctypes.c_double))
+        d = _Desc(self.nx, self.ny, self.nz, float(vx), float(vy), float(vz), float(ox),
+                  float(oy), float(oz), self.nu, self.nv, float(du), float(dv),
+                  float(det_off_u), float(det_off_v), float(sid), float(sdd), self.nviews, ang)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().ct_geometry_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("geometry is closed")
+        return self._h
+
+    @property
+    def vol_shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def sino_shape(self):
+        return (self.nviews, self.nv, self.nu)
+
+    def sizes(self):
+        n, m = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().ct_geometry_sizes(self.handle, ctypes.byref(n), ctypes.byref(m)))
+        return n.value, m.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().ct_geometry_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, shape, name: str, device) -> torch.Tensor:
+    if t.dtype != torch.float32:
+        raise TypeError("%s must be float32" % name)
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    if not t.is_cuda:
+        t = t.pin_memory().to(device, non_blocking=True) if t.device.type == "cpu" else t.to(device)
+    if t.device != device:
+        raise ValueError("%s is on %s, geometry on %s" % (name, t.device, device))
+    return t.contiguous()
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def project(g: Geometry, vol: torch.Tensor, out: Optional[torch.Tensor] = None,
+            alpha: float = 1.0, beta: float = 0.0, stream=None) -> torch.Tensor:
+    """out = alpha * A vol + beta * out (ct_project)."""
+    host = not vol.is_cuda
+    v = _dev(vol, g.vol_shape, "vol", g.device)
+    if out is None:
+        o = torch.empty(g.sino_shape, dtype=torch.float32, device=g.device)
+    else:
+        o = _dev(out, g.sino_shape, "out", g.device)
+    _check(lib().ct_project(g.handle, _ptr(v), _ptr(o), float(alpha), float(beta),
+                            _stream(stream)))
+    if out is not None and o.data_ptr() != out.data_ptr():
+        out.copy_(o)
+        return out
+    return o.cpu() if host else o
+
+
+def project_norm2(g: Geometry, vol: torch.Tensor, out: Optional[torch.Tensor] = None,
+                  alpha: float = 1.0, beta: float = 0.0, stream=None):
+    """(out, ||out||^2 as a 0-d cuda float64 tensor) (ct_project_norm2)."""
+    v = _dev(vol, g.vol_shape, "vol", g.device)
+    o = torch.empty(g.sino_shape, dtype=torch.float32, device=g.device) if out is None else out
+    nrm = torch.empty((), dtype=torch.float64, device=g.device)
+    _check(lib().ct_project_norm2(g.handle, _ptr(v), _ptr(o), float(alpha), float(beta),
+                                  _ptr(nrm), _stream(stream)))
+    return o, nrm
+
+
+def backproject(g: Geometry, sino: torch.Tensor, out: Optional[torch.Tensor] = None,
+                alpha: float = 1.0, beta: float = 0.0, stream=None) -> torch.Tensor:
+    """out = alpha * A^T sino + beta * out (ct_backproject)."""
+    host = not sino.is_cuda
+    s = _dev(sino, g.sino_shape, "sino", g.device)
+    if out is None:
+        o = torch.empty(g.vol_shape, dtype=torch.float32, device=g.device)
+    else:
+        o = _dev(out, g.vol_shape, "out", g.device)
+    _check(lib().ct_backproject(g.handle, _ptr(s), _ptr(o), float(alpha), float(beta),
+                                _stream(stream)))
+    if out is not None and o.data_ptr() != out.data_ptr():
+        out.copy_(o)
+        return out
+    return o.cpu() if host else o
+
+
+def count_nnz(g: Geometry, stream=None) -> int:
+    """Nonzeros of A: (ray, voxel) pairs with positive length (ct_count_nnz)."""
+    n = ctypes.c_int64()
+    _check(lib().ct_count_nnz(g.handle, ctypes.byref(n), _stream(stream)))
+    return n.value
+
+
+def precond_weights(g: Geometry, kind, stream=None):
+    """(vol_w, sino_w or None) of CT_PRECOND_JACOBI / CT_PRECOND_ROWCOL."""
+    k = _PRECOND[kind]
+    vw = torch.empty(g.vol_shape, dtype=torch.float32, device=g.device)
+    sw = torch.empty(g.sino_shape, dtype=torch.float32, device=g.device) if k == 2 else None
+    _check(lib().ct_precond_weights(g.handle, k, _ptr(vw), _ptr(sw), _stream(stream)))
+    return vw, sw
+
+
+def _solve(fn, g: Geometry, b, x0, max_iter, err_tol, precond, recompute_every, timing,
+           stream):
+    host = not b.is_cuda
+    bd = _dev(b, g.sino_shape, "b", g.device)
+    if x0 is None:
+        x = torch.zeros(g.vol_shape, dtype=torch.float32, device=g.device)
+    else:
+        x = _dev(x0, g.vol_shape, "x0", g.device).clone()
+    opts = SolverOpts(int(max_iter), float(err_tol), _PRECOND[precond], 0.0,
+                      int(recompute_every), 1 if timing else 0)
+    hist = (ctypes.c_double * int(max_iter))()
+    rep = _Report(0, 0.0, 0.0, ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)),
+                  int(max_iter), 0, 0, 0.0, 0.0)
+    _check(fn(g.handle, _ptr(bd), _ptr(x), ctypes.byref(opts), ctypes.byref(rep),
+              _stream(stream)))
+    r = SolveReport(rep.iterations, rep.nb0, rep.nb, list(hist[:rep.iterations]),
+                    rep.n_forward, rep.n_back, rep.ms_forward, rep.ms_back)
+    return (x.cpu() if host else x), r
+
+
+def cgls(g: Geometry, b: torch.Tensor, x0: Optional[torch.Tensor] = None, max_iter: int = 20,
+         err_tol: float = 0.0, precond="none", recompute_every: int = 0, timing: bool = False,
+         stream=None):
+    """CGLS with delayed residual computation (Algorithm 1) -> (x, SolveReport)."""
+    return _solve(lib().ct_cgls, g, b, x0, max_iter, err_tol, precond, recompute_every, timing,
+                  stream)
+
+
+def lsqr(g: Geometry, b: torch.Tensor, x0: Optional[torch.Tensor] = None, max_iter: int = 20,
+         err_tol: float = 0.0, precond="none", timing: bool = False, stream=None):
+    """LSQR (Paige & Saunders 1982) -> (x, SolveReport); NB is the phi_bar estimate."""
+    return _solve(lib().ct_lsqr, g, b, x0, max_iter, err_tol, precond, 0, timing, stream)

@@ -1,0 +1,423 @@
+// C ABI: geometry, projector entry points, nnz count, preconditioner
+// weights, error strings.  The solvers live in solvers.cu.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "ct_internal.h"
+
+namespace ct {
+
+namespace {
+thread_local std::string g_last_error;
+std::atomic<long long> g_launches{0};
+}
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+ct_status set_error(ct_status st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+ct_status cuda_error(cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" +
+                    cudaGetErrorString(e) + ")";
+    return set_error(e == cudaErrorMemoryAllocation ? CT_ERR_OOM : CT_ERR_CUDA, m);
+}
+
+void clear_error() { g_last_error.clear(); }
+
+Workspace::~Workspace() {
+    for (void *p : ptrs_) cudaFreeAsync(p, stream_);
+}
+
+ct_status Workspace::alloc(void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, stream_);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_error(e, "cudaMallocAsync (workspace)");
+    }
+    ptrs_.push_back(*p);
+    return CT_OK;
+}
+
+DeviceGuard::DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev_) != cudaSuccess) {
+        st_ = set_error(CT_ERR_CUDA, "cudaGetDevice failed");
+        return;
+    }
+    if (prev_ != dev) {
+        cudaError_t e = cudaSetDevice(dev);
+        if (e != cudaSuccess) {
+            st_ = cuda_error(e, "cudaSetDevice");
+            return;
+        }
+        changed_ = true;
+    }
+}
+
+DeviceGuard::~DeviceGuard() {
+    if (changed_) cudaSetDevice(prev_);
+}
+
+ct_status precond_weights_impl(const ct_geometry *g, int kind, float *vol_w, float *sino_w,
+                               Workspace &ws, cudaStream_t st) {
+    const ProjGeom &pg = g->pg;
+    float *part = nullptr, *acc_t = nullptr;
+    const int64_t np = std::max<int64_t>(vec_grid(g->nvox), vec_grid(g->nrays));
+    CT_TRY(ws.alloc(&part, (size_t)np));
+    if (kind == CT_PRECOND_JACOBI) {
+        // D = diag(A^T A) = (A o A)^T 1: squared lengths scattered from unit rays
+        CT_TRY(ws.alloc(&acc_t, (size_t)g->nvox));
+        CT_CUDA_TRY(cudaMemsetAsync(vol_w, 0, (size_t)g->nvox * sizeof(float), st));
+        CT_CUDA_TRY(cudaMemsetAsync(acc_t, 0, (size_t)g->nvox * sizeof(float), st));
+        CT_TRY(launch_backward(pg, nullptr, nullptr, Coef{}, vol_w, acc_t, 2, st));
+        CT_TRY(launch_combine(pg, vol_w, acc_t, nullptr, nullptr, st));
+        CT_TRY(launch_inv_sqrt_guarded(vol_w, g->nvox, 1e-6f, part, st));
+        return CT_OK;
+    }
+    if (kind == CT_PRECOND_ROWCOL) {
+        // R = A 1 (row sums) and C = A^T 1 (column sums)
+        CT_TRY(launch_forward(pg, nullptr, nullptr, sino_w, nullptr, Coef{}, nullptr, st));
+        CT_TRY(launch_inv_sqrt_guarded(sino_w, g->nrays, 1e-6f, part, st));
+        CT_TRY(ws.alloc(&acc_t, (size_t)g->nvox));
+        CT_CUDA_TRY(cudaMemsetAsync(vol_w, 0, (size_t)g->nvox * sizeof(float), st));
+        CT_CUDA_TRY(cudaMemsetAsync(acc_t, 0, (size_t)g->nvox * sizeof(float), st));
+        CT_TRY(launch_backward(pg, nullptr, nullptr, Coef{}, vol_w, acc_t, 1, st));
+        CT_TRY(launch_combine(pg, vol_w, acc_t, nullptr, nullptr, st));
+        CT_TRY(launch_inv_sqrt_guarded(vol_w, g->nvox, 1e-6f, part, st));
+        return CT_OK;
+    }
+    return set_error(CT_ERR_INVALID_ARG, "unknown preconditioner kind");
+}
+
+}  // namespace ct
+
+using namespace ct;
+
+namespace {
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+ct_status check_geom(const ct_geometry *g) {
+    if (!g) return set_error(CT_ERR_INVALID_ARG, "geometry is NULL");
+    return CT_OK;
+}
+
+// Per-view ray constants, FP64 on the host, stored FP32 in voxel units.
+void view_constants(const ct_geometry_desc &d, const std::vector<double> &ang,
+                    std::vector<ViewConst> &out) {
+    const double h[3] = {d.vx, d.vy, d.vz};
+    const double lo[3] = {-0.5 * d.nx * d.vx + d.off_x, -0.5 * d.ny * d.vy + d.off_y,
+                          -0.5 * d.nz * d.vz + d.off_z};
+    out.resize(ang.size());
+    for (size_t k = 0; k < ang.size(); ++k) {
+        const double c = std::cos(ang[k]), s = std::sin(ang[k]);
+        const double src[3] = {d.sid * c, d.sid * s, 0.0};
+        const double cd = -(d.sdd - d.sid);
+        const double eu[3] = {-s, c, 0.0}, ev[3] = {0.0, 0.0, 1.0};
+        // centre of the pixel grid (u = (nu-1)/2, v = (nv-1)/2) incl. offsets
+        double pc[3];
+        for (int a = 0; a < 3; ++a) {
+            const double dc = (a == 0 ? cd * c : (a == 1 ? cd * s : 0.0));
+            pc[a] = dc + d.det_off_u * eu[a] + d.det_off_v * ev[a];
+        }
+        ViewConst &vc = out[k];
+        for (int a = 0; a < 3; ++a) {
+            vc.s[a] = (float)((src[a] - lo[a]) / h[a]);
+            vc.p00[a] = (float)((pc[a] - lo[a]) / h[a]);
+            vc.eu[a] = (float)(d.du * eu[a] / h[a]);
+            vc.ev[a] = (float)(d.dv * ev[a] / h[a]);
+        }
+    }
+}
+
+// Per-column ray parameters (see ColParams), in FP64, stored FP32.
+void column_params(const ct_geometry_desc &d, const std::vector<double> &ang,
+                   std::vector<float4> &ca_out, std::vector<float4> &cb_out,
+                   std::vector<int> &fl_out) {
+    const double h[3] = {d.vx, d.vy, d.vz};
+    const int N[3] = {d.nx, d.ny, d.nz};
+    const double lo[3] = {-0.5 * d.nx * d.vx + d.off_x, -0.5 * d.ny * d.vy + d.off_y,
+                          -0.5 * d.nz * d.vz + d.off_z};
+    const size_t ncol = ang.size() * (size_t)d.nu;
+    ca_out.resize(ncol);
+    cb_out.resize(ncol);
+    fl_out.resize(ncol);
+    for (size_t k = 0; k < ang.size(); ++k) {
+        const double c = std::cos(ang[k]), s = std::sin(ang[k]);
+        const double src[3] = {d.sid * c, d.sid * s, 0.0};
+        const double cd = -(d.sdd - d.sid);
+        const double eu[3] = {-s, c, 0.0};
+        const double pc[3] = {cd * c + d.det_off_u * eu[0], cd * s + d.det_off_u * eu[1],
+                              d.det_off_v};
+        double S[3], Pc[3], EU[3];
+        for (int a = 0; a < 3; ++a) {
+            S[a] = (src[a] - lo[a]) / h[a];
+            Pc[a] = (pc[a] - lo[a]) / h[a];
+            EU[a] = d.du * eu[a] / h[a];
+        }
+        const double EVz = d.dv / h[2];
+        for (int u = 0; u < d.nu; ++u) {
+            const double uc = u - 0.5 * (d.nu - 1);
+            double P[3], D[3];
+            for (int a = 0; a < 3; ++a) {
+                P[a] = Pc[a] + uc * EU[a];
+                D[a] = P[a] - S[a];
+            }
+            const int ax = std::fabs(D[0]) >= std::fabs(D[1]) ? 0 : 1;
+            const int la = 1 - ax;
+            const bool rev = D[ax] < 0.0;
+            const int Ns = N[ax], Na = N[la], Nb = N[2];
+            const int cs = Ns / 2, cl = Na / 2, cz = Nb / 2;
+            const double Ds = D[ax];
+            const double sig0 = rev ? (double)(Ns - cs) : (double)cs;
+            const double adx = std::fabs(Ds);
+            const size_t i = k * (size_t)d.nu + (size_t)u;
+            if (adx == 0.0) {  // degenerate: never hits (pixel at the source)
+                ca_out[i] = make_float4(0.f, 1e30f, 0.f, 0.f);
+                cb_out[i] = make_float4(1e30f, 0.f, 0.f, -1.f);
+                fl_out[i] = 0;
+                continue;
+            }
+            const double A = D[la] / adx;
+            const double XI0 = S[la] - cl + (sig0 - S[ax]) * D[la] / Ds;
+            const double C0 = D[2] / adx;
+            const double C1 = EVz / adx;
+            const double Z0 = S[2] - cz + (sig0 - S[ax]) * D[2] / Ds;
+            const double Z1 = (sig0 - S[ax]) * EVz / Ds;
+            const double wsrc = (rev ? Ns - S[ax] : S[ax]) - cs;
+            const double wpix = (rev ? Ns - P[ax] : P[ax]) - cs;
+            ca_out[i] = make_float4((float)A, (float)XI0, (float)C0, (float)C1);
+            cb_out[i] = make_float4((float)Z0, (float)Z1, (float)wsrc, (float)wpix);
+            fl_out[i] = (ax == 0 ? 1 : 0) | (rev ? 2 : 0);
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out) {
+    clear_error();
+    if (!desc || !out) return set_error(CT_ERR_INVALID_ARG, "desc and out must be non-NULL");
+    *out = nullptr;
+    const ct_geometry_desc &d = *desc;
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1)
+        return set_error(CT_ERR_INVALID_ARG, "nx, ny, nz must be >= 1");
+    if (d.nu < 0 || d.nv < 0 || d.nviews < 0)
+        return set_error(CT_ERR_INVALID_ARG, "nu, nv, nviews must be >= 0");
+    if (!finite_pos(d.vx) || !finite_pos(d.vy) || !finite_pos(d.vz) || !finite_pos(d.du) ||
+        !finite_pos(d.dv))
+        return set_error(CT_ERR_INVALID_ARG, "voxel and pixel pitches must be finite and > 0");
+    if (!finite_pos(d.sid) || !std::isfinite(d.sdd) || !(d.sdd > d.sid))
+        return set_error(CT_ERR_INVALID_ARG, "need 0 < sid < sdd");
+    if (!std::isfinite(d.off_x) || !std::isfinite(d.off_y) || !std::isfinite(d.off_z) ||
+        !std::isfinite(d.det_off_u) || !std::isfinite(d.det_off_v))
+        return set_error(CT_ERR_INVALID_ARG, "offsets must be finite");
+    const int64_t nvox = (int64_t)d.nx * d.ny * d.nz;
+    if (nvox >= (int64_t(1) << 31))
+        return set_error(CT_ERR_INVALID_ARG, "volume must hold fewer than 2^31 voxels");
+    if (d.nz > 65535 || d.nviews > 65535)
+        return set_error(CT_ERR_INVALID_ARG, "nz and nviews must be <= 65535");
+    if ((int64_t)d.nx * d.ny >= (int64_t(1) << 31))
+        return set_error(CT_ERR_INVALID_ARG, "nx * ny too large");
+    if (d.nviews > 0 && d.angles_rad) {
+        for (int k = 0; k < d.nviews; ++k)
+            if (!std::isfinite(d.angles_rad[k]))
+                return set_error(CT_ERR_INVALID_ARG, "angles must be finite");
+    }
+    ct_geometry *g = new (std::nothrow) ct_geometry();
+    if (!g) return set_error(CT_ERR_OOM, "host allocation failed");
+    g->desc = d;
+    g->angles.resize((size_t)d.nviews);
+    for (int k = 0; k < d.nviews; ++k)
+        g->angles[(size_t)k] = d.angles_rad ? d.angles_rad[k] : 2.0 * M_PI * k / d.nviews;
+    g->desc.angles_rad = g->angles.data();
+    g->nvox = nvox;
+    g->nrays = (int64_t)d.nviews * d.nv * d.nu;
+    g->d_views = nullptr;
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_error(e, "cudaGetDevice");
+    }
+    std::vector<ViewConst> vcs;
+    view_constants(d, g->angles, vcs);
+    std::vector<float4> cola, colb;
+    std::vector<int> colf;
+    column_params(d, g->angles, cola, colb, colf);
+    g->d_cols = nullptr;
+    const size_t ncol = cola.size();
+    if (d.nviews > 0) {
+        e = cudaMalloc(&g->d_views, sizeof(ViewConst) * vcs.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g->d_views, vcs.data(), sizeof(ViewConst) * vcs.size(),
+                           cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && ncol > 0) {
+            e = cudaMalloc(&g->d_cols, ncol * (2 * sizeof(float4) + sizeof(int)));
+            char *base = (char *)g->d_cols;
+            if (e == cudaSuccess)
+                e = cudaMemcpy(base, cola.data(), ncol * sizeof(float4), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(base + ncol * sizeof(float4), colb.data(), ncol * sizeof(float4),
+                               cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(base + 2 * ncol * sizeof(float4), colf.data(), ncol * sizeof(int),
+                               cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) {
+            if (g->d_views) cudaFree(g->d_views);
+            if (g->d_cols) cudaFree(g->d_cols);
+            delete g;
+            return cuda_error(e, "geometry upload");
+        }
+    }
+    g->pg.views = g->d_views;
+    g->pg.col_a = g->d_cols ? (const float4 *)g->d_cols : nullptr;
+    g->pg.col_b = g->d_cols ? (const float4 *)((char *)g->d_cols + ncol * sizeof(float4)) : nullptr;
+    g->pg.col_flags =
+        g->d_cols ? (const int *)((char *)g->d_cols + 2 * ncol * sizeof(float4)) : nullptr;
+    g->pg.nx = d.nx; g->pg.ny = d.ny; g->pg.nz = d.nz;
+    g->pg.nu = d.nu; g->pg.nv = d.nv; g->pg.nviews = d.nviews;
+    g->pg.hx = (float)d.vx; g->pg.hy = (float)d.vy; g->pg.hz = (float)d.vz;
+    *out = g;
+    return CT_OK;
+}
+
+void ct_geometry_destroy(ct_geometry *g) {
+    if (!g) return;
+    if (g->d_views || g->d_cols) {
+        DeviceGuard dg(g->device);
+        if (g->d_views) cudaFree(g->d_views);
+        if (g->d_cols) cudaFree(g->d_cols);
+    }
+    delete g;
+}
+
+ct_status ct_geometry_sizes(const ct_geometry *g, int64_t *n_vox, int64_t *n_rays) {
+    clear_error();
+    CT_TRY(check_geom(g));
+    if (n_vox) *n_vox = g->nvox;
+    if (n_rays) *n_rays = g->nrays;
+    return CT_OK;
+}
+
+ct_status ct_project(const ct_geometry *g, const float *d_vol, float *d_sino, float alpha,
+                     float beta, void *stream) {
+    clear_error();
+    CT_TRY(check_geom(g));
+    if (g->nrays == 0) return CT_OK;
+    if (!d_vol || !d_sino) return set_error(CT_ERR_INVALID_ARG, "NULL vector");
+    DeviceGuard dg(g->device);
+    CT_TRY(dg.status());
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace ws(st);
+    float *vol_t = nullptr;
+    CT_TRY(ws.alloc(&vol_t, (size_t)g->nvox));
+    CT_TRY(launch_transpose(g->pg, d_vol, nullptr, vol_t, nullptr, st));
+    Coef c;
+    c.alpha = alpha;
+    c.beta = beta;
+    return launch_forward(g->pg, d_vol, vol_t, d_sino, nullptr, c, nullptr, st);
+}
+
+ct_status ct_project_norm2(const ct_geometry *g, const float *d_vol, float *d_sino, float alpha,
+                           float beta, double *d_norm2, void *stream) {
+    clear_error();
+    CT_TRY(check_geom(g));
+    if (!d_norm2) return set_error(CT_ERR_INVALID_ARG, "d_norm2 is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (g->nrays == 0) {
+        DeviceGuard dg(g->device);
+        CT_TRY(dg.status());
+        CT_CUDA_TRY(cudaMemsetAsync(d_norm2, 0, sizeof(double), st));
+        return CT_OK;
+    }
+    if (!d_vol || !d_sino) return set_error(CT_ERR_INVALID_ARG, "NULL vector");
+    DeviceGuard dg(g->device);
+    CT_TRY(dg.status());
+    Workspace ws(st);
+    float *vol_t = nullptr;
+    double *part = nullptr;
+    const int64_t np = forward_partials(g->pg);
+    CT_TRY(ws.alloc(&vol_t, (size_t)g->nvox));
+    CT_TRY(ws.alloc(&part, (size_t)np));
+    CT_TRY(launch_transpose(g->pg, d_vol, nullptr, vol_t, nullptr, st));
+    Coef c;
+    c.alpha = alpha;
+    c.beta = beta;
+    CT_TRY(launch_forward(g->pg, d_vol, vol_t, d_sino, nullptr, c, part, st));
+    return launch_sum(part, np, d_norm2, st);
+}
+
+ct_status ct_backproject(const ct_geometry *g, const float *d_sino, float *d_vol, float alpha,
+                         float beta, void *stream) {
+    clear_error();
+    CT_TRY(check_geom(g));
+    if (!d_vol) return set_error(CT_ERR_INVALID_ARG, "NULL vector");
+    if (g->nrays > 0 && !d_sino) return set_error(CT_ERR_INVALID_ARG, "NULL vector");
+    DeviceGuard dg(g->device);
+    CT_TRY(dg.status());
+    cudaStream_t st = (cudaStream_t)stream;
+    CT_TRY(launch_scale(d_vol, g->nvox, beta, st));
+    if (g->nrays == 0 || alpha == 0.f) return CT_OK;
+    Workspace ws(st);
+    float *acc_t = nullptr;
+    CT_TRY(ws.alloc(&acc_t, (size_t)g->nvox));
+    CT_CUDA_TRY(cudaMemsetAsync(acc_t, 0, (size_t)g->nvox * sizeof(float), st));
+    Coef c;
+    c.alpha = alpha;
+    CT_TRY(launch_backward(g->pg, d_sino, nullptr, c, d_vol, acc_t, 1, st));
+    return launch_combine(g->pg, d_vol, acc_t, nullptr, nullptr, st);
+}
+
+ct_status ct_count_nnz(const ct_geometry *g, int64_t *out, void *stream) {
+    clear_error();
+    CT_TRY(check_geom(g));
+    if (!out) return set_error(CT_ERR_INVALID_ARG, "out is NULL");
+    DeviceGuard dg(g->device);
+    CT_TRY(dg.status());
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace ws(st);
+    unsigned long long *d = nullptr;
+    CT_TRY(ws.alloc(&d, 1));
+    CT_TRY(launch_count(g->pg, d, st));
+    unsigned long long h = 0;
+    CT_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CT_CUDA_TRY(cudaStreamSynchronize(st));
+    *out = (int64_t)h;
+    return CT_OK;
+}
+
+ct_status ct_precond_weights(const ct_geometry *g, int32_t kind, float *d_vol_w, float *d_sino_w,
+                             void *stream) {
+    clear_error();
+    CT_TRY(check_geom(g));
+    if (kind != CT_PRECOND_JACOBI && kind != CT_PRECOND_ROWCOL)
+        return set_error(CT_ERR_INVALID_ARG, "kind must be CT_PRECOND_JACOBI or CT_PRECOND_ROWCOL");
+    if (!d_vol_w || (kind == CT_PRECOND_ROWCOL && g->nrays > 0 && !d_sino_w))
+        return set_error(CT_ERR_INVALID_ARG, "NULL weight vector");
+    DeviceGuard dg(g->device);
+    CT_TRY(dg.status());
+    cudaStream_t st = (cudaStream_t)stream;
+    {
+        Workspace ws(st);
+        CT_TRY(precond_weights_impl(g, kind, d_vol_w, d_sino_w, ws, st));
+    }
+    CT_CUDA_TRY(cudaStreamSynchronize(st));
+    return CT_OK;
+}
+
+const char *ct_last_error(void) { return g_last_error.c_str(); }
+
+const char *ct_version(void) { return "ct-gb300 0.1.0 (sm_103a)"; }
+
+int64_t ct_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,186 @@
+// Internal declarations of the GB300 CBCT library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ct.h"
+
+namespace ct {
+
+// Per-view ray constants in VOXEL units, relative to the volume box's low
+// corner: a point q (mm) maps to (q - box_lo) / h per axis.  A ray of pixel
+// (u, v) runs from s to p00 + uc * eu + vc * ev, where p00 is the centre of
+// the pixel grid, uc = u - (nu-1)/2 and vc = v - (nv-1)/2.
+struct ViewConst {
+    float s[3];
+    float p00[3];
+    float eu[3];
+    float ev[3];
+};
+
+// Per detector column (view, u) ray parameters, computed in FP64 on the host
+// and stored FP32.  For a flat detector whose v axis is the rotation axis,
+// the in-plane direction of ray (u, v) depends on u only, so the slab axis s
+// (x or y, whichever the ray advances along faster), the walk direction and
+// the lateral slope A are per column; the z terms are affine in v.
+//
+// Coordinates are in voxel units, centred on integer planes: walk coordinate
+// w = (sigma or Ns - sigma) - Ns/2 (sigma = coordinate along s, increasing
+// along the ray), lateral xi = coordinate along the other in-plane axis
+// minus Na/2, zeta = z coordinate minus Nz/2 (integer halves).  On the ray:
+//   xi(w)   = XI0 + A w,            zeta(w) = (Z0 + vc Z1) + (C0 + vc C1) w,
+// with vc = v - (nv-1)/2, and w runs from wsrc (source) to wpix (pixel).
+struct ColParams {
+    float4 a;  // A, XI0, C0, C1
+    float4 b;  // Z0, Z1, wsrc, wpix
+};
+
+// Everything a projector kernel needs, passed by value.
+struct ProjGeom {
+    const ViewConst *views;  // device array [nviews] (rays advancing along z)
+    const float4 *col_a;     // device arrays [nviews * nu]: ColParams::a
+    const float4 *col_b;     //                               ColParams::b
+    const int *col_flags;    // bit 0: slab axis is x (else y); bit 1: walk reversed
+    int nx, ny, nz;
+    int nu, nv, nviews;
+    float hx, hy, hz;        // voxel pitch, mm
+};
+
+}  // namespace ct
+
+struct ct_geometry {
+    ct_geometry_desc desc;       // copy; desc.angles_rad points into angles
+    std::vector<double> angles;  // nviews
+    int device;
+    int64_t nvox, nrays;
+    ct::ViewConst *d_views;      // device
+    void *d_cols;                // device: col_a, col_b, col_flags in one allocation
+    ct::ProjGeom pg;
+};
+
+namespace ct {
+
+// ---- error reporting (thread-local message) --------------------------------
+ct_status set_error(ct_status st, const std::string &msg);
+ct_status cuda_error(cudaError_t e, const char *where);
+void clear_error();
+
+#define CT_CUDA_TRY(expr)                                          \
+    do {                                                           \
+        cudaError_t _e = (expr);                                   \
+        if (_e != cudaSuccess) return ::ct::cuda_error(_e, #expr); \
+    } while (0)
+
+#define CT_TRY(expr)                      \
+    do {                                  \
+        ct_status _s = (expr);            \
+        if (_s != CT_OK) return _s;       \
+    } while (0)
+
+// Counts one kernel launch of this library (ct_kernel_launches) and checks
+// that it was accepted.
+void note_launch();
+#define CT_CHECK_LAUNCH()                               \
+    do {                                                \
+        ::ct::note_launch();                            \
+        CT_CUDA_TRY(cudaGetLastError());                \
+    } while (0)
+
+// ---- stream-ordered device workspace ---------------------------------------
+// Allocations are freed on the same stream when the Workspace goes out of
+// scope, so kernels enqueued before the free still see valid memory.
+class Workspace {
+public:
+    explicit Workspace(cudaStream_t s) : stream_(s) {}
+    ~Workspace();
+    Workspace(const Workspace &) = delete;
+    Workspace &operator=(const Workspace &) = delete;
+    // Returns CT_OK and sets *p, or CT_ERR_OOM / CT_ERR_CUDA.
+    ct_status alloc(void **p, size_t bytes);
+    template <class T>
+    ct_status alloc(T **p, size_t count) {
+        return alloc(reinterpret_cast<void **>(p), count * sizeof(T));
+    }
+
+private:
+    cudaStream_t stream_;
+    std::vector<void *> ptrs_;
+};
+
+// ---- projector launches (projector.cu) -------------------------------------
+// Coefficients of an epilogue out = alpha * op(in) + beta * out.  When dev is
+// non-NULL the pair is read on the device from dev[0], dev[1] (FP64).
+struct Coef {
+    float alpha = 1.f, beta = 0.f;
+    const double *dev = nullptr;
+};
+
+// Number of FP64 norm partials a forward launch writes (one per CTA).
+int64_t forward_partials(const ProjGeom &pg);
+
+// p = alpha * rho o (A vol) + beta * p.  vol_t is the same volume in the
+// transposed layout [nz][nx][ny] (used by rays that advance mostly along x).
+// rho may be NULL (all ones).  partials may be NULL; else one FP64 partial
+// sum of p^2 per CTA.
+ct_status launch_forward(const ProjGeom &pg, const float *vol, const float *vol_t, float *p,
+                         const float *rho, Coef c, double *partials, cudaStream_t st);
+
+// acc += alpha * A^T (rho o e), scattered with float atomics into acc
+// ([nz][ny][nx]) for rays that advance mostly along y or z and into acc_t
+// ([nz][nx][ny]) for rays that advance mostly along x.  power = 2 scatters
+// squared lengths (diag(A^T A) with e = 1).
+ct_status launch_backward(const ProjGeom &pg, const float *e, const float *rho, Coef c,
+                          float *acc, float *acc_t, int power, cudaStream_t st);
+
+// Count the (ray, voxel) pairs with positive length into *d_count (int64).
+ct_status launch_count(const ProjGeom &pg, unsigned long long *d_count, cudaStream_t st);
+
+// ---- volume / sinogram kernels (vector_ops.cu) ------------------------------
+int vec_grid(int64_t n);  // CTAs of a streaming kernel (also its partial count)
+constexpr int kVecThreads = 256;
+
+// t = transpose of v: [nz][ny][nx] -> [nz][nx][ny]; optional scale w (t = w v)
+// and optional plain copy out (out = w v in the original layout).
+ct_status launch_transpose(const ProjGeom &pg, const float *v, const float *w, float *t,
+                           float *out_plain, cudaStream_t st);
+// g = acc + transpose(acc_t)  ([nz][nx][ny] -> [nz][ny][nx]); with partials,
+// one FP64 partial per CTA of sum (w o g)^2 (w may be NULL).
+int transpose_grid_count(const ProjGeom &pg);
+ct_status launch_combine(const ProjGeom &pg, float *g, const float *acc_t, const float *w,
+                         double *partials, cudaStream_t st);
+// out = beta * out (beta == 0 writes zeros without reading)
+ct_status launch_scale(float *out, int64_t n, float beta, cudaStream_t st);
+ct_status launch_scale_dev(float *out, int64_t n, const double *beta, cudaStream_t st);
+// Sum of partials[0..n) in a fixed order into *out (FP64, deterministic).
+ct_status launch_sum(const double *partials, int64_t n, double *out, cudaStream_t st);
+// partial sums of (w o v)^2 (w may be NULL), vec_grid(n) partials
+ct_status launch_norm2(const float *v, const float *w, int64_t n, double *partials,
+                       cudaStream_t st);
+
+}  // namespace ct
+
+namespace ct {
+// v = 1/sqrt(v) where v > rel * max(v), else 0.  part: vec_grid(n) floats.
+ct_status launch_inv_sqrt_guarded(float *v, int64_t n, float rel, float *part, cudaStream_t st);
+
+// Preconditioner weights into caller buffers (see ct_precond_weights).
+ct_status precond_weights_impl(const ct_geometry *g, int kind, float *vol_w, float *sino_w,
+                               Workspace &ws, cudaStream_t st);
+
+// Makes g's device current for the lifetime of the guard.
+class DeviceGuard {
+public:
+    explicit DeviceGuard(int dev);
+    ~DeviceGuard();
+    ct_status status() const { return st_; }
+
+private:
+    int prev_ = -1;
+    bool changed_ = false;
+    ct_status st_ = CT_OK;
+};
+}  // namespace ct

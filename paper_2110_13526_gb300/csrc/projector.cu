@@ -1,0 +1,374 @@
+// Ray-driven Siddon projector pair for sm_103a: A (gather) and its exact
+// transpose A^T (atomic scatter), plus an nnz counter.
+//
+// The operator (Materials and Methods, Eq. 1; Software section: Siddon
+// ray-caster): A_ij = length in mm of ray i inside voxel j.
+//
+// Traversal ("slab walk").  Every ray picks its dominant axis s (largest
+// |direction| in voxel units) and is walked one voxel slab of that axis at a
+// time.  In voxel units the lateral coordinates along the ray are affine in
+// the slab coordinate sigma, xi(sigma) = xi0 + A sigma and zeta(sigma) =
+// ze0 + C sigma with |A|, |C| <= 1, so inside one slab the ray crosses at
+// most one plane of each lateral axis: at most three voxels per slab.  Every
+// plane crossing is computed directly from its plane index (no incremental
+// parameter that drifts), and the crossing order inside a slab decides the
+// middle voxel.  Summing (segment length in sigma) * value and multiplying by
+// the ray's mm-per-sigma factor gives exactly the Siddon line integral up to
+// FP32 rounding of the crossing positions.
+//
+// Coherence.  The 32 lanes of a warp are 32 adjacent detector columns u of
+// one detector row, and the slab loop is warp-synchronous (the loop index is
+// the same physical slab for all lanes), so at every step the lanes touch 32
+// neighbouring voxels along the lateral axis that varies with u.  That axis
+// is x for rays advancing along y (layout [z][y][x], x fastest) and y for
+// rays advancing along x, which therefore read a transposed copy laid out
+// [z][x][y] (y fastest).  Either way the warp's gathers (and the
+// backprojector's atomics) fall on one or two 128-byte lines.
+#include <climits>
+
+#include "ct_internal.h"
+
+namespace ct {
+namespace {
+
+constexpr int kTU = 32;  // detector columns per CTA (one warp row)
+constexpr int kTV = 8;   // detector rows per CTA
+
+struct Ray {
+    int soff0 = 0, sstep = 0;   // memory offset of walk slab k: soff0 + k * sstep + i + j * bstride
+    int bstride = 0;            // stride of lateral axis b (lateral a has stride 1)
+    int cs = 0;                 // walk slab k spans w in [k - cs, k + 1 - cs]
+    float fa_lo = 0.f, fa_hi = 0.f, fb_lo = 0.f, fb_hi = 0.f;  // centred index ranges
+    float xi0 = 0.f, A = 0.f, invA = 0.f;
+    float ze0 = 0.f, C = 0.f, invC = 0.f;
+    float w_in = 0.f, w_out = 0.f;
+    int k_first = INT_MAX, k_last = -1;
+    float lsig = 0.f;           // mm of ray per unit w
+    bool transposed = false;    // walks the [z][x][y] copy
+};
+
+// Clip to the box and the source..pixel segment; fills the walk range and
+// the mm-per-w factor.  Ns, Na, Nb: sizes along the slab and lateral axes.
+__device__ __forceinline__ bool ray_clip(Ray &r, int Ns, int Na, int Nb, int ca, int cb,
+                                         float wsrc, float wpix, float hs, float ha, float hb) {
+    r.invA = 1.f / r.A;
+    r.invC = 1.f / r.C;
+    r.fa_lo = (float)(-ca);
+    r.fa_hi = (float)(Na - 1 - ca);
+    r.fb_lo = (float)(-cb);
+    r.fb_hi = (float)(Nb - 1 - cb);
+    float lo = fmaxf((float)(-r.cs), wsrc), hi = fminf((float)(Ns - r.cs), wpix);
+    if (r.A != 0.f) {
+        const float t0 = ((float)(-ca) - r.xi0) * r.invA, t1 = ((float)(Na - ca) - r.xi0) * r.invA;
+        lo = fmaxf(lo, fminf(t0, t1));
+        hi = fminf(hi, fmaxf(t0, t1));
+    } else if (!(r.xi0 >= (float)(-ca) && r.xi0 < (float)(Na - ca))) {
+        return false;
+    }
+    if (r.C != 0.f) {
+        const float t0 = ((float)(-cb) - r.ze0) * r.invC, t1 = ((float)(Nb - cb) - r.ze0) * r.invC;
+        lo = fmaxf(lo, fminf(t0, t1));
+        hi = fminf(hi, fmaxf(t0, t1));
+    } else if (!(r.ze0 >= (float)(-cb) && r.ze0 < (float)(Nb - cb))) {
+        return false;
+    }
+    if (!(lo < hi)) return false;
+    r.w_in = lo;
+    r.w_out = hi;
+    r.k_first = max(0, (int)floorf(lo) + r.cs);
+    r.k_last = min(Ns - 1, (int)ceilf(hi) - 1 + r.cs);
+    if (r.k_first > r.k_last) return false;
+    const float la = r.A * (ha / hs), lb = r.C * (hb / hs);
+    r.lsig = hs * sqrtf(fmaf(la, la, fmaf(lb, lb, 1.f)));
+    return true;
+}
+
+// Ray (u, v) of one view; returns false if it misses the volume box.
+// Rays advancing mostly along x or y use the per-column FP64-derived
+// parameters; the rare rays advancing mostly along z (very large cone angles)
+// are set up from the per-view constants in FP32.
+__device__ __forceinline__ bool ray_setup(const ProjGeom &g, int view, int u, int v, Ray &r) {
+    const float vc = (float)v - 0.5f * (float)(g.nv - 1);
+    const size_t ci = (size_t)view * g.nu + u;
+    const float4 pa = __ldg(g.col_a + ci);
+    const float4 pb = __ldg(g.col_b + ci);
+    const int fl = __ldg(g.col_flags + ci);
+    const float C = fmaf(vc, pa.w, pa.z);
+    if (fabsf(C) <= 1.f) {
+        int Ns, Na, sstride;
+        float hs, ha;
+        if (fl & 1) {            // slabs along x; lateral a = y; transposed copy [z][x][y]
+            Ns = g.nx; Na = g.ny; sstride = g.ny; hs = g.hx; ha = g.hy;
+            r.transposed = true;
+        } else {                 // slabs along y; lateral a = x
+            Ns = g.ny; Na = g.nx; sstride = g.nx; hs = g.hy; ha = g.hx;
+            r.transposed = false;
+        }
+        const int Nb = g.nz, ca = Na / 2, cb = Nb / 2;
+        r.cs = Ns / 2;
+        r.bstride = g.nx * g.ny;
+        if (fl & 2) {
+            r.soff0 = (Ns - 1) * sstride;
+            r.sstep = -sstride;
+        } else {
+            r.soff0 = 0;
+            r.sstep = sstride;
+        }
+        r.soff0 += ca + cb * r.bstride;
+        r.A = pa.x;
+        r.xi0 = pa.y;
+        r.C = C;
+        r.ze0 = fmaf(vc, pb.y, pb.x);
+        return ray_clip(r, Ns, Na, Nb, ca, cb, pb.z, pb.w, hs, ha, g.hz);
+    }
+    // slabs along z; lateral a = x, b = y; main layout
+    const ViewConst *vcp = g.views + view;
+    const float uc = (float)u - 0.5f * (float)(g.nu - 1);
+    float S[3], D[3];
+    for (int a = 0; a < 3; ++a) {
+        S[a] = __ldg(&vcp->s[a]);
+        const float p = fmaf(vc, __ldg(&vcp->ev[a]), fmaf(uc, __ldg(&vcp->eu[a]), __ldg(&vcp->p00[a])));
+        D[a] = p - S[a];
+    }
+    const int Ns = g.nz, Na = g.nx, Nb = g.ny, ca = Na / 2, cb = Nb / 2;
+    const int sstride = g.nx * g.ny;
+    r.cs = Ns / 2;
+    r.bstride = g.nx;
+    r.transposed = false;
+    const bool rev = D[2] < 0.f;
+    if (rev) {
+        r.soff0 = (Ns - 1) * sstride;
+        r.sstep = -sstride;
+    } else {
+        r.soff0 = 0;
+        r.sstep = sstride;
+    }
+    r.soff0 += ca + cb * r.bstride;
+    const float ad = fabsf(D[2]);
+    if (!(ad > 0.f)) return false;
+    const float sig0 = rev ? (float)(Ns - r.cs) : (float)r.cs;
+    const float t0 = (sig0 - S[2]) / D[2];
+    r.A = D[0] / ad;
+    r.C = D[1] / ad;
+    r.xi0 = fmaf(t0, D[0], S[0] - (float)ca);
+    r.ze0 = fmaf(t0, D[1], S[1] - (float)cb);
+    const float wsrc = (rev ? (float)Ns - S[2] : S[2]) - (float)r.cs;
+    const float wpix = (rev ? (float)Ns - (S[2] + D[2]) : S[2] + D[2]) - (float)r.cs;
+    return ray_clip(r, Ns, Na, Nb, ca, cb, wsrc, wpix, g.hz, g.hx, g.hy);
+}
+
+// Warp-synchronous slab walk.  fn(offset, w_length) is called for the up to
+// three segments of each slab (lengths may be 0; offsets always in range).
+// Must be called by all 32 lanes of the warp.
+template <class Fn>
+__device__ __forceinline__ void walk(const Ray &r, bool valid, Fn &&fn) {
+    const int kb = __reduce_min_sync(0xffffffffu, valid ? r.k_first : INT_MAX);
+    const int ke = __reduce_max_sync(0xffffffffu, valid ? r.k_last : -1);
+    if (kb > ke) return;
+    float w_lo = r.w_in;
+    float fi_lo = fminf(fmaxf(floorf(fmaf(w_lo, r.A, r.xi0)), r.fa_lo), r.fa_hi);
+    float fk_lo = fminf(fmaxf(floorf(fmaf(w_lo, r.C, r.ze0)), r.fb_lo), r.fb_hi);
+    for (int k = kb; k <= ke; ++k) {
+        if (valid && k >= r.k_first && k <= r.k_last) {
+            const float w_hi = fminf((float)(k + 1 - r.cs), r.w_out);
+            const float fi_n = fminf(fmaxf(floorf(fmaf(w_hi, r.A, r.xi0)), r.fa_lo), r.fa_hi);
+            const float fk_n = fminf(fmaxf(floorf(fmaf(w_hi, r.C, r.ze0)), r.fb_lo), r.fb_hi);
+            // at most one crossing per lateral axis inside a slab
+            const float fi_hi = fminf(fmaxf(fi_n, fi_lo - 1.f), fi_lo + 1.f);
+            const float fk_hi = fminf(fmaxf(fk_n, fk_lo - 1.f), fk_lo + 1.f);
+            float sx = (fi_hi != fi_lo) ? (fmaxf(fi_lo, fi_hi) - r.xi0) * r.invA : w_hi;
+            float sz = (fk_hi != fk_lo) ? (fmaxf(fk_lo, fk_hi) - r.ze0) * r.invC : w_hi;
+            sx = fminf(fmaxf(sx, w_lo), w_hi);
+            sz = fminf(fmaxf(sz, w_lo), w_hi);
+            const float s1 = fminf(sx, sz), s2 = fmaxf(sx, sz);
+            const int soff = r.soff0 + k * r.sstep;
+            const int ilo = (int)fi_lo, ihi = (int)fi_hi;
+            const int blo = (int)fk_lo * r.bstride, bhi = (int)fk_hi * r.bstride;
+            const int o1 = soff + ilo + blo;
+            const int o2 = (sx <= sz) ? soff + ihi + blo : soff + ilo + bhi;
+            const int o3 = soff + ihi + bhi;
+            fn(o1, s1 - w_lo);
+            fn(o2, s2 - s1);
+            fn(o3, w_hi - s2);
+            w_lo = w_hi;
+            fi_lo = fi_n;
+            fk_lo = fk_n;
+        }
+    }
+}
+
+__device__ __forceinline__ double block_sum_d(double x, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    const int lane = threadIdx.x & 31;
+    const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (blockDim.x * blockDim.y) >> 5;
+    if (lane == 0) sh[warp] = x;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = lane < nw ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    }
+    return t;  // valid in thread (0, 0)
+}
+
+__device__ __forceinline__ void coef_of(const Coef &c, float &alpha, float &beta) {
+    if (c.dev) {
+        alpha = (float)c.dev[0];
+        beta = (float)c.dev[1];
+    } else {
+        alpha = c.alpha;
+        beta = c.beta;
+    }
+}
+
+// p = alpha * rho o (A vol) + beta * p.  vol == NULL means the all-ones volume.
+template <bool HAS_RHO, bool NORM, bool UNIT_VOL>
+__global__ void __launch_bounds__(kTU *kTV) k_forward(ProjGeom g, const float *__restrict__ vol,
+                                                      const float *__restrict__ vol_t,
+                                                      float *__restrict__ out,
+                                                      const float *__restrict__ rho, Coef c,
+                                                      double *__restrict__ partials) {
+    __shared__ double sh[32];
+    const int u = blockIdx.x * kTU + threadIdx.x;
+    const int v = blockIdx.y * kTV + threadIdx.y;
+    const int view = blockIdx.z;
+    const bool inb = (u < g.nu) && (v < g.nv);
+    Ray r;
+    const bool valid = inb && ray_setup(g, view, u, v, r);
+    const float *base = r.transposed ? vol_t : vol;
+    float acc = 0.f;
+    walk(r, valid, [&](int o, float l) {
+        if (l > 0.f) acc = fmaf(l, UNIT_VOL ? 1.f : __ldg(base + o), acc);
+    });
+    float alpha, beta;
+    coef_of(c, alpha, beta);
+    double sq = 0.0;
+    if (inb) {
+        const size_t idx = ((size_t)view * g.nv + v) * g.nu + u;
+        float val = valid ? acc * r.lsig : 0.f;
+        if (HAS_RHO) val *= rho[idx];
+        float o = alpha * val;
+        if (beta != 0.f) o = fmaf(beta, out[idx], o);
+        out[idx] = o;
+        if (NORM) sq = (double)o * (double)o;
+    }
+    if (NORM) {
+        double t = block_sum_d(sq, sh);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            partials[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = t;
+    }
+}
+
+// acc += alpha * (A o A ... )^T: POWER 1 scatters length * w, POWER 2 scatters
+// length^2 * w, w = alpha * rho_i * e_i (e == NULL means e = 1).
+template <bool HAS_RHO, int POWER>
+__global__ void __launch_bounds__(kTU *kTV) k_backward(ProjGeom g, const float *__restrict__ e,
+                                                       const float *__restrict__ rho, Coef c,
+                                                       float *__restrict__ acc,
+                                                       float *__restrict__ acc_t) {
+    const int u = blockIdx.x * kTU + threadIdx.x;
+    const int v = blockIdx.y * kTV + threadIdx.y;
+    const int view = blockIdx.z;
+    const bool inb = (u < g.nu) && (v < g.nv);
+    Ray r;
+    bool valid = inb && ray_setup(g, view, u, v, r);
+    float alpha, beta;
+    coef_of(c, alpha, beta);
+    float w = 0.f;
+    if (valid) {
+        const size_t idx = ((size_t)view * g.nv + v) * g.nu + u;
+        w = alpha * (e ? e[idx] : 1.f);
+        if (HAS_RHO) w *= rho[idx];
+        if (POWER == 1) w *= r.lsig;
+    }
+    valid = valid && (w != 0.f);
+    float *base = r.transposed ? acc_t : acc;
+    const float ls = r.lsig;
+    walk(r, valid, [&](int o, float l) {
+        if (l > 0.f) {
+            if (POWER == 1) {
+                atomicAdd(base + o, w * l);
+            } else {
+                const float lm = l * ls;
+                atomicAdd(base + o, w * lm * lm);
+            }
+        }
+    });
+}
+
+__global__ void __launch_bounds__(kTU *kTV) k_count(ProjGeom g,
+                                                    unsigned long long *__restrict__ count) {
+    __shared__ double sh[32];
+    const int u = blockIdx.x * kTU + threadIdx.x;
+    const int v = blockIdx.y * kTV + threadIdx.y;
+    const int view = blockIdx.z;
+    const bool inb = (u < g.nu) && (v < g.nv);
+    Ray r;
+    const bool valid = inb && ray_setup(g, view, u, v, r);
+    int n = 0;
+    walk(r, valid, [&](int, float l) { n += (l > 0.f) ? 1 : 0; });
+    double t = block_sum_d((double)n, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(count, (unsigned long long)(t + 0.5));
+}
+
+dim3 proj_grid(const ProjGeom &pg) {
+    return dim3((unsigned)((pg.nu + kTU - 1) / kTU), (unsigned)((pg.nv + kTV - 1) / kTV),
+                (unsigned)pg.nviews);
+}
+
+bool empty(const ProjGeom &pg) { return pg.nu <= 0 || pg.nv <= 0 || pg.nviews <= 0; }
+
+}  // namespace
+
+int64_t forward_partials(const ProjGeom &pg) {
+    if (empty(pg)) return 0;
+    dim3 gr = proj_grid(pg);
+    return (int64_t)gr.x * gr.y * gr.z;
+}
+
+ct_status launch_forward(const ProjGeom &pg, const float *vol, const float *vol_t, float *p,
+                         const float *rho, Coef c, double *partials, cudaStream_t st) {
+    if (empty(pg)) return CT_OK;
+    dim3 gr = proj_grid(pg), bl(kTU, kTV);
+    const bool unit = (vol == nullptr);
+    const bool hr = (rho != nullptr), nm = (partials != nullptr);
+#define CT_FWD(HR, NM, UV) \
+    k_forward<HR, NM, UV><<<gr, bl, 0, st>>>(pg, vol, vol_t, p, rho, c, partials)
+    if (unit) {
+        if (hr) { if (nm) CT_FWD(true, true, true); else CT_FWD(true, false, true); }
+        else    { if (nm) CT_FWD(false, true, true); else CT_FWD(false, false, true); }
+    } else {
+        if (hr) { if (nm) CT_FWD(true, true, false); else CT_FWD(true, false, false); }
+        else    { if (nm) CT_FWD(false, true, false); else CT_FWD(false, false, false); }
+    }
+#undef CT_FWD
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+ct_status launch_backward(const ProjGeom &pg, const float *e, const float *rho, Coef c,
+                          float *acc, float *acc_t, int power, cudaStream_t st) {
+    if (empty(pg)) return CT_OK;
+    dim3 gr = proj_grid(pg), bl(kTU, kTV);
+    const bool hr = (rho != nullptr);
+    if (power == 2) {
+        if (hr) k_backward<true, 2><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t);
+        else    k_backward<false, 2><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t);
+    } else {
+        if (hr) k_backward<true, 1><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t);
+        else    k_backward<false, 1><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t);
+    }
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+ct_status launch_count(const ProjGeom &pg, unsigned long long *d_count, cudaStream_t st) {
+    CT_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st));
+    if (empty(pg)) return CT_OK;
+    k_count<<<proj_grid(pg), dim3(kTU, kTV), 0, st>>>(pg, d_count);
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+}  // namespace ct

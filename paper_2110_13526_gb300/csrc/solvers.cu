@@ -1,0 +1,645 @@
+// CGLS (Algorithm 1, CGLS with delayed residual computation) and LSQR
+// (Paige & Saunders 1982) drivers.
+//
+// Vectors are FP32 in device memory; the Krylov scalars (NB0, NR2, NP2,
+// alpha, beta, NB and LSQR's rotation scalars) live in device memory in FP64
+// and are updated by one-CTA kernels that also finish the FP64 reductions, so
+// the host never needs them inside the loop.  The host reads NB back only
+// when a discrepancy tolerance ERR > 0 has to be tested.
+//
+// Preconditioning runs the unchanged recurrences on L A W (left ray weights
+// L, right voxel weights W) with x = x0 + W y: the direction is kept in
+// x-space, z = W d_y, so A is applied to z directly, and the weights are
+// folded into the streaming kernels (L into the projector's epilogue and the
+// backprojector's ray weight).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "ct_internal.h"
+
+namespace ct {
+namespace {
+
+__device__ __forceinline__ double block_sum(double x, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) sh[warp] = x;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = lane < nw ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    }
+    return t;  // valid in thread 0
+}
+
+// Fixed-order sum of partials by one CTA (1024 threads); result in thread 0.
+__device__ __forceinline__ double sum_partials(const double *__restrict__ p, int64_t n,
+                                               double *sh) {
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += p[i];
+    return block_sum(s, sh);
+}
+
+__device__ __forceinline__ double safe_div(double a, double b) { return b != 0.0 ? a / b : 0.0; }
+
+// ---- CGLS ------------------------------------------------------------------
+struct CglsS {
+    double nb0, nr2_old, nr2_now, np2, alpha, beta, nb, a_pend, tmp;
+};
+
+// e = L o b; partial sums of e^2 (one per CTA).
+__global__ void k_sino_weighted_copy(float *__restrict__ e, const float *__restrict__ b,
+                                     const float *__restrict__ L, int64_t n,
+                                     double *__restrict__ part) {
+    __shared__ double sh[32];
+    double sq = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = L ? L[i] * b[i] : b[i];
+        e[i] = v;
+        sq = fma((double)v, (double)v, sq);
+    }
+    const double t = block_sum(sq, sh);
+    if (threadIdx.x == 0 && part) part[blockIdx.x] = t;
+}
+
+// e_b = e_b - alpha p_b; partial sums of e_b^2 (Algorithm 1: NB = ||e_b||).
+__global__ void k_sino_axpy(float *__restrict__ e, const float *__restrict__ p, int64_t n,
+                            const double *__restrict__ alpha, double *__restrict__ part) {
+    __shared__ double sh[32];
+    const float a = (float)alpha[0];
+    double sq = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = fmaf(-a, p[i], e[i]);
+        e[i] = v;
+        sq = fma((double)v, (double)v, sq);
+    }
+    const double t = block_sum(sq, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// x = x + a_pend z (the x update delayed from the previous iteration), then
+// z = W^2 g + beta z (d_x = r_x + beta d_x in y-space, stored as z = W d).
+// first: z = W^2 g, neither x nor the old z is read.
+__global__ void k_vol_update(float *__restrict__ x, float *__restrict__ z,
+                             const float *__restrict__ g, const float *__restrict__ W, int64_t n,
+                             const double *__restrict__ a_pend, const double *__restrict__ beta,
+                             int first) {
+    const float a = first ? 0.f : (float)a_pend[0];
+    const float b = first ? 0.f : (float)beta[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float r = g[i];
+        if (W) {
+            const float w = W[i];
+            r *= w * w;
+        }
+        if (first) {
+            z[i] = r;
+        } else {
+            const float zo = z[i];
+            if (a != 0.f) x[i] = fmaf(a, zo, x[i]);
+            z[i] = fmaf(b, zo, r);
+        }
+    }
+}
+
+__global__ void k_vol_axpy(float *__restrict__ x, const float *__restrict__ z, int64_t n,
+                           const double *__restrict__ a) {
+    const float s = (float)a[0];
+    if (s == 0.f) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = fmaf(s, z[i], x[i]);
+}
+
+__global__ void __launch_bounds__(1024) k_cgls_nb0(const double *__restrict__ p, int64_t n,
+                                                   CglsS *S) {
+    __shared__ double sh[32];
+    const double t = sum_partials(p, n, sh);
+    if (threadIdx.x == 0) {
+        S->nb0 = sqrt(t);
+        S->a_pend = 0.0;
+        S->beta = 0.0;
+        S->alpha = 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_store_sum(const double *__restrict__ p, int64_t n,
+                                                    double *out) {
+    __shared__ double sh[32];
+    const double t = sum_partials(p, n, sh);
+    if (threadIdx.x == 0) out[0] = t;
+}
+
+// NR2_now = ||r_x||^2; beta = NR2_now / NR2_old; NR2_old = NR2_now.
+__global__ void __launch_bounds__(1024) k_cgls_nr2(const double *__restrict__ p, int64_t n,
+                                                   CglsS *S, int first) {
+    __shared__ double sh[32];
+    const double t = sum_partials(p, n, sh);
+    if (threadIdx.x == 0) {
+        S->nr2_now = t;
+        S->beta = first ? 0.0 : safe_div(t, S->nr2_old);
+        S->nr2_old = t;
+    }
+}
+
+// NP2 = ||p_b||^2; alpha = NR2_old / NP2 (also the pending x step).
+__global__ void __launch_bounds__(1024) k_cgls_np2(const double *__restrict__ p, int64_t n,
+                                                   CglsS *S) {
+    __shared__ double sh[32];
+    const double t = sum_partials(p, n, sh);
+    if (threadIdx.x == 0) {
+        S->np2 = t;
+        S->alpha = safe_div(S->nr2_old, t);
+        S->a_pend = S->alpha;
+    }
+}
+
+// NB = ||e_b||; history[i] = NB / NB0.
+__global__ void __launch_bounds__(1024) k_cgls_nb(const double *__restrict__ p, int64_t n,
+                                                  CglsS *S, double *hist, int i) {
+    __shared__ double sh[32];
+    const double t = sum_partials(p, n, sh);
+    if (threadIdx.x == 0) {
+        S->nb = sqrt(t);
+        hist[i] = safe_div(S->nb, S->nb0);
+    }
+}
+
+__global__ void k_set_zero(double *p) { p[0] = 0.0; }
+
+// ---- LSQR ------------------------------------------------------------------
+struct LsqrS {
+    double nb0, alpha, beta, inv_beta, inv_alpha, rhobar, phibar, x_step, w_step, tmp;
+    double coef_fwd[2];   // projector epilogue: u = 1 * L A t - alpha / beta_old * u
+    double coef_back[2];  // backprojector scale: 1 / beta
+};
+
+__global__ void __launch_bounds__(1024) k_lsqr_nb0(const double *__restrict__ p, int64_t n,
+                                                   LsqrS *S) {
+    __shared__ double sh[32];
+    const double t = sum_partials(p, n, sh);
+    if (threadIdx.x == 0) S->nb0 = sqrt(t);
+}
+
+// beta u = A v - alpha u: beta = ||u_s||, u = u_s / beta (kept as a scale).
+__global__ void __launch_bounds__(1024) k_lsqr_beta(const double *__restrict__ p, int64_t n,
+                                                    LsqrS *S) {
+    __shared__ double sh[32];
+    const double t = sum_partials(p, n, sh);
+    if (threadIdx.x == 0) {
+        S->beta = sqrt(t);
+        S->inv_beta = safe_div(1.0, S->beta);
+        S->coef_back[0] = S->inv_beta;
+        S->coef_back[1] = 0.0;
+    }
+}
+
+// alpha_1 = ||W A^T u_1||; rhobar = alpha_1; phibar = beta_1.
+__global__ void __launch_bounds__(1024) k_lsqr_alpha0(const double *__restrict__ p, int64_t n,
+                                                      LsqrS *S) {
+    __shared__ double sh[32];
+    const double t = sum_partials(p, n, sh);
+    if (threadIdx.x == 0) {
+        S->alpha = sqrt(t);
+        S->inv_alpha = safe_div(1.0, S->alpha);
+        S->rhobar = S->alpha;
+        S->phibar = S->beta;
+    }
+}
+
+__global__ void k_lsqr_coef_fwd(LsqrS *S) {
+    S->coef_fwd[0] = 1.0;
+    S->coef_fwd[1] = -S->alpha * S->inv_beta;
+}
+
+// v = W g / alpha; w = v.
+__global__ void k_lsqr_vinit(float *__restrict__ v, float *__restrict__ wv,
+                             const float *__restrict__ g, const float *__restrict__ W, int64_t n,
+                             const LsqrS *__restrict__ S) {
+    const float ia = (float)S->inv_alpha;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float t = g[i] * ia;
+        if (W) t *= W[i];
+        v[i] = t;
+        wv[i] = t;
+    }
+}
+
+// alpha v = A^T u - beta v: v_s = W g - beta v (v normalised); partial ||v_s||^2.
+__global__ void k_lsqr_v(float *__restrict__ v, const float *__restrict__ g,
+                         const float *__restrict__ W, int64_t n, const LsqrS *__restrict__ S,
+                         double *__restrict__ part) {
+    __shared__ double sh[32];
+    const float b = (float)S->beta;
+    double sq = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float t = g[i];
+        if (W) t *= W[i];
+        t = fmaf(-b, v[i], t);
+        v[i] = t;
+        sq = fma((double)t, (double)t, sq);
+    }
+    const double t = block_sum(sq, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// Plane rotation of the bidiagonal (Paige & Saunders): rho, c, s, theta,
+// rhobar, phi, phibar; history[i] = phibar / NB0.
+__global__ void __launch_bounds__(1024) k_lsqr_rot(const double *__restrict__ p, int64_t n,
+                                                   LsqrS *S, double *hist, int i) {
+    __shared__ double sh[32];
+    const double t = sum_partials(p, n, sh);
+    if (threadIdx.x == 0) {
+        const double alpha = sqrt(t);
+        const double beta = S->beta;
+        const double rho = sqrt(S->rhobar * S->rhobar + beta * beta);
+        const double c = rho != 0.0 ? S->rhobar / rho : 1.0;
+        const double s = rho != 0.0 ? beta / rho : 0.0;
+        const double theta = s * alpha;
+        S->rhobar = -c * alpha;
+        const double phi = c * S->phibar;
+        S->phibar = s * S->phibar;
+        S->x_step = safe_div(phi, rho);
+        S->w_step = safe_div(theta, rho);
+        S->alpha = alpha;
+        S->inv_alpha = safe_div(1.0, alpha);
+        hist[i] = safe_div(S->phibar, S->nb0);
+    }
+}
+
+// v = v_s / alpha; x += (phi / rho) W w; w = v - (theta / rho) w.
+__global__ void k_lsqr_update(float *__restrict__ x, float *__restrict__ v, float *__restrict__ wv,
+                              const float *__restrict__ W, int64_t n,
+                              const LsqrS *__restrict__ S) {
+    const float ia = (float)S->inv_alpha, xs = (float)S->x_step, ws = (float)S->w_step;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float vn = v[i] * ia;
+        const float wo = wv[i];
+        const float step = W ? xs * W[i] : xs;
+        x[i] = fmaf(step, wo, x[i]);
+        v[i] = vn;
+        wv[i] = fmaf(-ws, wo, vn);
+    }
+}
+
+// ---- helpers -----------------------------------------------------------------
+struct OpTimer {
+    bool on;
+    cudaStream_t st;
+    std::vector<cudaEvent_t> fwd, back;
+    OpTimer(bool enabled, cudaStream_t s) : on(enabled), st(s) {}
+    ~OpTimer() {
+        for (auto e : fwd) cudaEventDestroy(e);
+        for (auto e : back) cudaEventDestroy(e);
+    }
+    ct_status mark(std::vector<cudaEvent_t> &v) {
+        if (!on) return CT_OK;
+        cudaEvent_t e;
+        CT_CUDA_TRY(cudaEventCreate(&e));
+        v.push_back(e);
+        CT_CUDA_TRY(cudaEventRecord(e, st));
+        return CT_OK;
+    }
+    double total(const std::vector<cudaEvent_t> &v) const {
+        double ms = 0.0;
+        for (size_t k = 0; k + 1 < v.size(); k += 2) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, v[k], v[k + 1]) == cudaSuccess) ms += t;
+        }
+        return ms;
+    }
+};
+
+ct_status check_opts(const ct_geometry *g, const float *b, float *x, const ct_solver_opts *o) {
+    if (!g) return set_error(CT_ERR_INVALID_ARG, "geometry is NULL");
+    if (!o) return set_error(CT_ERR_INVALID_ARG, "opts is NULL");
+    if (!x || (g->nrays > 0 && !b)) return set_error(CT_ERR_INVALID_ARG, "NULL vector");
+    if (o->max_iter < 1) return set_error(CT_ERR_INVALID_ARG, "max_iter must be >= 1");
+    if (!std::isfinite(o->err_tol) || o->err_tol < 0.0)
+        return set_error(CT_ERR_INVALID_ARG, "err_tol must be finite and >= 0");
+    if (o->precond != CT_PRECOND_NONE && o->precond != CT_PRECOND_JACOBI &&
+        o->precond != CT_PRECOND_ROWCOL)
+        return set_error(CT_ERR_INVALID_ARG, "unknown precond");
+    if (o->tikhonov_lambda != 0.0)
+        return set_error(CT_ERR_INVALID_ARG, "Tikhonov regularisation is not supported");
+    if (o->recompute_every < 0) return set_error(CT_ERR_INVALID_ARG, "recompute_every < 0");
+    return CT_OK;
+}
+
+// Common state of one solve: workspace vectors, weights, timing, op counts.
+struct Solve {
+    const ct_geometry *g;
+    const ProjGeom &pg;
+    cudaStream_t st;
+    Workspace ws;
+    OpTimer tm;
+    int n_fwd = 0, n_back = 0;
+    float *T = nullptr;           // transposed scratch volume (input copy / accumulator)
+    double *part = nullptr;       // FP64 partial sums
+    float *W = nullptr, *L = nullptr;
+    int64_t n, m;
+    Solve(const ct_geometry *g_, cudaStream_t s, bool timing)
+        : g(g_), pg(g_->pg), st(s), ws(s), tm(timing, s), n(g_->nvox), m(g_->nrays) {}
+
+    ct_status init(int precond) {
+        CT_TRY(ws.alloc(&T, (size_t)n));
+        int64_t np = std::max<int64_t>(forward_partials(pg), transpose_grid_count(pg));
+        np = std::max<int64_t>(np, std::max(vec_grid(n), vec_grid(m)));
+        CT_TRY(ws.alloc(&part, (size_t)np));
+        if (precond != CT_PRECOND_NONE) {
+            CT_TRY(ws.alloc(&W, (size_t)n));
+            if (precond == CT_PRECOND_ROWCOL) CT_TRY(ws.alloc(&L, (size_t)std::max<int64_t>(m, 1)));
+            CT_TRY(precond_weights_impl(g, precond, W, L, ws, st));
+        }
+        return CT_OK;
+    }
+    // out = c.alpha * L o (A vol) + c.beta * out (vol_main may already be
+    // accompanied by its transposed copy in T when have_t).
+    ct_status forward(const float *vol, bool have_t, float *out, Coef c, double *partials) {
+        if (!have_t) CT_TRY(launch_transpose(pg, vol, nullptr, T, nullptr, st));
+        CT_TRY(tm.mark(tm.fwd));
+        CT_TRY(launch_forward(pg, vol, T, out, L, c, partials, st));
+        CT_TRY(tm.mark(tm.fwd));
+        ++n_fwd;
+        return CT_OK;
+    }
+    // gout = c * A^T (L o e), then partials of (Wg)^2 if requested.
+    ct_status back(const float *e, float *gout, Coef c, const float *wnorm, double *partials) {
+        CT_CUDA_TRY(cudaMemsetAsync(gout, 0, (size_t)n * sizeof(float), st));
+        CT_CUDA_TRY(cudaMemsetAsync(T, 0, (size_t)n * sizeof(float), st));
+        CT_TRY(tm.mark(tm.back));
+        CT_TRY(launch_backward(pg, e, L, c, gout, T, 1, st));
+        CT_TRY(tm.mark(tm.back));
+        ++n_back;
+        return launch_combine(pg, gout, T, wnorm, partials, st);
+    }
+    // Is x0 nonzero?  (One reduction and one host read.)
+    ct_status nonzero(const float *x, bool *out) {
+        CT_TRY(launch_norm2(x, nullptr, n, part, st));
+        double *d = nullptr;
+        CT_TRY(ws.alloc(&d, 1));
+        k_store_sum<<<1, 1024, 0, st>>>(part, vec_grid(n), d);
+        CT_CHECK_LAUNCH();
+        double h = 0.0;
+        CT_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CT_CUDA_TRY(cudaStreamSynchronize(st));
+        *out = (h != 0.0);
+        return CT_OK;
+    }
+    void report(ct_solver_report *r, int iters, double nb0, double nb, const std::vector<double> &h) {
+        if (!r) return;
+        r->iterations = iters;
+        r->nb0 = nb0;
+        r->nb = nb;
+        r->n_forward = n_fwd;
+        r->n_back = n_back;
+        r->ms_forward = tm.on ? tm.total(tm.fwd) : 0.0;
+        r->ms_back = tm.on ? tm.total(tm.back) : 0.0;
+        if (r->history_nb && r->history_cap > 0) {
+            const int k = std::min<int>(iters, r->history_cap);
+            for (int j = 0; j < k; ++j) r->history_nb[j] = h[(size_t)j];
+        }
+    }
+};
+
+template <class S>
+ct_status read_scalars(const S *d, S *h, cudaStream_t st) {
+    CT_CUDA_TRY(cudaMemcpyAsync(h, d, sizeof(S), cudaMemcpyDeviceToHost, st));
+    CT_CUDA_TRY(cudaStreamSynchronize(st));
+    return CT_OK;
+}
+
+
+ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_solver_opts *o,
+                    ct_solver_report *rep, cudaStream_t st) {
+    const int K = o->max_iter;
+    const double ERR = o->err_tol;
+    Solve sv(g, st, o->timing != 0);
+    CT_TRY(sv.init(o->precond));
+    const int64_t n = sv.n, m = sv.m;
+    const int gn = vec_grid(n), gm = vec_grid(m);
+    const int64_t nfp = forward_partials(sv.pg), ncp = transpose_grid_count(sv.pg);
+    float *z = nullptr, *gv = nullptr, *e = nullptr, *p = nullptr;
+    CglsS *S = nullptr;
+    double *hist = nullptr;
+    CT_TRY(sv.ws.alloc(&z, (size_t)n));
+    CT_TRY(sv.ws.alloc(&gv, (size_t)n));
+    CT_TRY(sv.ws.alloc(&e, (size_t)std::max<int64_t>(m, 1)));
+    CT_TRY(sv.ws.alloc(&p, (size_t)std::max<int64_t>(m, 1)));
+    CT_TRY(sv.ws.alloc(&S, 1));
+    CT_TRY(sv.ws.alloc(&hist, (size_t)K));
+    CT_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(CglsS), st));
+    Coef one;                              // (1, 0)
+    Coef sub;                              // (-1, 1): e = e - L A x
+    sub.alpha = -1.f;
+    sub.beta = 1.f;
+
+    // NB0 = ||b||; e_b = b - A x0 (the A x0 call is skipped for x0 = 0)
+    bool x0nz = false;
+    CT_TRY(sv.nonzero(x, &x0nz));
+    k_sino_weighted_copy<<<gm, kVecThreads, 0, st>>>(e, b, sv.L, m, sv.part);
+    CT_CHECK_LAUNCH();
+    k_cgls_nb0<<<1, 1024, 0, st>>>(sv.part, gm, S);
+    CT_CHECK_LAUNCH();
+    if (x0nz) CT_TRY(sv.forward(x, false, e, sub, nullptr));
+    // r_x = A^T e_b; d_x = r_x; NR2_old = ||r_x||^2
+    CT_TRY(sv.back(e, gv, one, sv.W, sv.part));
+    k_cgls_nr2<<<1, 1024, 0, st>>>(sv.part, ncp, S, 1);
+    CT_CHECK_LAUNCH();
+    k_vol_update<<<gn, kVecThreads, 0, st>>>(x, z, gv, sv.W, n, &S->a_pend, &S->beta, 1);
+    CT_CHECK_LAUNCH();
+    // p_b = A d_x; NP2; alpha
+    CT_TRY(sv.forward(z, false, p, one, sv.part));
+    k_cgls_np2<<<1, 1024, 0, st>>>(sv.part, nfp, S);
+    CT_CHECK_LAUNCH();
+    // (x = x + alpha d_x is delayed into the next volume update)
+    // e_b = e_b - alpha p_b; NB = ||e_b||
+    k_sino_axpy<<<gm, kVecThreads, 0, st>>>(e, p, m, &S->alpha, sv.part);
+    CT_CHECK_LAUNCH();
+    k_cgls_nb<<<1, 1024, 0, st>>>(sv.part, gm, S, hist, 0);
+    CT_CHECK_LAUNCH();
+    int i = 1;
+    CglsS hs{};
+    auto keep_going = [&](bool *go) -> ct_status {
+        *go = i < K;
+        if (*go && ERR > 0.0) {
+            CT_TRY(read_scalars(S, &hs, st));
+            *go = (hs.nb0 > 0.0) && (hs.nb / hs.nb0 > ERR);
+        }
+        return CT_OK;
+    };
+    bool go = false;
+    CT_TRY(keep_going(&go));
+    while (go) {
+        // r_x = A^T e_b; NR2_now; beta; NR2_old = NR2_now
+        CT_TRY(sv.back(e, gv, one, sv.W, sv.part));
+        k_cgls_nr2<<<1, 1024, 0, st>>>(sv.part, ncp, S, 0);
+        CT_CHECK_LAUNCH();
+        // x = x + alpha d_x (previous iteration); d_x = r_x + beta d_x
+        k_vol_update<<<gn, kVecThreads, 0, st>>>(x, z, gv, sv.W, n, &S->a_pend, &S->beta, 0);
+        CT_CHECK_LAUNCH();
+        // p_b = A d_x; NP2; alpha
+        CT_TRY(sv.forward(z, false, p, one, sv.part));
+        k_cgls_np2<<<1, 1024, 0, st>>>(sv.part, nfp, S);
+        CT_CHECK_LAUNCH();
+        // e_b = e_b - alpha p_b; NB
+        k_sino_axpy<<<gm, kVecThreads, 0, st>>>(e, p, m, &S->alpha, sv.part);
+        CT_CHECK_LAUNCH();
+        ++i;
+        if (o->recompute_every > 0 && i % o->recompute_every == 0) {
+            // discrepancy recomputed from the solution (Discussion)
+            k_vol_axpy<<<gn, kVecThreads, 0, st>>>(x, z, n, &S->a_pend);
+            CT_CHECK_LAUNCH();
+            k_set_zero<<<1, 1, 0, st>>>(&S->a_pend);
+            CT_CHECK_LAUNCH();
+            k_sino_weighted_copy<<<gm, kVecThreads, 0, st>>>(e, b, sv.L, m, nullptr);
+            CT_CHECK_LAUNCH();
+            CT_TRY(sv.forward(x, false, e, sub, nullptr));
+            CT_TRY(launch_norm2(e, nullptr, m, sv.part, st));
+        }
+        k_cgls_nb<<<1, 1024, 0, st>>>(sv.part, gm, S, hist, i - 1);
+        CT_CHECK_LAUNCH();
+        CT_TRY(keep_going(&go));
+    }
+    // the last pending x = x + alpha d_x
+    k_vol_axpy<<<gn, kVecThreads, 0, st>>>(x, z, n, &S->a_pend);
+    CT_CHECK_LAUNCH();
+    std::vector<double> h((size_t)K, 0.0);
+    CT_CUDA_TRY(cudaMemcpyAsync(h.data(), hist, sizeof(double) * (size_t)i,
+                                cudaMemcpyDeviceToHost, st));
+    CT_TRY(read_scalars(S, &hs, st));
+    sv.report(rep, i, hs.nb0, hs.nb, h);
+    return CT_OK;
+}
+
+ct_status lsqr_impl(const ct_geometry *g, const float *b, float *x, const ct_solver_opts *o,
+                    ct_solver_report *rep, cudaStream_t st) {
+    const int K = o->max_iter;
+    const double ERR = o->err_tol;
+    Solve sv(g, st, o->timing != 0);
+    CT_TRY(sv.init(o->precond));
+    const int64_t n = sv.n, m = sv.m;
+    const int gn = vec_grid(n), gm = vec_grid(m);
+    const int64_t nfp = forward_partials(sv.pg), ncp = transpose_grid_count(sv.pg);
+    float *u = nullptr, *v = nullptr, *wv = nullptr, *gv = nullptr, *t = nullptr;
+    LsqrS *S = nullptr;
+    double *hist = nullptr;
+    CT_TRY(sv.ws.alloc(&u, (size_t)std::max<int64_t>(m, 1)));
+    CT_TRY(sv.ws.alloc(&v, (size_t)n));
+    CT_TRY(sv.ws.alloc(&wv, (size_t)n));
+    CT_TRY(sv.ws.alloc(&gv, (size_t)n));
+    if (sv.W) CT_TRY(sv.ws.alloc(&t, (size_t)n));
+    CT_TRY(sv.ws.alloc(&S, 1));
+    CT_TRY(sv.ws.alloc(&hist, (size_t)K));
+    CT_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(LsqrS), st));
+    Coef sub;
+    sub.alpha = -1.f;
+    sub.beta = 1.f;
+    Coef cf, cb;
+    cf.dev = S->coef_fwd;
+    cb.dev = S->coef_back;
+
+    // NB0 = ||L b||; beta_1 u_1 = L (b - A x0)
+    bool x0nz = false;
+    CT_TRY(sv.nonzero(x, &x0nz));
+    k_sino_weighted_copy<<<gm, kVecThreads, 0, st>>>(u, b, sv.L, m, sv.part);
+    CT_CHECK_LAUNCH();
+    k_lsqr_nb0<<<1, 1024, 0, st>>>(sv.part, gm, S);
+    CT_CHECK_LAUNCH();
+    if (x0nz) {
+        CT_TRY(sv.forward(x, false, u, sub, nullptr));
+        CT_TRY(launch_norm2(u, nullptr, m, sv.part, st));
+    }
+    k_lsqr_beta<<<1, 1024, 0, st>>>(sv.part, gm, S);
+    CT_CHECK_LAUNCH();
+    // alpha_1 v_1 = W A^T L u_1; w_1 = v_1; phibar = beta_1; rhobar = alpha_1
+    CT_TRY(sv.back(u, gv, cb, sv.W, sv.part));
+    k_lsqr_alpha0<<<1, 1024, 0, st>>>(sv.part, ncp, S);
+    CT_CHECK_LAUNCH();
+    k_lsqr_vinit<<<gn, kVecThreads, 0, st>>>(v, wv, gv, sv.W, n, S);
+    CT_CHECK_LAUNCH();
+    int i = 0;
+    LsqrS hs{};
+    bool go = K > 0;
+    if (go && ERR > 0.0) {
+        CT_TRY(read_scalars(S, &hs, st));
+        go = hs.nb0 > 0.0 && hs.phibar / hs.nb0 > ERR;
+    }
+    while (go) {
+        // beta u = L A W v - alpha u
+        const float *tin = v;
+        if (sv.W) {
+            CT_TRY(launch_transpose(sv.pg, v, sv.W, sv.T, t, st));
+            tin = t;
+        }
+        k_lsqr_coef_fwd<<<1, 1, 0, st>>>(S);
+        CT_CHECK_LAUNCH();
+        CT_TRY(sv.forward(tin, sv.W != nullptr, u, cf, sv.part));
+        k_lsqr_beta<<<1, 1024, 0, st>>>(sv.part, nfp, S);
+        CT_CHECK_LAUNCH();
+        // alpha v = W A^T L u - beta v
+        CT_TRY(sv.back(u, gv, cb, nullptr, nullptr));
+        k_lsqr_v<<<gn, kVecThreads, 0, st>>>(v, gv, sv.W, n, S, sv.part);
+        CT_CHECK_LAUNCH();
+        k_lsqr_rot<<<1, 1024, 0, st>>>(sv.part, gn, S, hist, i);
+        CT_CHECK_LAUNCH();
+        k_lsqr_update<<<gn, kVecThreads, 0, st>>>(x, v, wv, sv.W, n, S);
+        CT_CHECK_LAUNCH();
+        ++i;
+        go = i < K;
+        if (go && ERR > 0.0) {
+            CT_TRY(read_scalars(S, &hs, st));
+            go = hs.nb0 > 0.0 && hs.phibar / hs.nb0 > ERR;
+        }
+    }
+    std::vector<double> h((size_t)K, 0.0);
+    if (i > 0)
+        CT_CUDA_TRY(cudaMemcpyAsync(h.data(), hist, sizeof(double) * (size_t)i,
+                                    cudaMemcpyDeviceToHost, st));
+    CT_TRY(read_scalars(S, &hs, st));
+    sv.report(rep, i, hs.nb0, hs.phibar, h);
+    return CT_OK;
+}
+
+}  // namespace
+}  // namespace ct
+
+using namespace ct;
+
+extern "C" {
+
+ct_status ct_cgls(const ct_geometry *g, const float *d_b, float *d_x, const ct_solver_opts *opts,
+                  ct_solver_report *report, void *stream) {
+    clear_error();
+    CT_TRY(check_opts(g, d_b, d_x, opts));
+    DeviceGuard dg(g->device);
+    CT_TRY(dg.status());
+    cudaStream_t st = (cudaStream_t)stream;
+    ct_status s = cgls_impl(g, d_b, d_x, opts, report, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (s == CT_OK && e != cudaSuccess) return cuda_error(e, "ct_cgls");
+    return s;
+}
+
+ct_status ct_lsqr(const ct_geometry *g, const float *d_b, float *d_x, const ct_solver_opts *opts,
+                  ct_solver_report *report, void *stream) {
+    clear_error();
+    CT_TRY(check_opts(g, d_b, d_x, opts));
+    DeviceGuard dg(g->device);
+    CT_TRY(dg.status());
+    cudaStream_t st = (cudaStream_t)stream;
+    ct_status s = lsqr_impl(g, d_b, d_x, opts, report, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (s == CT_OK && e != cudaSuccess) return cuda_error(e, "ct_lsqr");
+    return s;
+}
+
+}  // extern "C"

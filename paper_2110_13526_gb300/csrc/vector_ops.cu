@@ -1,0 +1,233 @@
+// Streaming volume / sinogram kernels and deterministic FP64 reductions.
+//
+// Norms feeding the Krylov scalars (Algorithm 1: NR2 = ||r_x||^2,
+// NP2 = ||p_b||^2, NB = ||e_b||) are accumulated in FP64 (the Discussion
+// notes the package relies on double precision): each CTA writes one partial,
+// and one CTA sums the partials in a fixed order, so a result never depends
+// on scheduling.
+#include "ct_internal.h"
+
+namespace ct {
+namespace {
+
+constexpr int kTile = 32;
+
+__device__ __forceinline__ double block_sum_1d(double x, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nw = (blockDim.x * blockDim.y * blockDim.z) >> 5;
+    if (lane == 0) sh[warp] = x;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = lane < nw ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    }
+    return t;  // valid in thread 0
+}
+
+// in [nz][ny][nx] -> t [nz][nx][ny]; optionally scaled by w, optionally also
+// writing the scaled volume in the original layout.
+__global__ void __launch_bounds__(256) k_transpose(int nx, int ny, const float *__restrict__ in,
+                                                   const float *__restrict__ w,
+                                                   float *__restrict__ t,
+                                                   float *__restrict__ plain) {
+    __shared__ float tile[kTile][kTile + 1];
+    const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
+    const size_t zoff = (size_t)blockIdx.z * nx * ny;
+    for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
+        const int x = x0 + threadIdx.x, y = y0 + j;
+        if (x < nx && y < ny) {
+            const size_t i = zoff + (size_t)y * nx + x;
+            float val = in[i];
+            if (w) val *= w[i];
+            if (plain) plain[i] = val;
+            tile[j][threadIdx.x] = val;
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
+        const int y = y0 + threadIdx.x, x = x0 + j;
+        if (x < nx && y < ny) t[zoff + (size_t)x * ny + y] = tile[threadIdx.x][j];
+    }
+}
+
+// g[z][y][x] += acc_t[z][x][y]; optional partial of sum (w g)^2 per CTA.
+__global__ void __launch_bounds__(256) k_combine(int nx, int ny, float *__restrict__ g,
+                                                 const float *__restrict__ acc_t,
+                                                 const float *__restrict__ w,
+                                                 double *__restrict__ partials) {
+    __shared__ float tile[kTile][kTile + 1];
+    __shared__ double sh[32];
+    const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
+    const size_t zoff = (size_t)blockIdx.z * nx * ny;
+    for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
+        const int x = x0 + j, y = y0 + threadIdx.x;
+        if (x < nx && y < ny) tile[j][threadIdx.x] = acc_t[zoff + (size_t)x * ny + y];
+    }
+    __syncthreads();
+    double sq = 0.0;
+    for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
+        const int y = y0 + j, x = x0 + threadIdx.x;
+        if (x < nx && y < ny) {
+            const size_t i = zoff + (size_t)y * nx + x;
+            const float val = g[i] + tile[threadIdx.x][j];
+            g[i] = val;
+            const double q = w ? (double)(w[i] * val) : (double)val;
+            sq = fma(q, q, sq);
+        }
+    }
+    if (partials) {
+        const double t = block_sum_1d(sq, sh);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            partials[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = t;
+    }
+}
+
+__global__ void k_scale(float *__restrict__ out, int64_t n, float beta) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (beta == 0.f) ? 0.f : beta * out[i];
+}
+
+__global__ void k_scale_dev(float *__restrict__ out, int64_t n, const double *__restrict__ beta) {
+    const float b = (float)beta[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (b == 0.f) ? 0.f : b * out[i];
+}
+
+__global__ void k_norm2(const float *__restrict__ v, const float *__restrict__ w, int64_t n,
+                        double *__restrict__ partials) {
+    __shared__ double sh[32];
+    double sq = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double q = w ? (double)(w[i] * v[i]) : (double)v[i];
+        sq = fma(q, q, sq);
+    }
+    const double t = block_sum_1d(sq, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+// One CTA of 1024 threads: thread t sums partials t, t + 1024, ... in order,
+// then a fixed tree.
+__global__ void __launch_bounds__(1024) k_sum(const double *__restrict__ partials, int64_t n,
+                                              double *__restrict__ out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += partials[i];
+    const double t = block_sum_1d(s, sh);
+    if (threadIdx.x == 0) out[0] = t;
+}
+
+}  // namespace
+
+int vec_grid(int64_t n) {
+    int64_t b = (n + kVecThreads * 4 - 1) / (kVecThreads * 4);
+    if (b < 1) b = 1;
+    if (b > 152 * 8) b = 152 * 8;
+    return (int)b;
+}
+
+int transpose_grid_count(const ProjGeom &pg) {
+    return ((pg.nx + kTile - 1) / kTile) * ((pg.ny + kTile - 1) / kTile) * pg.nz;
+}
+
+ct_status launch_transpose(const ProjGeom &pg, const float *v, const float *w, float *t,
+                           float *out_plain, cudaStream_t st) {
+    dim3 gr((pg.nx + kTile - 1) / kTile, (pg.ny + kTile - 1) / kTile, pg.nz), bl(kTile, 8);
+    k_transpose<<<gr, bl, 0, st>>>(pg.nx, pg.ny, v, w, t, out_plain);
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+ct_status launch_combine(const ProjGeom &pg, float *g, const float *acc_t, const float *w,
+                         double *partials, cudaStream_t st) {
+    dim3 gr((pg.nx + kTile - 1) / kTile, (pg.ny + kTile - 1) / kTile, pg.nz), bl(kTile, 8);
+    k_combine<<<gr, bl, 0, st>>>(pg.nx, pg.ny, g, acc_t, w, partials);
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+ct_status launch_scale(float *out, int64_t n, float beta, cudaStream_t st) {
+    if (n <= 0) return CT_OK;
+    if (beta == 0.f) {
+        CT_CUDA_TRY(cudaMemsetAsync(out, 0, (size_t)n * sizeof(float), st));
+        return CT_OK;
+    }
+    if (beta == 1.f) return CT_OK;
+    k_scale<<<vec_grid(n), kVecThreads, 0, st>>>(out, n, beta);
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+ct_status launch_scale_dev(float *out, int64_t n, const double *beta, cudaStream_t st) {
+    if (n <= 0) return CT_OK;
+    k_scale_dev<<<vec_grid(n), kVecThreads, 0, st>>>(out, n, beta);
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+ct_status launch_sum(const double *partials, int64_t n, double *out, cudaStream_t st) {
+    k_sum<<<1, 1024, 0, st>>>(partials, n, out);
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+ct_status launch_norm2(const float *v, const float *w, int64_t n, double *partials,
+                       cudaStream_t st) {
+    k_norm2<<<vec_grid(n), kVecThreads, 0, st>>>(v, w, n, partials);
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+}  // namespace ct
+
+// ---- guarded inverse square roots (preconditioner weights) ------------------
+namespace ct {
+namespace {
+
+__global__ void k_max_partials(const float *__restrict__ v, int64_t n, float *__restrict__ part) {
+    __shared__ float sh[32];
+    float m = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, v[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_down_sync(0xffffffffu, t, o));
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
+    }
+}
+
+// v = 1 / sqrt(v) where v > rel * max(v), else 0.  part[0..np) hold block maxima.
+__global__ void k_inv_sqrt_guard(float *__restrict__ v, int64_t n, const float *__restrict__ part,
+                                 int np, float rel) {
+    float m = 0.f;
+    for (int i = 0; i < np; ++i) m = fmaxf(m, part[i]);
+    const float thr = rel * m;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = v[i];
+        v[i] = (x > thr && x > 0.f) ? 1.f / sqrtf(x) : 0.f;
+    }
+}
+
+}  // namespace
+
+ct_status launch_inv_sqrt_guarded(float *v, int64_t n, float rel, float *part, cudaStream_t st) {
+    if (n <= 0) return CT_OK;
+    const int gb = vec_grid(n);
+    k_max_partials<<<gb, kVecThreads, 0, st>>>(v, n, part);
+    CT_CHECK_LAUNCH();
+    k_inv_sqrt_guard<<<gb, kVecThreads, 0, st>>>(v, n, part, gb, rel);
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+}  // namespace ct

@@ -1,0 +1,180 @@
+"""GPU parity of ct_cgls / ct_lsqr with the FP64 oracle solvers.
+
+Tolerance: iterates within 1e-4 relative L2 of the oracle after k iterations
+(FP32 vectors, FP64 Krylov scalars)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle.solvers import cgls as ocgls
+from oracle.solvers import jacobi_weights, lsqr as olsqr, rowcol_weights
+
+pytestmark = pytest.mark.gpu
+
+TOL_X = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ct():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2110_13526_gb300 as m
+    m.lib()
+    oracle.build()
+    return m
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+@pytest.fixture(scope="module")
+def pr1():
+    """PR1: 64^3 nested phantom, 90 views, b = A x + 1 % Gaussian noise."""
+    cfg = synth.CONFIGS["PR1"]
+    og = oracle.OGeom(**cfg)
+    x = synth.voxelize(synth.nested_phantom(64.0, seed=0), cfg)
+    b = synth.gaussian_noise(oracle.project(og, x.astype(np.float64)), 0.01, seed=0)
+    return cfg, og, x, b.astype(np.float32)
+
+
+SMALL = dict(nx=30, ny=26, nz=18, vx=1.0, vy=1.0, vz=1.2, nu=44, nv=28, du=1.0, dv=1.0,
+             sid=250.0, sdd=400.0, nviews=24)
+
+
+@pytest.fixture(scope="module")
+def small():
+    og = oracle.OGeom(**SMALL)
+    ells = synth.random_ellipsoids(6, 5, *synth.box_of(SMALL), axis_range=(3.0, 10.0))
+    x = synth.voxelize(ells, SMALL)
+    b = synth.gaussian_noise(oracle.project(og, x.astype(np.float64)), 0.01, seed=1)
+    return SMALL, og, x, b.astype(np.float32)
+
+
+def test_cgls_pr1_k20(ct, pr1):
+    cfg, og, _, b = pr1
+    g = ct.Geometry(**cfg)
+    x, rep = ct.cgls(g, torch.from_numpy(b).cuda(), max_iter=20)
+    ref = ocgls(oracle.Operator(og), b.astype(np.float64), K=20)
+    assert rep.iterations == 20
+    assert rel(x.cpu().numpy(), ref.x) < TOL_X
+    np.testing.assert_allclose(rep.history, ref.history, rtol=TOL_X)
+    assert rep.nb0 == pytest.approx(ref.nb0, rel=1e-7)
+
+
+def test_lsqr_pr1_k20(ct, pr1):
+    cfg, og, _, b = pr1
+    g = ct.Geometry(**cfg)
+    x, rep = ct.lsqr(g, torch.from_numpy(b).cuda(), max_iter=20)
+    ref = olsqr(oracle.Operator(og), b.astype(np.float64), K=20)
+    assert rep.iterations == 20
+    assert rel(x.cpu().numpy(), ref.x) < TOL_X
+    np.testing.assert_allclose(rep.history, ref.history, rtol=TOL_X)
+
+
+def test_operator_call_counts(ct, small):
+    """Algorithm 1 saves a projection and a backprojection: K updates cost
+    2K operator calls (one more A for a nonzero x0); LSQR costs 2K + 1."""
+    cfg, _, _, b = small
+    g = ct.Geometry(**cfg)
+    bd = torch.from_numpy(b).cuda()
+    for K in (1, 2, 5):
+        _, r = ct.cgls(g, bd, max_iter=K)
+        assert (r.n_forward, r.n_back) == (K, K)
+        _, r = ct.cgls(g, bd, x0=torch.ones(g.vol_shape), max_iter=K)
+        assert (r.n_forward, r.n_back) == (K + 1, K)
+        _, r = ct.lsqr(g, bd, max_iter=K)
+        assert (r.n_forward, r.n_back) == (K, K + 1)
+
+
+def test_nonzero_x0_and_recompute(ct, small):
+    cfg, og, _, b = small
+    g = ct.Geometry(**cfg)
+    x0 = synth.random_field(g.vol_shape, seed=3) * 0.1
+    x, rep = ct.cgls(g, torch.from_numpy(b).cuda(), x0=torch.from_numpy(x0).cuda(), max_iter=8)
+    ref = ocgls(oracle.Operator(og), b.astype(np.float64), x0=x0.astype(np.float64), K=8)
+    assert rel(x.cpu().numpy(), ref.x) < TOL_X
+    x, rep = ct.lsqr(g, torch.from_numpy(b).cuda(), x0=torch.from_numpy(x0).cuda(), max_iter=8)
+    ref = olsqr(oracle.Operator(og), b.astype(np.float64), x0=x0.astype(np.float64), K=8)
+    assert rel(x.cpu().numpy(), ref.x) < TOL_X
+    x, rep = ct.cgls(g, torch.from_numpy(b).cuda(), max_iter=10, recompute_every=3)
+    ref = ocgls(oracle.Operator(og), b.astype(np.float64), K=10, recompute_every=3)
+    assert rel(x.cpu().numpy(), ref.x) < TOL_X
+    assert rep.nb == pytest.approx(ref.nb, rel=1e-4)
+    assert rep.n_forward == 10 + 3            # three recomputations at i = 3, 6, 9
+
+
+def test_stopping_rule(ct, small):
+    cfg, og, _, b = small
+    g = ct.Geometry(**cfg)
+    ref = ocgls(oracle.Operator(og), b.astype(np.float64), K=30)
+    err = 0.5 * (ref.history[5] + ref.history[6])   # met at the 7th update
+    _, rep = ct.cgls(g, torch.from_numpy(b).cuda(), max_iter=30, err_tol=err)
+    assert rep.iterations == 7 and rep.nb / rep.nb0 <= err
+    refl = olsqr(oracle.Operator(og), b.astype(np.float64), K=30, err=err)
+    _, rep = ct.lsqr(g, torch.from_numpy(b).cuda(), max_iter=30, err_tol=err)
+    assert rep.iterations == refl.iterations
+
+
+def test_precond_weights_match_oracle(ct, small):
+    cfg, og, _, _ = small
+    g = ct.Geometry(**cfg)
+    wj, _ = ct.precond_weights(g, "jacobi")
+    assert rel(wj.cpu().numpy(), jacobi_weights(og)) < 1e-5
+    wc, wr = ct.precond_weights(g, "rowcol")
+    L, C = rowcol_weights(og)
+    assert rel(wr.cpu().numpy(), L) < 1e-5
+    assert rel(wc.cpu().numpy(), C) < 1e-5
+    assert torch.isfinite(wj).all() and torch.isfinite(wr).all()
+    # rays that miss the volume (wide detector) have no data: weight 0, no inf/NaN
+    wide = dict(cfg, du=3.0, dv=3.0)
+    gw = ct.Geometry(**wide)
+    _, wr2 = ct.precond_weights(gw, "rowcol")
+    L2, _ = rowcol_weights(oracle.OGeom(**wide))
+    assert torch.isfinite(wr2).all() and (wr2 == 0).any()
+    assert torch.equal(wr2 == 0, torch.from_numpy(L2 == 0).cuda())
+
+
+@pytest.mark.parametrize("kind", ["jacobi", "rowcol"])
+def test_preconditioned_solvers(ct, small, kind):
+    cfg, og, _, b = small
+    g = ct.Geometry(**cfg)
+    if kind == "jacobi":
+        left, right = None, jacobi_weights(og)
+    else:
+        left, right = rowcol_weights(og)
+    for solver, osolver in ((ct.cgls, ocgls), (ct.lsqr, olsqr)):
+        x, rep = solver(g, torch.from_numpy(b).cuda(), max_iter=10, precond=kind)
+        ref = osolver(oracle.Operator(og), b.astype(np.float64), K=10, left=left, right=right)
+        assert rel(x.cpu().numpy(), ref.x) < TOL_X
+        np.testing.assert_allclose(rep.history, ref.history, rtol=TOL_X)
+
+
+def test_timing_report_and_host_path(ct, small):
+    cfg, _, _, b = small
+    g = ct.Geometry(**cfg)
+    xd, rd = ct.cgls(g, torch.from_numpy(b).cuda(), max_iter=4, timing=True)
+    assert rd.ms_forward > 0 and rd.ms_back > 0
+    xh, rh = ct.cgls(g, torch.from_numpy(b), max_iter=4)       # host tensors in and out
+    assert xh.device.type == "cpu"
+    assert rel(xh.numpy(), xd.cpu().numpy()) < 1e-5
+
+
+def test_b256_first_iterate_property(ct):
+    """256^3: one CGLS update equals the closed form x1 = (||A^T b||^2 /
+    ||A A^T b||^2) A^T b evaluated with the library's own A and A^T."""
+    cfg = synth.CONFIGS["B256"]
+    g = ct.Geometry(**cfg)
+    lo, hi = synth.box_of(cfg)
+    x = torch.from_numpy(synth.voxelize(synth.random_ellipsoids(40, 1, lo, hi), cfg)).cuda()
+    b = ct.project(g, x)
+    x1, rep = ct.cgls(g, b, max_iter=1)
+    r = ct.backproject(g, b)
+    ar = ct.project(g, r)
+    a = float((r.double() ** 2).sum() / (ar.double() ** 2).sum())
+    assert rel(x1.cpu().numpy(), (a * r.double()).cpu().numpy()) < 1e-5
+    _, rep5 = ct.cgls(g, b, max_iter=5)
+    h = rep5.history
+    assert all(h[k + 1] <= h[k] * (1 + 1e-6) for k in range(len(h) - 1))
