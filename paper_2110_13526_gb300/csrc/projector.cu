@@ -16,6 +16,13 @@
 // the ray's mm-per-sigma factor gives exactly the Siddon line integral up to
 // FP32 rounding of the crossing positions.
 //
+// Precision.  All coordinates are relative to the volume centre (shifted by
+// integer plane counts, so floors stay exact), which keeps them below N/2 in
+// magnitude; the ray parameters come from a per-column table computed in FP64
+// on the host (ColParams), because a ray's in-plane direction depends on its
+// detector column only.  Anchoring rays at the source (hundreds of voxels
+// away) in FP32 instead costs an order of magnitude in accuracy.
+//
 // Coherence.  The 32 lanes of a warp are 32 adjacent detector columns u of
 // one detector row, and the slab loop is warp-synchronous (the loop index is
 // the same physical slab for all lanes), so at every step the lanes touch 32
