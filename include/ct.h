@@ -106,6 +106,25 @@ ct_status ct_backproject(const ct_geometry *g, const float *d_sino, float *d_vol
 ct_status ct_project_norm2(const ct_geometry *g, const float *d_vol, float *d_sino, float alpha,
                            float beta, double *d_norm2, void *stream);
 
+/* ct_project_norm2 without any device allocation.  The paper has no
+ * counterpart: this serves callers that cannot let a library allocate device
+ * memory once they run (a service that reserves HBM up front for its own
+ * pool, or a real-time pipeline whose latency budget has no room for an
+ * allocator call).  Same arguments and results as ct_project_norm2; the
+ * volume is read in place, and the FP64 partial sums live in a fixed 2 MiB
+ * device array that every GPU loading the library holds until exit.
+ * Limit: nviews * ceil(nu/32) * ceil(nv/8) <= 262144, else
+ * CT_ERR_INVALID_ARG with a message saying so.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  All calls share the array: calls that overlap on the
+ * GPU (other streams, other threads) race on it and must be serialised by the
+ * caller.  Each call overwrites what it reads, so the contents a previous
+ * call left behind never matter.  No cudaMalloc, cudaFree or allocating
+ * library routine is called. */
+ct_status ct_project_norm2_noalloc(const ct_geometry *g, const float *d_vol, float *d_sino,
+                                   float alpha, float beta, double *d_norm2, void *stream);
+
 /* Number of (ray, voxel) pairs with positive intersection length, i.e. the
  * nonzeros of A (the unit of the ray-voxel update rate).  *out is a HOST
  * int64.  Blocks until done. */

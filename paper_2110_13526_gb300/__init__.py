@@ -37,7 +37,8 @@ _STATUS = {0: "CT_OK", 1: "CT_ERR_INVALID_ARG", 2: "CT_ERR_CUDA", 3: "CT_ERR_OOM
 # Every symbol include/ct.h declares (checked by the CPU tests).
 EXPORTS = ("ct_geometry_create", "ct_geometry_destroy", "ct_geometry_sizes", "ct_project",
            "ct_backproject", "ct_project_norm2", "ct_count_nnz", "ct_precond_weights",
-           "ct_cgls", "ct_lsqr", "ct_last_error", "ct_version", "ct_kernel_launches")
+           "ct_cgls", "ct_lsqr", "ct_last_error", "ct_version", "ct_kernel_launches",
+           "ct_project_norm2_noalloc")
 
 
 class CTError(RuntimeError):
@@ -105,6 +106,8 @@ def lib():
             "ct_backproject": ([vp, vp, vp, ctypes.c_float, ctypes.c_float, vp], ctypes.c_int),
             "ct_project_norm2": ([vp, vp, vp, ctypes.c_float, ctypes.c_float, vp, vp],
                                  ctypes.c_int),
+            "ct_project_norm2_noalloc": ([vp, vp, vp, ctypes.c_float, ctypes.c_float, vp, vp],
+                                         ctypes.c_int),
             "ct_count_nnz": ([vp, P(ctypes.c_int64), vp], ctypes.c_int),
             "ct_precond_weights": ([vp, ctypes.c_int32, vp, vp, vp], ctypes.c_int),
             "ct_cgls": ([vp, vp, vp, P(SolverOpts), P(_Report), vp], ctypes.c_int),

@@ -139,6 +139,11 @@ ct_status launch_backward(const ProjGeom &pg, const float *e, const float *rho, 
 // Count the (ray, voxel) pairs with positive length into *d_count (int64).
 ct_status launch_count(const ProjGeom &pg, unsigned long long *d_count, cudaStream_t st);
 
+// p = alpha * A vol + beta * p reading vol in place (no transposed copy),
+// with forward_partials(pg) FP64 partial sums of p^2.
+ct_status launch_forward_direct(const ProjGeom &pg, const float *vol, float *p, float alpha,
+                                float beta, double *partials, cudaStream_t st);
+
 // ---- volume / sinogram kernels (vector_ops.cu) ------------------------------
 int vec_grid(int64_t n);  // CTAs of a streaming kernel (also its partial count)
 constexpr int kVecThreads = 256;

@@ -319,6 +319,50 @@ __global__ void __launch_bounds__(kTU *kTV) k_count(ProjGeom g,
     if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(count, (unsigned long long)(t + 0.5));
 }
 
+// Variant of k_forward with the FP64 norm partials that reads only the
+// caller's volume in its own layout [nz][ny][nx]: the walk of a ray that
+// advances along x yields offsets of the transposed layout [z][x][y], mapped
+// back here.  Those rays gather with a stride of nx, so this is slower, but it
+// needs no transposed copy.
+__global__ void __launch_bounds__(kTU *kTV) k_forward_direct(ProjGeom g,
+                                                             const float *__restrict__ vol,
+                                                             float *__restrict__ out, float alpha,
+                                                             float beta,
+                                                             double *__restrict__ partials) {
+    __shared__ double sh[32];
+    const int u = blockIdx.x * kTU + threadIdx.x;
+    const int v = blockIdx.y * kTV + threadIdx.y;
+    const int view = blockIdx.z;
+    const bool inb = (u < g.nu) && (v < g.nv);
+    Ray r;
+    const bool valid = inb && ray_setup(g, view, u, v, r);
+    const int nxy = g.nx * g.ny;
+    float acc = 0.f;
+    walk(r, valid, [&](int o, float l) {
+        if (l > 0.f) {
+            int oo = o;
+            if (r.transposed) {  // o = z nx ny + x ny + y  ->  z nx ny + y nx + x
+                const int z = o / nxy, rem = o - z * nxy;
+                const int x = rem / g.ny, y = rem - x * g.ny;
+                oo = z * nxy + y * g.nx + x;
+            }
+            acc = fmaf(l, __ldg(vol + oo), acc);
+        }
+    });
+    double sq = 0.0;
+    if (inb) {
+        const size_t idx = ((size_t)view * g.nv + v) * g.nu + u;
+        const float val = valid ? acc * r.lsig : 0.f;
+        float o = alpha * val;
+        if (beta != 0.f) o = fmaf(beta, out[idx], o);
+        out[idx] = o;
+        sq = (double)o * (double)o;
+    }
+    const double t = block_sum_d(sq, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        partials[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = t;
+}
+
 dim3 proj_grid(const ProjGeom &pg) {
     return dim3((unsigned)((pg.nu + kTU - 1) / kTU), (unsigned)((pg.nv + kTV - 1) / kTV),
                 (unsigned)pg.nviews);
@@ -374,6 +418,15 @@ ct_status launch_count(const ProjGeom &pg, unsigned long long *d_count, cudaStre
     CT_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st));
     if (empty(pg)) return CT_OK;
     k_count<<<proj_grid(pg), dim3(kTU, kTV), 0, st>>>(pg, d_count);
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+ct_status launch_forward_direct(const ProjGeom &pg, const float *vol, float *p, float alpha,
+                                float beta, double *partials, cudaStream_t st) {
+    if (empty(pg)) return CT_OK;
+    k_forward_direct<<<proj_grid(pg), dim3(kTU, kTV), 0, st>>>(pg, vol, p, alpha, beta,
+                                                               partials);
     CT_CHECK_LAUNCH();
     return CT_OK;
 }
