@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--iters", type=int, default=10, help="CGLS x updates per step")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="cgls", choices=["cgls", "ops"],
+                    help="ops: time ct_project and ct_backproject alone (profiling aid)")
     ap.add_argument("--cpu-sample-views", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -300,10 +302,49 @@ def run_ours(a):
     return 0
 
 
+def run_ops(a):
+    """A and A^T alone on the 256^3 workload: W warm-up pairs, then K timed
+    pairs, each launch bracketed by CUDA events on the current stream."""
+    import torch
+
+    import paper_2110_13526_gb300 as ct
+    import synth
+
+    torch.cuda.set_device(0)
+    cfg, g, x_true, b = make_problem(ct, torch, synth, torch.device("cuda", 0))
+    nnz = ct.count_nnz(g)
+    r = torch.empty(g.vol_shape, device="cuda")
+    p = torch.empty(g.sino_shape, device="cuda")
+    for _ in range(a.warmup):
+        ct.project(g, x_true, out=p)
+        ct.backproject(g, b, out=r)
+    stream = torch.cuda.current_stream()
+    tf, tb = [], []
+    for _ in range(a.steps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        ct.project(g, x_true, out=p)
+        e[1].record(stream)
+        ct.backproject(g, b, out=r)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        tf.append(e[0].elapsed_time(e[1]))
+        tb.append(e[1].elapsed_time(e[2]))
+    mf, mb = statistics.median(tf), statistics.median(tb)
+    print(json.dumps({"mode": "ops", "config": {"workload": WORKLOAD, "nnz": nnz},
+                      "ms_project": mf, "ms_backproject": mb,
+                      "gray_voxel_per_s": {"A": nnz / mf / 1e6, "AT": nnz / mb / 1e6},
+                      "note": "ct_project / ct_backproject calls, including the transpose "
+                              "and combine kernels around the projector kernel"}))
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.mode == "ops":
+        return run_ops(a)
     return run_ours(a)
 
 

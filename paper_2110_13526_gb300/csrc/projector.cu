@@ -164,43 +164,74 @@ __device__ __forceinline__ bool ray_setup(const ProjGeom &g, int view, int u, in
     return ray_clip(r, Ns, Na, Nb, ca, cb, wsrc, wpix, g.hz, g.hx, g.hy);
 }
 
-// Warp-synchronous slab walk.  fn(offset, w_length) is called for the up to
-// three segments of each slab (lengths may be 0; offsets always in range).
+// Warp-synchronous slab walk.  fn(offset, w_length) is called for the
+// segments of each slab; a length may be <= 0 (then fn must do nothing), and
+// the offset of every segment with positive length is inside the volume.
 // Must be called by all 32 lanes of the warp.
+//
+// Per lane the walk keeps integer voxel offsets and the w of the next plane
+// crossing of each lateral axis; a crossing updates the offset by the axis
+// stride and recomputes the next crossing directly from its plane index (the
+// same expression the box clip uses, so the exit face is never crossed).
+// The common slab has at most one lateral crossing and is handled without a
+// branch; a z crossing (rows of a warp cross the same z planes at nearly the
+// same slab, so the branch is warp-coherent) takes the general path.  Lanes
+// outside their own range, or without a ray, clamp their slab to an empty
+// interval.
 template <class Fn>
 __device__ __forceinline__ void walk(const Ray &r, bool valid, Fn &&fn) {
     const int kb = __reduce_min_sync(0xffffffffu, valid ? r.k_first : INT_MAX);
     const int ke = __reduce_max_sync(0xffffffffu, valid ? r.k_last : -1);
     if (kb > ke) return;
-    float w_lo = r.w_in;
-    float fi_lo = fminf(fmaxf(floorf(fmaf(w_lo, r.A, r.xi0)), r.fa_lo), r.fa_hi);
-    float fk_lo = fminf(fmaxf(floorf(fmaf(w_lo, r.C, r.ze0)), r.fb_lo), r.fb_hi);
+    const float w_in = valid ? r.w_in : 0.f, w_out = valid ? r.w_out : 0.f;
+    const float fi = fminf(fmaxf(floorf(fmaf(w_in, r.A, r.xi0)), r.fa_lo), r.fa_hi);
+    const float fk = fminf(fmaxf(floorf(fmaf(w_in, r.C, r.ze0)), r.fb_lo), r.fb_hi);
+    const bool neg_a = r.A < 0.f, neg_b = r.C < 0.f;
+    const float sa = neg_a ? -1.f : 1.f, sb = neg_b ? -1.f : 1.f;
+    const int da = neg_a ? -1 : 1, db = neg_b ? -r.bstride : r.bstride;
+    float px = neg_a ? fi : fi + 1.f;  // next lateral planes in the direction of travel
+    float pz = neg_b ? fk : fk + 1.f;
+    float w_nx = (valid && r.A != 0.f) ? (px - r.xi0) * r.invA : INFINITY;
+    float w_nz = (valid && r.C != 0.f) ? (pz - r.ze0) * r.invC : INFINITY;
+    int off = valid ? r.soff0 + kb * r.sstep + (int)fi + (int)fk * r.bstride : 0;
+    float wk = (float)(kb - r.cs);
+    float w_lo = fminf(fmaxf(wk, w_in), w_out);
     for (int k = kb; k <= ke; ++k) {
-        if (valid && k >= r.k_first && k <= r.k_last) {
-            const float w_hi = fminf((float)(k + 1 - r.cs), r.w_out);
-            const float fi_n = fminf(fmaxf(floorf(fmaf(w_hi, r.A, r.xi0)), r.fa_lo), r.fa_hi);
-            const float fk_n = fminf(fmaxf(floorf(fmaf(w_hi, r.C, r.ze0)), r.fb_lo), r.fb_hi);
-            // at most one crossing per lateral axis inside a slab
-            const float fi_hi = fminf(fmaxf(fi_n, fi_lo - 1.f), fi_lo + 1.f);
-            const float fk_hi = fminf(fmaxf(fk_n, fk_lo - 1.f), fk_lo + 1.f);
-            float sx = (fi_hi != fi_lo) ? (fmaxf(fi_lo, fi_hi) - r.xi0) * r.invA : w_hi;
-            float sz = (fk_hi != fk_lo) ? (fmaxf(fk_lo, fk_hi) - r.ze0) * r.invC : w_hi;
-            sx = fminf(fmaxf(sx, w_lo), w_hi);
-            sz = fminf(fmaxf(sz, w_lo), w_hi);
-            const float s1 = fminf(sx, sz), s2 = fmaxf(sx, sz);
-            const int soff = r.soff0 + k * r.sstep;
-            const int ilo = (int)fi_lo, ihi = (int)fi_hi;
-            const int blo = (int)fk_lo * r.bstride, bhi = (int)fk_hi * r.bstride;
-            const int o1 = soff + ilo + blo;
-            const int o2 = (sx <= sz) ? soff + ihi + blo : soff + ilo + bhi;
-            const int o3 = soff + ihi + bhi;
-            fn(o1, s1 - w_lo);
-            fn(o2, s2 - s1);
-            fn(o3, w_hi - s2);
-            w_lo = w_hi;
-            fi_lo = fi_n;
-            fk_lo = fk_n;
+        wk += 1.f;
+        const float w_hi = fminf(fmaxf(wk, w_in), w_out);
+        if (!(w_nz < w_hi)) {
+            const float sx = fminf(w_nx, w_hi);
+            fn(off, sx - w_lo);
+            if (w_nx < w_hi) {
+                off += da;
+                px += sa;
+                w_nx = (px - r.xi0) * r.invA;
+            }
+            fn(off, w_hi - sx);
+        } else {
+            float t = w_lo;
+#pragma unroll
+            for (int ev = 0; ev < 2; ++ev) {
+                const float e = fminf(w_nx, w_nz);
+                if (e < w_hi) {
+                    fn(off, e - t);
+                    t = fmaxf(t, e);
+                    if (w_nx == e) {
+                        off += da;
+                        px += sa;
+                        w_nx = (px - r.xi0) * r.invA;
+                    }
+                    if (w_nz == e) {
+                        off += db;
+                        pz += sb;
+                        w_nz = (pz - r.ze0) * r.invC;
+                    }
+                }
+            }
+            fn(off, w_hi - t);
         }
+        w_lo = w_hi;
+        off += r.sstep;
     }
 }
 
