@@ -169,15 +169,16 @@ __device__ __forceinline__ bool ray_setup(const ProjGeom &g, int view, int u, in
 // the offset of every segment with positive length is inside the volume.
 // Must be called by all 32 lanes of the warp.
 //
-// Per lane the walk keeps integer voxel offsets and the w of the next plane
-// crossing of each lateral axis; a crossing updates the offset by the axis
+// Per lane the walk keeps an integer voxel offset and, per lateral axis, the
+// w of the next plane crossing; a crossing moves the offset by the axis
 // stride and recomputes the next crossing directly from its plane index (the
-// same expression the box clip uses, so the exit face is never crossed).
-// The common slab has at most one lateral crossing and is handled without a
-// branch; a z crossing (rows of a warp cross the same z planes at nearly the
-// same slab, so the branch is warp-coherent) takes the general path.  Lanes
-// outside their own range, or without a ray, clamp their slab to an empty
-// interval.
+// same expression the box clip uses, so a lane never steps through the exit
+// face).  All per-lane decisions are selects, so lanes never diverge.  A slab
+// in which no lane of the warp crosses a z plane (the common case: rows of a
+// warp cross the same z planes at nearly the same slab) has at most one
+// lateral crossing per lane and takes the short path; otherwise the whole
+// warp takes the general path with up to three segments.  Lanes outside
+// their own range, or without a ray, clamp their slab to an empty interval.
 template <class Fn>
 __device__ __forceinline__ void walk(const Ray &r, bool valid, Fn &&fn) {
     const int kb = __reduce_min_sync(0xffffffffu, valid ? r.k_first : INT_MAX);
@@ -189,49 +190,41 @@ __device__ __forceinline__ void walk(const Ray &r, bool valid, Fn &&fn) {
     const bool neg_a = r.A < 0.f, neg_b = r.C < 0.f;
     const float sa = neg_a ? -1.f : 1.f, sb = neg_b ? -1.f : 1.f;
     const int da = neg_a ? -1 : 1, db = neg_b ? -r.bstride : r.bstride;
+    const float xi0 = r.xi0, ze0 = r.ze0, invA = r.invA, invC = r.invC;
     float px = neg_a ? fi : fi + 1.f;  // next lateral planes in the direction of travel
     float pz = neg_b ? fk : fk + 1.f;
-    float w_nx = (valid && r.A != 0.f) ? (px - r.xi0) * r.invA : INFINITY;
-    float w_nz = (valid && r.C != 0.f) ? (pz - r.ze0) * r.invC : INFINITY;
+    float w_nx = (valid && r.A != 0.f) ? (px - xi0) * invA : INFINITY;
+    float w_nz = (valid && r.C != 0.f) ? (pz - ze0) * invC : INFINITY;
     int off = valid ? r.soff0 + kb * r.sstep + (int)fi + (int)fk * r.bstride : 0;
+    const int sstep = r.sstep;
     float wk = (float)(kb - r.cs);
     float w_lo = fminf(fmaxf(wk, w_in), w_out);
     for (int k = kb; k <= ke; ++k) {
         wk += 1.f;
         const float w_hi = fminf(fmaxf(wk, w_in), w_out);
-        if (!(w_nz < w_hi)) {
-            const float sx = fminf(w_nx, w_hi);
+        const bool cx = w_nx < w_hi;
+        const float sx = fminf(w_nx, w_hi);
+        const int dax = cx ? da : 0;
+        if (!__any_sync(0xffffffffu, w_nz < w_hi)) {
             fn(off, sx - w_lo);
-            if (w_nx < w_hi) {
-                off += da;
-                px += sa;
-                w_nx = (px - r.xi0) * r.invA;
-            }
+            off += dax;
             fn(off, w_hi - sx);
         } else {
-            float t = w_lo;
-#pragma unroll
-            for (int ev = 0; ev < 2; ++ev) {
-                const float e = fminf(w_nx, w_nz);
-                if (e < w_hi) {
-                    fn(off, e - t);
-                    t = fmaxf(t, e);
-                    if (w_nx == e) {
-                        off += da;
-                        px += sa;
-                        w_nx = (px - r.xi0) * r.invA;
-                    }
-                    if (w_nz == e) {
-                        off += db;
-                        pz += sb;
-                        w_nz = (pz - r.ze0) * r.invC;
-                    }
-                }
-            }
-            fn(off, w_hi - t);
+            const bool cz = w_nz < w_hi;
+            const float sz = fminf(w_nz, w_hi);
+            const float s1 = fminf(sx, sz), s2 = fmaxf(sx, sz);
+            const int dbz = cz ? db : 0;
+            fn(off, s1 - w_lo);
+            fn(off + (sx <= sz ? dax : dbz), s2 - s1);
+            off += dax + dbz;
+            fn(off, w_hi - s2);
+            pz = cz ? pz + sb : pz;
+            w_nz = cz ? (pz - ze0) * invC : w_nz;
         }
+        px = cx ? px + sa : px;
+        w_nx = cx ? (px - xi0) * invA : w_nx;
         w_lo = w_hi;
-        off += r.sstep;
+        off += sstep;
     }
 }
 
@@ -277,7 +270,9 @@ __global__ void __launch_bounds__(kTU *kTV) k_forward(ProjGeom g, const float *_
     const float *base = r.transposed ? vol_t : vol;
     float acc = 0.f;
     walk(r, valid, [&](int o, float l) {
-        if (l > 0.f) acc = fmaf(l, UNIT_VOL ? 1.f : __ldg(base + o), acc);
+        float val = 0.f;
+        if (l > 0.f) val = UNIT_VOL ? 1.f : __ldg(base + o);
+        acc = fmaf(fmaxf(l, 0.f), val, acc);
     });
     float alpha, beta;
     coef_of(c, alpha, beta);
