@@ -228,6 +228,16 @@ __device__ __forceinline__ void walk(const Ray &r, bool valid, Fn &&fn) {
     }
 }
 
+// Predicated float reduction into global memory (no branch around it): the
+// lanes of a warp reach it together whether or not they have a segment.
+__device__ __forceinline__ void red_add_if(float *addr, float val, bool pred) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p red.global.add.f32 [%0], %1;\n\t}"
+        :
+        : "l"(addr), "f"(val), "r"((int)pred)
+        : "memory");
+}
+
 __device__ __forceinline__ double block_sum_d(double x, double *sh) {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     const int lane = threadIdx.x & 31;
@@ -255,7 +265,7 @@ __device__ __forceinline__ void coef_of(const Coef &c, float &alpha, float &beta
 
 // p = alpha * rho o (A vol) + beta * p.  vol == NULL means the all-ones volume.
 template <bool HAS_RHO, bool NORM, bool UNIT_VOL>
-__global__ void __launch_bounds__(kTU *kTV) k_forward(ProjGeom g, const float *__restrict__ vol,
+__global__ void __launch_bounds__(kTU *kTV, 6) k_forward(ProjGeom g, const float *__restrict__ vol,
                                                       const float *__restrict__ vol_t,
                                                       float *__restrict__ out,
                                                       const float *__restrict__ rho, Coef c,
@@ -296,7 +306,7 @@ __global__ void __launch_bounds__(kTU *kTV) k_forward(ProjGeom g, const float *_
 // acc += alpha * (A o A ... )^T: POWER 1 scatters length * w, POWER 2 scatters
 // length^2 * w, w = alpha * rho_i * e_i (e == NULL means e = 1).
 template <bool HAS_RHO, int POWER>
-__global__ void __launch_bounds__(kTU *kTV) k_backward(ProjGeom g, const float *__restrict__ e,
+__global__ void __launch_bounds__(kTU *kTV, 6) k_backward(ProjGeom g, const float *__restrict__ e,
                                                        const float *__restrict__ rho, Coef c,
                                                        float *__restrict__ acc,
                                                        float *__restrict__ acc_t) {
@@ -319,14 +329,8 @@ __global__ void __launch_bounds__(kTU *kTV) k_backward(ProjGeom g, const float *
     float *base = r.transposed ? acc_t : acc;
     const float ls = r.lsig;
     walk(r, valid, [&](int o, float l) {
-        if (l > 0.f) {
-            if (POWER == 1) {
-                atomicAdd(base + o, w * l);
-            } else {
-                const float lm = l * ls;
-                atomicAdd(base + o, w * lm * lm);
-            }
-        }
+        const float lm = l * ls;
+        red_add_if(base + o, POWER == 1 ? w * l : w * lm * lm, l > 0.f);
     });
 }
 
