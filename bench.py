@@ -55,6 +55,23 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_max(x: float, device=None) -> float:
+    """Max of a per-rank scalar over all ranks (the job is as slow as its
+    slowest rank); the value itself when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Units processed by all ranks together per second of the slowest rank."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 def measured_peak_gbs():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -243,11 +260,8 @@ def run_ours(a):
     ev1.record(stream)
     torch.cuda.synchronize()
     launches = (ct.kernel_launches() - l0) // max(a.steps, 1)
-    ms = ev0.elapsed_time(ev1)
+    ms = reduce_max(ev0.elapsed_time(ev1), dev)
     if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     clk = clocks.stop()
 
@@ -275,7 +289,7 @@ def run_ours(a):
             "kernel": kname, "peak_source": peak_kind,
             "ms_per_launch": t_dom * 1e3,
             "algorithmic_bytes_per_launch": by_dom}
-    value = world * a.steps * K / (ms * 1e-3)
+    value = whole_job_rate(a.steps * K, world, ms)
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
