@@ -32,6 +32,7 @@
 // [z][x][y] (y fastest).  Either way the warp's gathers (and the
 // backprojector's atomics) fall on one or two 128-byte lines.
 #include <climits>
+#include <type_traits>
 
 #include "ct_internal.h"
 
@@ -164,9 +165,11 @@ __device__ __forceinline__ bool ray_setup(const ProjGeom &g, int view, int u, in
     return ray_clip(r, Ns, Na, Nb, ca, cb, wsrc, wpix, g.hz, g.hx, g.hy);
 }
 
-// Warp-synchronous slab walk.  fn(offset, w_length) is called for the
-// segments of each slab; a length may be <= 0 (then fn must do nothing), and
-// the offset of every segment with positive length is inside the volume.
+// Warp-synchronous slab walk.  fn(offset, w_length, p) is called for the
+// segments of each slab.  p says whether the segment may be accessed: when p
+// is set the offset is inside the volume (the length may still be zero or a
+// rounding-size negative, which contributes nothing); when p is clear fn
+// must not touch memory.
 // Must be called by all 32 lanes of the warp.
 //
 // Per lane the walk keeps an integer voxel offset and, per lateral axis, the
@@ -178,12 +181,23 @@ __device__ __forceinline__ bool ray_setup(const ProjGeom &g, int view, int u, in
 // warp cross the same z planes at nearly the same slab) has at most one
 // lateral crossing per lane and takes the short path; otherwise the whole
 // warp takes the general path with up to three segments.  Lanes outside
-// their own range, or without a ray, clamp their slab to an empty interval.
+// their own range, or without a ray, clamp their slab to an empty interval;
+// the interior slabs, which every lane of a full warp covers entirely, skip
+// that clamp.
 template <class Fn>
 __device__ __forceinline__ void walk(const Ray &r, bool valid, Fn &&fn) {
-    const int kb = __reduce_min_sync(0xffffffffu, valid ? r.k_first : INT_MAX);
-    const int ke = __reduce_max_sync(0xffffffffu, valid ? r.k_last : -1);
+    const unsigned full = 0xffffffffu;
+    const int kb = __reduce_min_sync(full, valid ? r.k_first : INT_MAX);
+    const int ke = __reduce_max_sync(full, valid ? r.k_last : -1);
     if (kb > ke) return;
+    // interior slabs [k_mid0, k_mid1]: after every lane's entry slab and
+    // before every lane's exit slab, only when all 32 lanes hold a ray
+    int k_mid0 = __reduce_max_sync(full, valid ? r.k_first : INT_MAX) + 1;
+    int k_mid1 = __reduce_min_sync(full, valid ? r.k_last : -1) - 1;
+    if (!__all_sync(full, valid) || k_mid0 > k_mid1) {
+        k_mid0 = ke + 1;
+        k_mid1 = ke;
+    }
     const float w_in = valid ? r.w_in : 0.f, w_out = valid ? r.w_out : 0.f;
     const float fi = fminf(fmaxf(floorf(fmaf(w_in, r.A, r.xi0)), r.fa_lo), r.fa_hi);
     const float fk = fminf(fmaxf(floorf(fmaf(w_in, r.C, r.ze0)), r.fb_lo), r.fb_hi);
@@ -199,33 +213,46 @@ __device__ __forceinline__ void walk(const Ray &r, bool valid, Fn &&fn) {
     const int sstep = r.sstep;
     float wk = (float)(kb - r.cs);
     float w_lo = fminf(fmaxf(wk, w_in), w_out);
-    for (int k = kb; k <= ke; ++k) {
+    auto slab = [&](auto clamp) {
         wk += 1.f;
-        const float w_hi = fminf(fmaxf(wk, w_in), w_out);
+        const float w_hi = decltype(clamp)::value ? fminf(fmaxf(wk, w_in), w_out) : wk;
         const bool cx = w_nx < w_hi;
         const float sx = fminf(w_nx, w_hi);
         const int dax = cx ? da : 0;
-        if (!__any_sync(0xffffffffu, w_nz < w_hi)) {
-            fn(off, sx - w_lo);
+        if (!__any_sync(full, w_nz < w_hi)) {
+            // interior slabs: every lane is inside its range, so its first
+            // segment is always a real voxel; the second exists iff cx
+            fn(off, sx - w_lo, decltype(clamp)::value ? (sx - w_lo > 0.f) : true);
             off += dax;
-            fn(off, w_hi - sx);
+            fn(off, w_hi - sx, cx);
         } else {
             const bool cz = w_nz < w_hi;
             const float sz = fminf(w_nz, w_hi);
             const float s1 = fminf(sx, sz), s2 = fmaxf(sx, sz);
             const int dbz = cz ? db : 0;
-            fn(off, s1 - w_lo);
-            fn(off + (sx <= sz ? dax : dbz), s2 - s1);
+            fn(off, s1 - w_lo, s1 - w_lo > 0.f);
+            fn(off + (sx <= sz ? dax : dbz), s2 - s1, s2 - s1 > 0.f);
             off += dax + dbz;
-            fn(off, w_hi - s2);
-            pz = cz ? pz + sb : pz;
-            w_nz = cz ? (pz - ze0) * invC : w_nz;
+            fn(off, w_hi - s2, w_hi - s2 > 0.f);
+            if (cz) {
+                pz += sb;
+                w_nz = (pz - ze0) * invC;
+            }
         }
-        px = cx ? px + sa : px;
-        w_nx = cx ? (px - xi0) * invA : w_nx;
+        if (cx) {
+            px += sa;
+            w_nx = (px - xi0) * invA;
+        }
         w_lo = w_hi;
         off += sstep;
-    }
+    };
+    using clamped = std::integral_constant<bool, true>;
+    using interior = std::integral_constant<bool, false>;
+    int k = kb;
+    for (; k < k_mid0; ++k) slab(clamped{});
+#pragma unroll 2
+    for (; k <= k_mid1; ++k) slab(interior{});
+    for (; k <= ke; ++k) slab(clamped{});
 }
 
 // Predicated float reduction into global memory (no branch around it): the
@@ -234,8 +261,7 @@ __device__ __forceinline__ void red_add_if(float *addr, float val, bool pred) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p red.global.add.f32 [%0], %1;\n\t}"
         :
-        : "l"(addr), "f"(val), "r"((int)pred)
-        : "memory");
+        : "l"(addr), "f"(val), "r"((int)pred));
 }
 
 __device__ __forceinline__ double block_sum_d(double x, double *sh) {
@@ -279,10 +305,10 @@ __global__ void __launch_bounds__(kTU *kTV, 6) k_forward(ProjGeom g, const float
     const bool valid = inb && ray_setup(g, view, u, v, r);
     const float *base = r.transposed ? vol_t : vol;
     float acc = 0.f;
-    walk(r, valid, [&](int o, float l) {
+    walk(r, valid, [&](int o, float l, bool p) {
         float val = 0.f;
-        if (l > 0.f) val = UNIT_VOL ? 1.f : __ldg(base + o);
-        acc = fmaf(fmaxf(l, 0.f), val, acc);
+        if (p) val = UNIT_VOL ? 1.f : __ldg(base + o);
+        acc = fmaf(l, val, acc);
     });
     float alpha, beta;
     coef_of(c, alpha, beta);
@@ -328,9 +354,9 @@ __global__ void __launch_bounds__(kTU *kTV, 6) k_backward(ProjGeom g, const floa
     valid = valid && (w != 0.f);
     float *base = r.transposed ? acc_t : acc;
     const float ls = r.lsig;
-    walk(r, valid, [&](int o, float l) {
+    walk(r, valid, [&](int o, float l, bool p) {
         const float lm = l * ls;
-        red_add_if(base + o, POWER == 1 ? w * l : w * lm * lm, l > 0.f);
+        red_add_if(base + o, POWER == 1 ? w * l : w * lm * lm, p);
     });
 }
 
@@ -344,7 +370,7 @@ __global__ void __launch_bounds__(kTU *kTV) k_count(ProjGeom g,
     Ray r;
     const bool valid = inb && ray_setup(g, view, u, v, r);
     int n = 0;
-    walk(r, valid, [&](int, float l) { n += (l > 0.f) ? 1 : 0; });
+    walk(r, valid, [&](int, float l, bool p) { n += (p && l > 0.f) ? 1 : 0; });
     double t = block_sum_d((double)n, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(count, (unsigned long long)(t + 0.5));
 }
@@ -368,8 +394,8 @@ __global__ void __launch_bounds__(kTU *kTV) k_forward_direct(ProjGeom g,
     const bool valid = inb && ray_setup(g, view, u, v, r);
     const int nxy = g.nx * g.ny;
     float acc = 0.f;
-    walk(r, valid, [&](int o, float l) {
-        if (l > 0.f) {
+    walk(r, valid, [&](int o, float l, bool p) {
+        if (p && l > 0.f) {
             int oo = o;
             if (r.transposed) {  // o = z nx ny + x ny + y  ->  z nx ny + y nx + x
                 const int z = o / nxy, rem = o - z * nxy;
