@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="cgls", choices=["cgls", "ops"],
                     help="ops: time ct_project and ct_backproject alone (profiling aid)")
+    ap.add_argument("--workload", default="B256", choices=["B256", "P512"],
+                    help="ops mode only: 256^3 (default) or the 512^3, 720-view workload")
     ap.add_argument("--cpu-sample-views", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -151,11 +153,15 @@ def traffic_for(kernel: str):
     return None
 
 
-def make_problem(ct, torch, synth, dev):
-    cfg = synth.CONFIGS["B256"]
+PHANTOM_SEED = {"B256": 1, "P512": 2}
+
+
+def make_problem(ct, torch, synth, dev, workload="B256"):
+    cfg = synth.CONFIGS[workload]
     g = ct.Geometry(**cfg)
     lo, hi = synth.box_of(cfg)
-    x_true = torch.from_numpy(synth.voxelize(synth.random_ellipsoids(40, 1, lo, hi), cfg)).to(dev)
+    x_true = torch.from_numpy(synth.voxelize(synth.random_ellipsoids(40, PHANTOM_SEED[workload],
+                                                                     lo, hi), cfg)).to(dev)
     b = ct.project(g, x_true)
     torch.cuda.synchronize()
     return cfg, g, x_true, b
@@ -325,7 +331,7 @@ def run_ops(a):
     import synth
 
     torch.cuda.set_device(0)
-    cfg, g, x_true, b = make_problem(ct, torch, synth, torch.device("cuda", 0))
+    cfg, g, x_true, b = make_problem(ct, torch, synth, torch.device("cuda", 0), a.workload)
     nnz = ct.count_nnz(g)
     r = torch.empty(g.vol_shape, device="cuda")
     p = torch.empty(g.sino_shape, device="cuda")
@@ -345,7 +351,7 @@ def run_ops(a):
         tf.append(e[0].elapsed_time(e[1]))
         tb.append(e[1].elapsed_time(e[2]))
     mf, mb = statistics.median(tf), statistics.median(tb)
-    print(json.dumps({"mode": "ops", "config": {"workload": WORKLOAD, "nnz": nnz},
+    print(json.dumps({"mode": "ops", "config": {"workload": a.workload, "nnz": nnz},
                       "ms_project": mf, "ms_backproject": mb,
                       "gray_voxel_per_s": {"A": nnz / mf / 1e6, "AT": nnz / mb / 1e6},
                       "note": "ct_project / ct_backproject calls, including the transpose "
