@@ -40,8 +40,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--iters", type=int, default=10, help="CGLS x updates per step")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="cgls", choices=["cgls", "ops"],
-                    help="ops: time ct_project and ct_backproject alone (profiling aid)")
+    ap.add_argument("--mode", default="cgls", choices=["cgls", "ops", "serve"],
+                    help="ops: time ct_project and ct_backproject alone (profiling aid); "
+                         "serve: the continuous-batching request stream alone")
+    ap.add_argument("--requests", type=int, default=128, help="serve mode: requests")
+    ap.add_argument("--rate", type=float, default=20.0, help="serve mode: arrivals per second")
+    ap.add_argument("--slots", type=int, default=8, help="serve mode: concurrent jobs")
+    ap.add_argument("--serve-requests", type=int, default=32,
+                    help="default mode: requests of the served-latency block (0 = skip)")
     ap.add_argument("--workload", default="B256", choices=["B256", "P512"],
                     help="ops mode only: 256^3 (default) or the 512^3, 720-view workload")
     ap.add_argument("--cpu-sample-views", type=int, default=8)
@@ -311,6 +317,8 @@ def run_ours(a):
                     "h2d_bytes_per_step": 4 * n_rays, "d2h_bytes_per_step": 4 * n_vox},
             "gpu_launches": int(launches) * a.steps,
             "clocks": clk}
+    if a.serve_requests > 0:
+        line["served"] = serve_stream(a.serve_requests, 20.0, 8)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cb = cpu_baseline(cfg, a.cpu_sample_views, K)
         cb.pop("seconds", None)
@@ -359,12 +367,59 @@ def run_ops(a):
     return 0
 
 
+def serve_stream(n_requests: int, rate: float, slots: int, budget_gb: float = 150.0):
+    """Serving workload: Poisson arrivals (seed 3), volumes 64..256^3, 60..360
+    views, detector scaled to magnification 1.6, CGLS or LSQR to relative
+    discrepancy 1e-3 or 50 updates; continuous batching over ``slots``
+    streams under an HBM budget.  Returns the stats dict of the run."""
+    import torch
+
+    import paper_2110_13526_gb300 as ct
+    import synth
+    from paper_2110_13526_gb300.serving import Request, Server
+
+    stream = synth.serving_stream(n_requests, rate, 3)
+    reqs, geoms = [], {}
+    for s in stream:
+        cfg = synth.serving_geometry(s["n"], s["views"])
+        key = (s["n"], s["views"])
+        if key not in geoms:
+            geoms[key] = ct.Geometry(**cfg)
+        x = torch.from_numpy(synth.serving_phantom(s["n"], s["phantom_seed"])).cuda()
+        b = ct.project(geoms[key], x)
+        reqs.append(Request(s["rid"], cfg, b, s["solver"], s["arrival"], max_iter=50,
+                            err_tol=1e-3))
+    torch.cuda.synchronize()
+    stats = Server(slots=slots, hbm_budget_bytes=budget_gb * 1e9).run(reqs)
+    iters = stats.iterations
+    return {"requests": len(reqs), "rate_per_s": rate, "slots": slots,
+            "p50_s": stats.p50, "p99_s": stats.p99, "wall_s": stats.wall_s,
+            "requests_per_s": len(reqs) / stats.wall_s, "solver_iters_per_s": iters / stats.wall_s,
+            "max_concurrent": stats.max_concurrent,
+            "max_gb_in_use": stats.max_bytes_in_use / 1e9,
+            "mean_iterations": iters / max(len(reqs), 1),
+            "workload": "Poisson arrivals (seed 3); n in {64,128,192,256}, views in "
+                        "{60,120,180,360}, detector 1.5n x 1.125n of 1.6 mm; CGLS/LSQR to "
+                        "1e-3 or 50 updates; 8-ellipsoid phantoms; FP32"}
+
+
+def run_serve(a):
+    import torch
+    torch.cuda.set_device(0)
+    out = {"mode": "serve"}
+    out.update(serve_stream(a.requests, a.rate, a.slots))
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
     if a.mode == "ops":
         return run_ops(a)
+    if a.mode == "serve":
+        return run_serve(a)
     return run_ours(a)
 
 

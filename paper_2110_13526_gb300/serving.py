@@ -1,0 +1,190 @@
+"""Continuous-batching reconstruction server over the C ABI.
+
+Requests (a sinogram, its scan geometry, CGLS or LSQR, a discrepancy
+tolerance and an iteration cap) arrive over time.  The server admits a
+request as soon as a slot is free and its device footprint fits the HBM
+budget, and runs it on its own CUDA stream from a worker thread; the ctypes
+calls release the GIL, so the jobs of all occupied slots overlap on the GPU.
+Requests that arrive while others run wait in FIFO order and are admitted as
+slots and memory free up (no head-of-line skipping, so service order is
+arrival order).  Every solve is the unchanged library call (ct_cgls /
+ct_lsqr): a result does not depend on which other jobs share the GPU, up to
+the float-atomic summation order of the backprojection.
+
+Latency of a request = completion time - arrival time.
+"""
+from __future__ import annotations
+
+import threading
+import time
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Tuple
+
+import numpy as np
+import torch
+
+from . import Geometry, cgls, lsqr
+
+
+@dataclass
+class Request:
+    rid: int
+    geometry: dict                 # keyword arguments of Geometry
+    b: torch.Tensor                # sinogram on the device
+    solver: str = "cgls"           # "cgls" or "lsqr"
+    arrival: float = 0.0           # seconds after the start of the run
+    max_iter: int = 50
+    err_tol: float = 1e-3
+
+
+@dataclass
+class Result:
+    rid: int
+    x: torch.Tensor
+    iterations: int
+    rel_discrepancy: float
+    arrival: float
+    start: float
+    end: float
+
+    @property
+    def latency(self) -> float:
+        return self.end - self.arrival
+
+
+def footprint_bytes(geometry: dict, solver: str) -> int:
+    """Device bytes a solve holds: the library's workspace plus x.
+
+    CGLS: x, z, g, transposed scratch (4 volumes) + e, p (2 sinograms);
+    LSQR: x, v, w, g, transposed scratch (5 volumes) + u (1 sinogram);
+    plus per-view and per-column constants and FP64 partial sums."""
+    n = geometry["nx"] * geometry["ny"] * geometry["nz"]
+    m = geometry["nviews"] * geometry["nu"] * geometry["nv"]
+    vols, sinos = (4, 2) if solver == "cgls" else (5, 1)
+    cols = geometry["nviews"] * geometry["nu"] * 36 + geometry["nviews"] * 48
+    partials = 8 * (m // 256 + n // 1024 + 4096)
+    return 4 * (vols * n + sinos * m) + cols + partials
+
+
+@dataclass
+class ServeStats:
+    results: List[Result]
+    wall_s: float
+    max_concurrent: int
+    max_bytes_in_use: int
+    iterations: int = 0
+    p50: float = 0.0
+    p99: float = 0.0
+    extra: dict = field(default_factory=dict)
+
+
+class Server:
+    def __init__(self, slots: int = 8, hbm_budget_bytes: float = 150e9, device=None):
+        if slots < 1:
+            raise ValueError("slots must be >= 1")
+        self.slots = slots
+        self.budget = int(hbm_budget_bytes)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        self._geoms: Dict[Tuple, Geometry] = {}
+        self._lock = threading.Lock()
+
+    def geometry(self, cfg: dict) -> Geometry:
+        key = tuple(sorted(cfg.items()))
+        with self._lock:
+            g = self._geoms.get(key)
+            if g is None:
+                with torch.cuda.device(self.device):
+                    g = Geometry(**cfg)
+                self._geoms[key] = g
+            return g
+
+    def run(self, requests: List[Request]) -> ServeStats:
+        reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        for r in reqs:
+            fp = footprint_bytes(r.geometry, r.solver)
+            if fp > self.budget:
+                raise ValueError("request %d needs %d bytes, budget %d" % (r.rid, fp, self.budget))
+            self.geometry(r.geometry)          # geometries are built before the clock starts
+        torch.cuda.synchronize(self.device)
+        cv = threading.Condition()
+        state = {"free_slots": self.slots, "bytes": 0, "running": 0, "max_running": 0,
+                 "max_bytes": 0, "errors": []}
+        results: List[Result] = []
+        streams = [torch.cuda.Stream(device=self.device) for _ in range(self.slots)]
+        free_streams = list(range(self.slots))
+        t0 = time.perf_counter()
+
+        def worker(req: Request, si: int, fp: int, t_start: float):
+            try:
+                torch.cuda.set_device(self.device)
+                s = streams[si]
+                g = self.geometry(req.geometry)
+                fn = cgls if req.solver == "cgls" else lsqr
+                with torch.cuda.stream(s):
+                    x, rep = fn(g, req.b, max_iter=req.max_iter, err_tol=req.err_tol, stream=s)
+                    s.synchronize()
+                t_end = time.perf_counter() - t0
+                res = Result(req.rid, x, rep.iterations, rep.nb / rep.nb0 if rep.nb0 else 0.0,
+                             req.arrival, t_start, t_end)
+            except Exception as e:  # reported after the run
+                res = None
+                with cv:
+                    state["errors"].append((req.rid, repr(e)))
+            with cv:
+                if res is not None:
+                    results.append(res)
+                state["free_slots"] += 1
+                state["bytes"] -= fp
+                state["running"] -= 1
+                free_streams.append(si)
+                cv.notify_all()
+
+        threads = []
+        pending: List[Request] = []
+        i = 0
+        with cv:
+            while i < len(reqs) or pending or state["running"] > 0:
+                now = time.perf_counter() - t0
+                while i < len(reqs) and reqs[i].arrival <= now:
+                    pending.append(reqs[i])
+                    i += 1
+                # admit in arrival order while a slot and the budget allow
+                while pending and state["free_slots"] > 0:
+                    fp = footprint_bytes(pending[0].geometry, pending[0].solver)
+                    if state["bytes"] + fp > self.budget:
+                        break
+                    req = pending.pop(0)
+                    si = free_streams.pop(0)
+                    state["free_slots"] -= 1
+                    state["bytes"] += fp
+                    state["running"] += 1
+                    state["max_running"] = max(state["max_running"], state["running"])
+                    state["max_bytes"] = max(state["max_bytes"], state["bytes"])
+                    t = threading.Thread(target=worker, args=(req, si, fp, now), daemon=True)
+                    threads.append(t)
+                    t.start()
+                if i >= len(reqs) and not pending and state["running"] == 0:
+                    break
+                wait = None
+                if i < len(reqs):
+                    wait = max(0.0, reqs[i].arrival - (time.perf_counter() - t0))
+                cv.wait(timeout=wait if wait is not None else 0.5)
+        for t in threads:
+            t.join()
+        wall = time.perf_counter() - t0
+        if state["errors"]:
+            raise RuntimeError("requests failed: %s" % state["errors"])
+        results.sort(key=lambda r: r.rid)
+        lat = np.array([r.latency for r in results])
+        return ServeStats(results, wall, state["max_running"], state["max_bytes"],
+                          iterations=sum(r.iterations for r in results),
+                          p50=float(np.percentile(lat, 50)) if len(lat) else 0.0,
+                          p99=float(np.percentile(lat, 99)) if len(lat) else 0.0)
+
+
+def serving_geometry(n: int, views: int) -> dict:
+    """Scan of an n^3 volume of 1 mm voxels with a detector scaled to the
+    magnification 1200/750 = 1.6: 1.6 mm pixels, 1.5 n x 1.125 n of them."""
+    return dict(nx=n, ny=n, nz=n, vx=1.0, vy=1.0, vz=1.0, nu=int(1.5 * n), nv=int(1.125 * n),
+                du=1.6, dv=1.6, sid=750.0, sdd=1200.0, nviews=views)

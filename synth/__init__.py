@@ -156,6 +156,38 @@ def gaussian_noise(b: np.ndarray, frac: float, seed: int) -> np.ndarray:
     return (np.asarray(b, dtype=np.float64) + sigma * rng.standard_normal(b.shape))
 
 
+def serving_geometry(n: int, views: int) -> dict:
+    """Serving scan of an n^3 volume of 1 mm voxels, detector scaled to the
+    magnification 1.6: pixels of 1.6 mm, 1.5 n x 1.125 n of them."""
+    return dict(nx=n, ny=n, nz=n, vx=1.0, vy=1.0, vz=1.0, nu=int(1.5 * n), nv=int(1.125 * n),
+                du=1.6, dv=1.6, sid=750.0, sdd=1200.0, nviews=views)
+
+
+def serving_stream(n_requests: int = 128, rate: float = 20.0, seed: int = 3,
+                   sizes=(64, 128, 192, 256), views=(60, 120, 180, 360)):
+    """Poisson request stream: per request, in this order from
+    default_rng(seed): exponential inter-arrival time (mean 1/rate), volume
+    size, view count, solver (CGLS or LSQR), phantom seed."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for rid in range(n_requests):
+        t += rng.exponential(1.0 / rate)
+        n = int(rng.choice(sizes))
+        v = int(rng.choice(views))
+        solver = str(rng.choice(["cgls", "lsqr"]))
+        out.append(dict(rid=rid, arrival=t, n=n, views=v, solver=solver,
+                        phantom_seed=int(rng.integers(1 << 31))))
+    return out
+
+
+def serving_phantom(n: int, seed: int, n_ellipsoids: int = 8) -> np.ndarray:
+    """Random-ellipsoid phantom for an n^3 serving volume (semi-axes scaled by n/256)."""
+    cfg = serving_geometry(n, 1)
+    lo, hi = box_of(cfg)
+    return voxelize(random_ellipsoids(n_ellipsoids, seed, lo, hi, axis_scale=n / 256.0), cfg)
+
+
 def random_field(shape, seed: int, dtype=np.float32) -> np.ndarray:
     """Signed standard-normal test vector (negative values are allowed, Discussion)."""
     return np.random.default_rng(seed).standard_normal(shape).astype(dtype)
