@@ -81,6 +81,20 @@ ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out);
 /* Free the geometry (NULL is a no-op).  No call using it may be in flight. */
 void ct_geometry_destroy(ct_geometry *g);
 
+/* Deterministic accumulation (default off).  When on, every backprojection
+ * with this geometry (ct_backproject, the solvers, the preconditioner
+ * weights) sums its contributions as 64-bit fixed-point integers: each value
+ * is scaled by a power of two chosen from max |input| and a bound on the rays
+ * through one voxel, rounded to an integer and added with integer atomics.
+ * Integer addition does not depend on order, so results are bitwise
+ * reproducible from run to run and independent of other work sharing the
+ * GPU; each contribution is rounded to a multiple of at most 2^-61 times the
+ * bound on a voxel's sum.  Costs 16 bytes per voxel of workspace and a
+ * slower backprojection.  The forward projection, the vector updates and
+ * the FP64 reductions are deterministic in both modes.  Change the mode only
+ * while no call on this geometry is in flight. */
+ct_status ct_geometry_set_deterministic(ct_geometry *g, int32_t on);
+
 /* Sizes of the geometry: voxels (n = nx ny nz) and rays (m = nviews nv nu). */
 ct_status ct_geometry_sizes(const ct_geometry *g, int64_t *n_vox, int64_t *n_rays);
 

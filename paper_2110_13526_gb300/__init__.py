@@ -38,7 +38,7 @@ _STATUS = {0: "CT_OK", 1: "CT_ERR_INVALID_ARG", 2: "CT_ERR_CUDA", 3: "CT_ERR_OOM
 EXPORTS = ("ct_geometry_create", "ct_geometry_destroy", "ct_geometry_sizes", "ct_project",
            "ct_backproject", "ct_project_norm2", "ct_count_nnz", "ct_precond_weights",
            "ct_cgls", "ct_lsqr", "ct_last_error", "ct_version", "ct_kernel_launches",
-           "ct_project_norm2_noalloc")
+           "ct_project_norm2_noalloc", "ct_geometry_set_deterministic")
 
 
 class CTError(RuntimeError):
@@ -115,6 +115,7 @@ def lib():
             "ct_last_error": ([], ctypes.c_char_p),
             "ct_version": ([], ctypes.c_char_p),
             "ct_kernel_launches": ([], ctypes.c_int64),
+            "ct_geometry_set_deterministic": ([vp, ctypes.c_int32], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -147,7 +148,8 @@ class Geometry:
 
     def __init__(self, nx, ny, nz, vx, vy, vz, nu, nv, du, dv, sid, sdd, nviews,
                  ox=0.0, oy=0.0, oz=0.0, det_off_u=0.0, det_off_v=0.0,
-                 angles: Optional[Sequence[float]] = None, device=None):
+                 angles: Optional[Sequence[float]] = None, device=None,
+                 deterministic: bool = False):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.nu, self.nv, self.nviews = int(nu), int(nv), int(nviews)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
@@ -163,6 +165,9 @@ class Geometry:
         with torch.cuda.device(self.device):
             _check(lib().ct_geometry_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
+        self.deterministic = bool(deterministic)
+        if deterministic:
+            _check(lib().ct_geometry_set_deterministic(h, 1))
 
     @property
     def handle(self):

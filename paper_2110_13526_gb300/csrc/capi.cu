@@ -64,31 +64,68 @@ DeviceGuard::~DeviceGuard() {
     if (changed_) cudaSetDevice(prev_);
 }
 
+ct_status back_scratch_alloc(const ct_geometry *g, Workspace &ws, float *acc_t, BackScratch *s) {
+    *s = BackScratch{};
+    if (!g->deterministic) {
+        if (acc_t) {
+            s->acc_t = acc_t;
+            return CT_OK;
+        }
+        return ws.alloc(&s->acc_t, (size_t)g->nvox);
+    }
+    CT_TRY(ws.alloc(&s->q, 2 * (size_t)g->nvox));
+    CT_TRY(ws.alloc(&s->part, (size_t)vec_grid(std::max<int64_t>(g->nrays, 1))));
+    CT_TRY(ws.alloc(&s->scale, 1));
+    CT_TRY(ws.alloc(&s->inv, 1));
+    return CT_OK;
+}
+
+double det_value_bound(const ct_geometry *g, int power) {
+    // a segment contributes at most |alpha e rho| * hdiag^power (hdiag: voxel
+    // diagonal, the longest chord), and at most det_bound / 2 rays cross a voxel
+    const double hdiag = std::sqrt(g->desc.vx * g->desc.vx + g->desc.vy * g->desc.vy +
+                                   g->desc.vz * g->desc.vz);
+    return g->det_bound * (power == 2 ? hdiag * hdiag : hdiag);
+}
+
+ct_status backproject_impl(const ct_geometry *g, const BackScratch &s, const float *e,
+                           const float *rho, Coef c, float *out, float beta, int power,
+                           const float *w, double *partials, cudaStream_t st) {
+    const ProjGeom &pg = g->pg;
+    const int64_t n = g->nvox;
+    if (!g->deterministic) {
+        CT_TRY(launch_scale(out, n, beta, st));
+        CT_CUDA_TRY(cudaMemsetAsync(s.acc_t, 0, (size_t)n * sizeof(float), st));
+        CT_TRY(launch_backward(pg, e, rho, c, out, s.acc_t, power, st));
+        return launch_combine(pg, out, s.acc_t, w, partials, st);
+    }
+    CT_CUDA_TRY(cudaMemsetAsync(s.q, 0, 2 * (size_t)n * sizeof(long long), st));
+    CT_TRY(launch_det_scale(e, rho, g->nrays, det_value_bound(g, power), c, s.part, s.scale,
+                            s.inv, st));
+    CT_TRY(launch_backward_det(pg, e, rho, c, s.q, s.q + n, power, s.scale, st));
+    return launch_combine_det(pg, out, beta, s.q, s.q + n, s.inv, w, partials, st);
+}
+
 ct_status precond_weights_impl(const ct_geometry *g, int kind, float *vol_w, float *sino_w,
                                Workspace &ws, cudaStream_t st) {
     const ProjGeom &pg = g->pg;
-    float *part = nullptr, *acc_t = nullptr;
+    float *part = nullptr;
     const int64_t np = std::max<int64_t>(vec_grid(g->nvox), vec_grid(g->nrays));
     CT_TRY(ws.alloc(&part, (size_t)np));
+    BackScratch bs;
+    CT_TRY(back_scratch_alloc(g, ws, nullptr, &bs));
+    Coef one;
     if (kind == CT_PRECOND_JACOBI) {
         // D = diag(A^T A) = (A o A)^T 1: squared lengths scattered from unit rays
-        CT_TRY(ws.alloc(&acc_t, (size_t)g->nvox));
-        CT_CUDA_TRY(cudaMemsetAsync(vol_w, 0, (size_t)g->nvox * sizeof(float), st));
-        CT_CUDA_TRY(cudaMemsetAsync(acc_t, 0, (size_t)g->nvox * sizeof(float), st));
-        CT_TRY(launch_backward(pg, nullptr, nullptr, Coef{}, vol_w, acc_t, 2, st));
-        CT_TRY(launch_combine(pg, vol_w, acc_t, nullptr, nullptr, st));
+        CT_TRY(backproject_impl(g, bs, nullptr, nullptr, one, vol_w, 0.f, 2, nullptr, nullptr, st));
         CT_TRY(launch_inv_sqrt_guarded(vol_w, g->nvox, 1e-6f, part, st));
         return CT_OK;
     }
     if (kind == CT_PRECOND_ROWCOL) {
         // R = A 1 (row sums) and C = A^T 1 (column sums)
-        CT_TRY(launch_forward(pg, nullptr, nullptr, sino_w, nullptr, Coef{}, nullptr, st));
+        CT_TRY(launch_forward(pg, nullptr, nullptr, sino_w, nullptr, one, nullptr, st));
         CT_TRY(launch_inv_sqrt_guarded(sino_w, g->nrays, 1e-6f, part, st));
-        CT_TRY(ws.alloc(&acc_t, (size_t)g->nvox));
-        CT_CUDA_TRY(cudaMemsetAsync(vol_w, 0, (size_t)g->nvox * sizeof(float), st));
-        CT_CUDA_TRY(cudaMemsetAsync(acc_t, 0, (size_t)g->nvox * sizeof(float), st));
-        CT_TRY(launch_backward(pg, nullptr, nullptr, Coef{}, vol_w, acc_t, 1, st));
-        CT_TRY(launch_combine(pg, vol_w, acc_t, nullptr, nullptr, st));
+        CT_TRY(backproject_impl(g, bs, nullptr, nullptr, one, vol_w, 0.f, 1, nullptr, nullptr, st));
         CT_TRY(launch_inv_sqrt_guarded(vol_w, g->nvox, 1e-6f, part, st));
         return CT_OK;
     }
@@ -242,6 +279,28 @@ ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out) {
     g->nvox = nvox;
     g->nrays = (int64_t)d.nviews * d.nv * d.nu;
     g->d_views = nullptr;
+    g->deterministic = 0;
+    {
+        // rays through one voxel in all views: the voxel's detector footprint
+        // at the largest magnification (volume corner nearest the source),
+        // plus a margin of two pixels per axis; never more than all rays
+        double rmax = 0.0;
+        for (int cx = 0; cx < 2; ++cx)
+            for (int cy = 0; cy < 2; ++cy) {
+                const double x = (cx ? 0.5 : -0.5) * d.nx * d.vx + d.off_x;
+                const double y = (cy ? 0.5 : -0.5) * d.ny * d.vy + d.off_y;
+                rmax = std::max(rmax, std::sqrt(x * x + y * y));
+            }
+        const double hd = std::sqrt(d.vx * d.vx + d.vy * d.vy + d.vz * d.vz);
+        double rays = (double)g->nrays;
+        if (d.sid > rmax) {
+            const double mag = d.sdd / (d.sid - rmax);
+            const double per_view =
+                (std::ceil(hd * mag / d.du) + 2.0) * (std::ceil(hd * mag / d.dv) + 2.0);
+            rays = std::min(rays, (double)d.nviews * per_view);
+        }
+        g->det_bound = 2.0 * std::max(rays, 1.0);
+    }
     cudaError_t e = cudaGetDevice(&g->device);
     if (e != cudaSuccess) {
         delete g;
@@ -365,16 +424,20 @@ ct_status ct_backproject(const ct_geometry *g, const float *d_sino, float *d_vol
     DeviceGuard dg(g->device);
     CT_TRY(dg.status());
     cudaStream_t st = (cudaStream_t)stream;
-    CT_TRY(launch_scale(d_vol, g->nvox, beta, st));
-    if (g->nrays == 0 || alpha == 0.f) return CT_OK;
+    if (g->nrays == 0 || alpha == 0.f) return launch_scale(d_vol, g->nvox, beta, st);
     Workspace ws(st);
-    float *acc_t = nullptr;
-    CT_TRY(ws.alloc(&acc_t, (size_t)g->nvox));
-    CT_CUDA_TRY(cudaMemsetAsync(acc_t, 0, (size_t)g->nvox * sizeof(float), st));
+    BackScratch bs;
+    CT_TRY(back_scratch_alloc(g, ws, nullptr, &bs));
     Coef c;
     c.alpha = alpha;
-    CT_TRY(launch_backward(g->pg, d_sino, nullptr, c, d_vol, acc_t, 1, st));
-    return launch_combine(g->pg, d_vol, acc_t, nullptr, nullptr, st);
+    return backproject_impl(g, bs, d_sino, nullptr, c, d_vol, beta, 1, nullptr, nullptr, st);
+}
+
+ct_status ct_geometry_set_deterministic(ct_geometry *g, int32_t on) {
+    clear_error();
+    CT_TRY(check_geom(g));
+    g->deterministic = on ? 1 : 0;
+    return CT_OK;
 }
 
 ct_status ct_count_nnz(const ct_geometry *g, int64_t *out, void *stream) {

@@ -60,6 +60,8 @@ struct ct_geometry {
     ct::ViewConst *d_views;      // device
     void *d_cols;                // device: col_a, col_b, col_flags in one allocation
     ct::ProjGeom pg;
+    int deterministic;           // backprojections accumulate in int64 fixed point
+    double det_bound;            // bound on (rays through one voxel) * lsig_max
 };
 
 namespace ct {
@@ -139,6 +141,20 @@ ct_status launch_backward(const ProjGeom &pg, const float *e, const float *rho, 
 // Count the (ray, voxel) pairs with positive length into *d_count (int64).
 ct_status launch_count(const ProjGeom &pg, unsigned long long *d_count, cudaStream_t st);
 
+// The same scatter accumulating rint(value * scale) in int64 (scale =
+// det_scale[0], a power of two): order-independent, hence deterministic.
+ct_status launch_backward_det(const ProjGeom &pg, const float *e, const float *rho, Coef c,
+                              long long *acc, long long *acc_t, int power,
+                              const float *det_scale, cudaStream_t st);
+// scale[0] = 2^k (float) and inv[0] = 2^-k (double) with k the largest integer
+// such that |alpha| max|e rho| bound 2^k <= 2^62.  part: vec_grid(m) floats.
+ct_status launch_det_scale(const float *e, const float *rho, int64_t m, double bound, Coef c,
+                           float *part, float *scale, double *inv, cudaStream_t st);
+// out = beta out + (acc + transpose(acc_t)) inv; optional partials of (w out)^2.
+ct_status launch_combine_det(const ProjGeom &pg, float *out, float beta, const long long *acc,
+                             const long long *acc_t, const double *inv, const float *w,
+                             double *partials, cudaStream_t st);
+
 // p = alpha * A vol + beta * p reading vol in place (no transposed copy),
 // with forward_partials(pg) FP64 partial sums of p^2.
 ct_status launch_forward_direct(const ProjGeom &pg, const float *vol, float *p, float alpha,
@@ -171,6 +187,30 @@ ct_status launch_norm2(const float *v, const float *w, int64_t n, double *partia
 namespace ct {
 // v = 1/sqrt(v) where v > rel * max(v), else 0.  part: vec_grid(n) floats.
 ct_status launch_inv_sqrt_guarded(float *v, int64_t n, float rel, float *part, cudaStream_t st);
+
+// Device scratch of backprojections: a float accumulator in the transposed
+// layout, or, for a deterministic geometry, two int64 accumulators and the
+// fixed-point scale.  Allocate once per solve and reuse.
+struct BackScratch {
+    float *acc_t = nullptr;      // nvox floats
+    long long *q = nullptr;      // 2 nvox int64: main layout, then transposed
+    float *part = nullptr;       // vec_grid(nrays) floats
+    float *scale = nullptr;      // 1 float
+    double *inv = nullptr;       // 1 double
+};
+// acc_t may be a caller buffer of nvox floats (reused between calls).
+ct_status back_scratch_alloc(const ct_geometry *g, Workspace &ws, float *acc_t, BackScratch *s);
+// Bound on one voxel's backprojected sum per unit |alpha e rho| (power 1:
+// lengths, power 2: squared lengths), for the fixed-point scale.
+double det_value_bound(const ct_geometry *g, int power);
+
+// out = beta * out + alpha * A^T (rho o e) (POWER 2: squared lengths), in the
+// geometry's accumulation mode (float atomics, or int64 fixed point when the
+// geometry is deterministic); partials (may be NULL) receive per-CTA sums of
+// (w o out)^2, transpose_grid_count(pg) of them.
+ct_status backproject_impl(const ct_geometry *g, const BackScratch &s, const float *e,
+                           const float *rho, Coef c, float *out, float beta, int power,
+                           const float *w, double *partials, cudaStream_t st);
 
 // Preconditioner weights into caller buffers (see ct_precond_weights).
 ct_status precond_weights_impl(const ct_geometry *g, int kind, float *vol_w, float *sino_w,

@@ -264,6 +264,14 @@ __device__ __forceinline__ void red_add_if(float *addr, float val, bool pred) {
         : "l"(addr), "f"(val), "r"((int)pred));
 }
 
+// Predicated 64-bit integer reduction into global memory.
+__device__ __forceinline__ void red_add_u64_if(unsigned long long *addr, long long val, bool pred) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p red.global.add.u64 [%0], %1;\n\t}"
+        :
+        : "l"(addr), "l"(val), "r"((int)pred));
+}
+
 __device__ __forceinline__ double block_sum_d(double x, double *sh) {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     const int lane = threadIdx.x & 31;
@@ -330,12 +338,16 @@ __global__ void __launch_bounds__(kTU *kTV, 6) k_forward(ProjGeom g, const float
 }
 
 // acc += alpha * (A o A ... )^T: POWER 1 scatters length * w, POWER 2 scatters
-// length^2 * w, w = alpha * rho_i * e_i (e == NULL means e = 1).
-template <bool HAS_RHO, int POWER>
+// length^2 * w, w = alpha * rho_i * e_i (e == NULL means e = 1).  DET
+// accumulates q = rint(value * scale) in 64-bit integers (scale = a power of
+// two read from det_scale[0]): integer addition is associative, so the sums
+// do not depend on the order in which rays arrive.
+template <bool HAS_RHO, int POWER, bool DET>
 __global__ void __launch_bounds__(kTU *kTV, 6) k_backward(ProjGeom g, const float *__restrict__ e,
                                                        const float *__restrict__ rho, Coef c,
-                                                       float *__restrict__ acc,
-                                                       float *__restrict__ acc_t) {
+                                                       void *__restrict__ acc,
+                                                       void *__restrict__ acc_t,
+                                                       const float *__restrict__ det_scale) {
     const int u = blockIdx.x * kTU + threadIdx.x;
     const int v = blockIdx.y * kTV + threadIdx.y;
     const int view = blockIdx.z;
@@ -352,12 +364,23 @@ __global__ void __launch_bounds__(kTU *kTV, 6) k_backward(ProjGeom g, const floa
         if (POWER == 1) w *= r.lsig;
     }
     valid = valid && (w != 0.f);
-    float *base = r.transposed ? acc_t : acc;
     const float ls = r.lsig;
-    walk(r, valid, [&](int o, float l, bool p) {
-        const float lm = l * ls;
-        red_add_if(base + o, POWER == 1 ? w * l : w * lm * lm, p);
-    });
+    if constexpr (DET) {
+        const float scale = __ldg(det_scale);
+        unsigned long long *base =
+            static_cast<unsigned long long *>(r.transposed ? acc_t : acc);
+        walk(r, valid, [&](int o, float l, bool p) {
+            const float lm = l * ls;
+            const float val = POWER == 1 ? w * l : w * lm * lm;
+            red_add_u64_if(base + o, __float2ll_rn(val * scale), p);
+        });
+    } else {
+        float *base = static_cast<float *>(r.transposed ? acc_t : acc);
+        walk(r, valid, [&](int o, float l, bool p) {
+            const float lm = l * ls;
+            red_add_if(base + o, POWER == 1 ? w * l : w * lm * lm, p);
+        });
+    }
 }
 
 __global__ void __launch_bounds__(kTU *kTV) k_count(ProjGeom g,
@@ -460,11 +483,28 @@ ct_status launch_backward(const ProjGeom &pg, const float *e, const float *rho, 
     dim3 gr = proj_grid(pg), bl(kTU, kTV);
     const bool hr = (rho != nullptr);
     if (power == 2) {
-        if (hr) k_backward<true, 2><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t);
-        else    k_backward<false, 2><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t);
+        if (hr) k_backward<true, 2, false><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t, nullptr);
+        else    k_backward<false, 2, false><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t, nullptr);
     } else {
-        if (hr) k_backward<true, 1><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t);
-        else    k_backward<false, 1><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t);
+        if (hr) k_backward<true, 1, false><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t, nullptr);
+        else    k_backward<false, 1, false><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t, nullptr);
+    }
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+ct_status launch_backward_det(const ProjGeom &pg, const float *e, const float *rho, Coef c,
+                              long long *acc, long long *acc_t, int power,
+                              const float *det_scale, cudaStream_t st) {
+    if (empty(pg)) return CT_OK;
+    dim3 gr = proj_grid(pg), bl(kTU, kTV);
+    const bool hr = (rho != nullptr);
+    if (power == 2) {
+        if (hr) k_backward<true, 2, true><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t, det_scale);
+        else    k_backward<false, 2, true><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t, det_scale);
+    } else {
+        if (hr) k_backward<true, 1, true><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t, det_scale);
+        else    k_backward<false, 1, true><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t, det_scale);
     }
     CT_CHECK_LAUNCH();
     return CT_OK;

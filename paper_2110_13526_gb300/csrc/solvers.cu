@@ -343,6 +343,7 @@ struct Solve {
     OpTimer tm;
     int n_fwd = 0, n_back = 0;
     float *T = nullptr;           // transposed scratch volume (input copy / accumulator)
+    BackScratch bs;               // backprojection scratch (T, or int64 accumulators)
     double *part = nullptr;       // FP64 partial sums
     float *W = nullptr, *L = nullptr;
     int64_t n, m;
@@ -351,6 +352,7 @@ struct Solve {
 
     ct_status init(int precond) {
         CT_TRY(ws.alloc(&T, (size_t)n));
+        CT_TRY(back_scratch_alloc(g, ws, T, &bs));
         int64_t np = std::max<int64_t>(forward_partials(pg), transpose_grid_count(pg));
         np = std::max<int64_t>(np, std::max(vec_grid(n), vec_grid(m)));
         CT_TRY(ws.alloc(&part, (size_t)np));
@@ -371,15 +373,26 @@ struct Solve {
         ++n_fwd;
         return CT_OK;
     }
-    // gout = c * A^T (L o e), then partials of (Wg)^2 if requested.
+    // gout = c * A^T (L o e), then partials of (Wg)^2 if requested; the
+    // geometry decides float-atomic or fixed-point (deterministic) sums.
     ct_status back(const float *e, float *gout, Coef c, const float *wnorm, double *partials) {
-        CT_CUDA_TRY(cudaMemsetAsync(gout, 0, (size_t)n * sizeof(float), st));
-        CT_CUDA_TRY(cudaMemsetAsync(T, 0, (size_t)n * sizeof(float), st));
+        if (!g->deterministic) {
+            CT_CUDA_TRY(cudaMemsetAsync(gout, 0, (size_t)n * sizeof(float), st));
+            CT_CUDA_TRY(cudaMemsetAsync(T, 0, (size_t)n * sizeof(float), st));
+            CT_TRY(tm.mark(tm.back));
+            CT_TRY(launch_backward(pg, e, L, c, gout, T, 1, st));
+            CT_TRY(tm.mark(tm.back));
+            ++n_back;
+            return launch_combine(pg, gout, T, wnorm, partials, st);
+        }
+        CT_CUDA_TRY(cudaMemsetAsync(bs.q, 0, 2 * (size_t)n * sizeof(long long), st));
+        CT_TRY(launch_det_scale(e, L, m, det_value_bound(g, 1), c, bs.part, bs.scale, bs.inv,
+                                st));
         CT_TRY(tm.mark(tm.back));
-        CT_TRY(launch_backward(pg, e, L, c, gout, T, 1, st));
+        CT_TRY(launch_backward_det(pg, e, L, c, bs.q, bs.q + n, 1, bs.scale, st));
         CT_TRY(tm.mark(tm.back));
         ++n_back;
-        return launch_combine(pg, gout, T, wnorm, partials, st);
+        return launch_combine_det(pg, gout, 0.f, bs.q, bs.q + n, bs.inv, wnorm, partials, st);
     }
     // Is x0 nonzero?  (One reduction and one host read.)
     ct_status nonzero(const float *x, bool *out) {

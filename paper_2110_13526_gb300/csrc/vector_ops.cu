@@ -230,4 +230,108 @@ ct_status launch_inv_sqrt_guarded(float *v, int64_t n, float rel, float *part, c
     return CT_OK;
 }
 
+// ---- deterministic (fixed-point) backprojection support ---------------------
+namespace {
+
+// Block maxima of |e_i rho_i| (e or rho NULL: 1).
+__global__ void k_absmax_partials(const float *__restrict__ e, const float *__restrict__ rho,
+                                  int64_t n, float *__restrict__ part) {
+    __shared__ float sh[32];
+    float m = 0.f;
+    if (!e && !rho) {
+        m = n > 0 ? 1.f : 0.f;
+    } else {
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x)
+            m = fmaxf(m, fabsf((e ? e[i] : 1.f) * (rho ? rho[i] : 1.f)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_down_sync(0xffffffffu, t, o));
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
+    }
+}
+
+// scale = 2^k with k the largest integer such that |alpha| max|e rho| * bound
+// * 2^k <= 2^62 (clamped to [-126, 126]); out[0] = scale (float), and the
+// exact inverse 2^-k goes to inv[0] (double).
+__global__ void k_det_scale(const float *__restrict__ part, int np, double bound, Coef c,
+                            float *__restrict__ out, double *__restrict__ inv) {
+    float m = 0.f;
+    for (int i = 0; i < np; ++i) m = fmaxf(m, part[i]);
+    const double alpha = c.dev ? fabs(c.dev[0]) : fabs((double)c.alpha);
+    const double top = (double)m * alpha * bound;
+    int k = 126;
+    if (top > 0.0 && top < 1e300) {
+        int ex = 0;
+        (void)frexp(top, &ex);   // top = f 2^ex, f in [0.5, 1)
+        k = 62 - ex;
+        k = k > 126 ? 126 : (k < -126 ? -126 : k);
+    }
+    out[0] = __int_as_float((k + 127) << 23);
+    inv[0] = __longlong_as_double((long long)(1023 - k) << 52);
+}
+
+// out = beta * out + (acc + transpose(acc_t)) * inv; optional partials of
+// (w out)^2 per CTA.  acc: [nz][ny][nx], acc_t: [nz][nx][ny] (int64).
+__global__ void __launch_bounds__(256) k_combine_det(int nx, int ny, float *__restrict__ out,
+                                                     float beta, const long long *__restrict__ acc,
+                                                     const long long *__restrict__ acc_t,
+                                                     const double *__restrict__ inv,
+                                                     const float *__restrict__ w,
+                                                     double *__restrict__ partials) {
+    __shared__ long long tile[kTile][kTile + 1];
+    __shared__ double sh[32];
+    const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
+    const size_t zoff = (size_t)blockIdx.z * nx * ny;
+    for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
+        const int x = x0 + j, y = y0 + threadIdx.x;
+        if (x < nx && y < ny) tile[j][threadIdx.x] = acc_t[zoff + (size_t)x * ny + y];
+    }
+    __syncthreads();
+    const double s = inv[0];
+    double sq = 0.0;
+    for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
+        const int y = y0 + j, x = x0 + threadIdx.x;
+        if (x < nx && y < ny) {
+            const size_t i = zoff + (size_t)y * nx + x;
+            const long long q = acc[i] + tile[threadIdx.x][j];
+            float val = (float)((double)q * s);
+            if (beta != 0.f) val = fmaf(beta, out[i], val);
+            out[i] = val;
+            const double qq = w ? (double)(w[i] * val) : (double)val;
+            sq = fma(qq, qq, sq);
+        }
+    }
+    if (partials) {
+        const double t = block_sum_1d(sq, sh);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            partials[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = t;
+    }
+}
+
+}  // namespace
+
+ct_status launch_det_scale(const float *e, const float *rho, int64_t m, double bound, Coef c,
+                           float *part, float *scale, double *inv, cudaStream_t st) {
+    const int gb = vec_grid(m);
+    k_absmax_partials<<<gb, kVecThreads, 0, st>>>(e, rho, m, part);
+    CT_CHECK_LAUNCH();
+    k_det_scale<<<1, 1, 0, st>>>(part, gb, bound, c, scale, inv);
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+ct_status launch_combine_det(const ProjGeom &pg, float *out, float beta, const long long *acc,
+                             const long long *acc_t, const double *inv, const float *w,
+                             double *partials, cudaStream_t st) {
+    dim3 gr((pg.nx + kTile - 1) / kTile, (pg.ny + kTile - 1) / kTile, pg.nz), bl(kTile, 8);
+    k_combine_det<<<gr, bl, 0, st>>>(pg.nx, pg.ny, out, beta, acc, acc_t, inv, w, partials);
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
 }  // namespace ct

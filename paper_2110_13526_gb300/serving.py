@@ -79,10 +79,12 @@ class ServeStats:
 
 
 class Server:
-    def __init__(self, slots: int = 8, hbm_budget_bytes: float = 150e9, device=None):
+    def __init__(self, slots: int = 8, hbm_budget_bytes: float = 150e9, device=None,
+                 deterministic: bool = False):
         if slots < 1:
             raise ValueError("slots must be >= 1")
         self.slots = slots
+        self.deterministic = deterministic
         self.budget = int(hbm_budget_bytes)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
                                    else torch.device(device).index or 0)
@@ -95,7 +97,7 @@ class Server:
             g = self._geoms.get(key)
             if g is None:
                 with torch.cuda.device(self.device):
-                    g = Geometry(**cfg)
+                    g = Geometry(**cfg, deterministic=self.deterministic)
                 self._geoms[key] = g
             return g
 

@@ -65,3 +65,18 @@ def test_hbm_budget_limits_admission(ct):
     assert stats.max_bytes_in_use <= 1.5 * biggest
     with pytest.raises(ValueError):
         Server(slots=2, hbm_budget_bytes=0.5 * biggest).run(reqs)
+
+
+def test_deterministic_results_bitwise_equal_alone_and_in_the_mix(ct):
+    """With fixed-point backprojection every solve is bitwise reproducible, so
+    a result computed among concurrent jobs equals the one computed alone."""
+    from paper_2110_13526_gb300.serving import Server
+    reqs = make_requests(ct, n_req=8, rate=200.0, seed=13)
+    stats = Server(slots=4, deterministic=True).run(reqs)
+    assert stats.max_concurrent >= 2
+    for req, res in zip(reqs, stats.results):
+        g = ct.Geometry(**req.geometry, deterministic=True)
+        fn = ct.cgls if req.solver == "cgls" else ct.lsqr
+        x_alone, rep = fn(g, req.b, max_iter=req.max_iter, err_tol=req.err_tol)
+        assert res.iterations == rep.iterations
+        assert torch.equal(res.x, x_alone), req.rid

@@ -178,3 +178,17 @@ def test_b256_first_iterate_property(ct):
     _, rep5 = ct.cgls(g, b, max_iter=5)
     h = rep5.history
     assert all(h[k + 1] <= h[k] * (1 + 1e-6) for k in range(len(h) - 1))
+
+
+@pytest.mark.parametrize("precond", ["none", "rowcol"])
+def test_deterministic_solvers_bitwise_and_parity(ct, small, precond):
+    cfg, og, _, b = small
+    g = ct.Geometry(**cfg, deterministic=True)
+    bd = torch.from_numpy(b).cuda()
+    for solver, osolver in ((ct.cgls, ocgls), (ct.lsqr, olsqr)):
+        x1, r1 = solver(g, bd, max_iter=12, precond=precond)
+        x2, r2 = solver(g, bd, max_iter=12, precond=precond)
+        assert torch.equal(x1, x2) and r1.history == r2.history
+        left, right = (None, None) if precond == "none" else rowcol_weights(og)
+        ref = osolver(oracle.Operator(og), b.astype(np.float64), K=12, left=left, right=right)
+        assert rel(x1.cpu().numpy(), ref.x) < TOL_X
