@@ -54,6 +54,12 @@ typedef enum {
     CT_ERR_INTERNAL = 5     /* a device-side consistency check failed       */
 } ct_status;
 
+/* Storage element type of a volume or sinogram.  Arithmetic is FP32 along
+ * each ray (and FP64 for the Krylov scalars) whatever the storage; BF16/FP16
+ * only change what is read and what is rounded on store (the Discussion notes
+ * that much of the double precision could give way to lower precision). */
+typedef enum { CT_F32 = 0, CT_BF16 = 1, CT_F16 = 2 } ct_dtype;
+
 /* Opaque geometry: per-view ray constants on the device, library-owned. */
 typedef struct ct_geometry ct_geometry;
 
@@ -111,6 +117,17 @@ ct_status ct_project(const ct_geometry *g, const float *d_vol, float *d_sino, fl
  * atomics, so the last bits may differ between runs. */
 ct_status ct_backproject(const ct_geometry *g, const float *d_sino, float *d_vol, float alpha,
                          float beta, void *stream);
+
+/* ct_project / ct_backproject with typed storage: d_vol holds vol_dtype and
+ * d_sino sino_dtype elements (ct_dtype).  Values are read and converted to
+ * FP32, every ray or voxel sum is accumulated in FP32, and the result is
+ * rounded to the output type on store (round to nearest even).  Same layouts,
+ * alpha/beta semantics and errors as the FP32 calls. */
+ct_status ct_project_ex(const ct_geometry *g, const void *d_vol, int32_t vol_dtype, void *d_sino,
+                        int32_t sino_dtype, float alpha, float beta, void *stream);
+ct_status ct_backproject_ex(const ct_geometry *g, const void *d_sino, int32_t sino_dtype,
+                            void *d_vol, int32_t vol_dtype, float alpha, float beta,
+                            void *stream);
 
 /* ct_project plus the squared norm of the result (Algorithm 1 step
  * NP2 = ||p_b||_2^2), accumulated in FP64 in a fixed order (deterministic):
@@ -172,6 +189,9 @@ typedef struct {
     double tikhonov_lambda;  /* must be 0 (Tikhonov regularisation: not built) */
     int32_t recompute_every; /* k > 0: e_b = b - A x every k updates (CGLS)    */
     int32_t timing;          /* nonzero: time every A and A^T with CUDA events */
+    int32_t storage;         /* ct_dtype of the Krylov vectors d_x, e_b, p_b
+                                (CGLS; LSQR needs CT_F32).  x and the
+                                backprojection sums stay FP32. */
 } ct_solver_opts;
 
 /* Solver report, filled on return.  history_nb (HOST, caller-owned, may be

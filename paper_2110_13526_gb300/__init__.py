@@ -38,7 +38,8 @@ _STATUS = {0: "CT_OK", 1: "CT_ERR_INVALID_ARG", 2: "CT_ERR_CUDA", 3: "CT_ERR_OOM
 EXPORTS = ("ct_geometry_create", "ct_geometry_destroy", "ct_geometry_sizes", "ct_project",
            "ct_backproject", "ct_project_norm2", "ct_count_nnz", "ct_precond_weights",
            "ct_cgls", "ct_lsqr", "ct_last_error", "ct_version", "ct_kernel_launches",
-           "ct_project_norm2_noalloc", "ct_geometry_set_deterministic")
+           "ct_project_norm2_noalloc", "ct_geometry_set_deterministic", "ct_project_ex",
+           "ct_backproject_ex")
 
 
 class CTError(RuntimeError):
@@ -63,7 +64,8 @@ class _Desc(ctypes.Structure):
 class SolverOpts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("err_tol", ctypes.c_double),
                 ("precond", ctypes.c_int32), ("tikhonov_lambda", ctypes.c_double),
-                ("recompute_every", ctypes.c_int32), ("timing", ctypes.c_int32)]
+                ("recompute_every", ctypes.c_int32), ("timing", ctypes.c_int32),
+                ("storage", ctypes.c_int32)]
 
 
 class _Report(ctypes.Structure):
@@ -116,6 +118,10 @@ def lib():
             "ct_version": ([], ctypes.c_char_p),
             "ct_kernel_launches": ([], ctypes.c_int64),
             "ct_geometry_set_deterministic": ([vp, ctypes.c_int32], ctypes.c_int),
+            "ct_project_ex": ([vp, vp, ctypes.c_int32, vp, ctypes.c_int32, ctypes.c_float,
+                               ctypes.c_float, vp], ctypes.c_int),
+            "ct_backproject_ex": ([vp, vp, ctypes.c_int32, vp, ctypes.c_int32, ctypes.c_float,
+                                   ctypes.c_float, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -205,9 +211,21 @@ def _stream(stream=None) -> ctypes.c_void_p:
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _dev(t: torch.Tensor, shape, name: str, device) -> torch.Tensor:
-    if t.dtype != torch.float32:
-        raise TypeError("%s must be float32" % name)
+# storage element types (ct_dtype)
+DTYPES = {torch.float32: 0, torch.bfloat16: 1, torch.float16: 2}
+_DTYPE_NAMES = {"f32": torch.float32, "float32": torch.float32, "bf16": torch.bfloat16,
+                "bfloat16": torch.bfloat16, "f16": torch.float16, "float16": torch.float16}
+
+
+def _torch_dtype(d):
+    if d is None or isinstance(d, torch.dtype):
+        return d
+    return _DTYPE_NAMES[d]
+
+
+def _dev(t: torch.Tensor, shape, name: str, device, typed: bool = False) -> torch.Tensor:
+    if t.dtype != torch.float32 and not (typed and t.dtype in DTYPES):
+        raise TypeError("%s must be float32%s" % (name, " / bfloat16 / float16" if typed else ""))
     if tuple(t.shape) != tuple(shape):
         raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
     if not t.is_cuda:
@@ -222,16 +240,22 @@ def _ptr(t: Optional[torch.Tensor]):
 
 
 def project(g: Geometry, vol: torch.Tensor, out: Optional[torch.Tensor] = None,
-            alpha: float = 1.0, beta: float = 0.0, stream=None) -> torch.Tensor:
-    """out = alpha * A vol + beta * out (ct_project)."""
+            alpha: float = 1.0, beta: float = 0.0, stream=None, out_dtype=None) -> torch.Tensor:
+    """out = alpha * A vol + beta * out (ct_project; ct_project_ex for BF16/FP16
+    storage).  out_dtype (default: vol's dtype) types a new output."""
     host = not vol.is_cuda
-    v = _dev(vol, g.vol_shape, "vol", g.device)
+    v = _dev(vol, g.vol_shape, "vol", g.device, typed=True)
     if out is None:
-        o = torch.empty(g.sino_shape, dtype=torch.float32, device=g.device)
+        od = _torch_dtype(out_dtype) or v.dtype
+        o = torch.empty(g.sino_shape, dtype=od, device=g.device)
     else:
-        o = _dev(out, g.sino_shape, "out", g.device)
-    _check(lib().ct_project(g.handle, _ptr(v), _ptr(o), float(alpha), float(beta),
-                            _stream(stream)))
+        o = _dev(out, g.sino_shape, "out", g.device, typed=True)
+    if v.dtype == torch.float32 and o.dtype == torch.float32:
+        _check(lib().ct_project(g.handle, _ptr(v), _ptr(o), float(alpha), float(beta),
+                                _stream(stream)))
+    else:
+        _check(lib().ct_project_ex(g.handle, _ptr(v), DTYPES[v.dtype], _ptr(o), DTYPES[o.dtype],
+                                   float(alpha), float(beta), _stream(stream)))
     if out is not None and o.data_ptr() != out.data_ptr():
         out.copy_(o)
         return out
@@ -250,16 +274,24 @@ def project_norm2(g: Geometry, vol: torch.Tensor, out: Optional[torch.Tensor] = 
 
 
 def backproject(g: Geometry, sino: torch.Tensor, out: Optional[torch.Tensor] = None,
-                alpha: float = 1.0, beta: float = 0.0, stream=None) -> torch.Tensor:
-    """out = alpha * A^T sino + beta * out (ct_backproject)."""
+                alpha: float = 1.0, beta: float = 0.0, stream=None,
+                out_dtype=None) -> torch.Tensor:
+    """out = alpha * A^T sino + beta * out (ct_backproject; ct_backproject_ex for
+    BF16/FP16 storage).  out_dtype (default: sino's dtype) types a new output."""
     host = not sino.is_cuda
-    s = _dev(sino, g.sino_shape, "sino", g.device)
+    s = _dev(sino, g.sino_shape, "sino", g.device, typed=True)
     if out is None:
-        o = torch.empty(g.vol_shape, dtype=torch.float32, device=g.device)
+        od = _torch_dtype(out_dtype) or s.dtype
+        o = torch.empty(g.vol_shape, dtype=od, device=g.device)
     else:
-        o = _dev(out, g.vol_shape, "out", g.device)
-    _check(lib().ct_backproject(g.handle, _ptr(s), _ptr(o), float(alpha), float(beta),
-                                _stream(stream)))
+        o = _dev(out, g.vol_shape, "out", g.device, typed=True)
+    if s.dtype == torch.float32 and o.dtype == torch.float32:
+        _check(lib().ct_backproject(g.handle, _ptr(s), _ptr(o), float(alpha), float(beta),
+                                    _stream(stream)))
+    else:
+        _check(lib().ct_backproject_ex(g.handle, _ptr(s), DTYPES[s.dtype], _ptr(o),
+                                       DTYPES[o.dtype], float(alpha), float(beta),
+                                       _stream(stream)))
     if out is not None and o.data_ptr() != out.data_ptr():
         out.copy_(o)
         return out
@@ -283,7 +315,7 @@ def precond_weights(g: Geometry, kind, stream=None):
 
 
 def _solve(fn, g: Geometry, b, x0, max_iter, err_tol, precond, recompute_every, timing,
-           stream):
+           stream, storage="f32"):
     host = not b.is_cuda
     bd = _dev(b, g.sino_shape, "b", g.device)
     if x0 is None:
@@ -291,7 +323,8 @@ def _solve(fn, g: Geometry, b, x0, max_iter, err_tol, precond, recompute_every, 
     else:
         x = _dev(x0, g.vol_shape, "x0", g.device).clone()
     opts = SolverOpts(int(max_iter), float(err_tol), _PRECOND[precond], 0.0,
-                      int(recompute_every), 1 if timing else 0)
+                      int(recompute_every), 1 if timing else 0,
+                      DTYPES[_torch_dtype(storage)])
     hist = (ctypes.c_double * int(max_iter))()
     rep = _Report(0, 0.0, 0.0, ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)),
                   int(max_iter), 0, 0, 0.0, 0.0)
@@ -304,10 +337,13 @@ def _solve(fn, g: Geometry, b, x0, max_iter, err_tol, precond, recompute_every, 
 
 def cgls(g: Geometry, b: torch.Tensor, x0: Optional[torch.Tensor] = None, max_iter: int = 20,
          err_tol: float = 0.0, precond="none", recompute_every: int = 0, timing: bool = False,
-         stream=None):
-    """CGLS with delayed residual computation (Algorithm 1) -> (x, SolveReport)."""
+         stream=None, storage="f32"):
+    """CGLS with delayed residual computation (Algorithm 1) -> (x, SolveReport).
+
+    storage ("f32", "bf16", "f16") types the Krylov vectors d_x, e_b, p_b; x,
+    the backprojection sums and the FP64 scalars keep their precision."""
     return _solve(lib().ct_cgls, g, b, x0, max_iter, err_tol, precond, recompute_every, timing,
-                  stream)
+                  stream, storage)
 
 
 def lsqr(g: Geometry, b: torch.Tensor, x0: Optional[torch.Tensor] = None, max_iter: int = 20,

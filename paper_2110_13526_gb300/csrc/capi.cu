@@ -100,8 +100,8 @@ ct_status backproject_impl(const ct_geometry *g, const BackScratch &s, const flo
         return launch_combine(pg, out, s.acc_t, w, partials, st);
     }
     CT_CUDA_TRY(cudaMemsetAsync(s.q, 0, 2 * (size_t)n * sizeof(long long), st));
-    CT_TRY(launch_det_scale(e, rho, g->nrays, det_value_bound(g, power), c, s.part, s.scale,
-                            s.inv, st));
+    CT_TRY(launch_det_scale(e, CT_F32, rho, g->nrays, det_value_bound(g, power), c, s.part,
+                            s.scale, s.inv, st));
     CT_TRY(launch_backward_det(pg, e, rho, c, s.q, s.q + n, power, s.scale, st));
     return launch_combine_det(pg, out, beta, s.q, s.q + n, s.inv, w, partials, st);
 }
@@ -431,6 +431,64 @@ ct_status ct_backproject(const ct_geometry *g, const float *d_sino, float *d_vol
     Coef c;
     c.alpha = alpha;
     return backproject_impl(g, bs, d_sino, nullptr, c, d_vol, beta, 1, nullptr, nullptr, st);
+}
+
+ct_status ct_project_ex(const ct_geometry *g, const void *d_vol, int32_t vol_dtype, void *d_sino,
+                        int32_t sino_dtype, float alpha, float beta, void *stream) {
+    clear_error();
+    CT_TRY(check_geom(g));
+    if (dtype_size(vol_dtype) == 0 || dtype_size(sino_dtype) == 0)
+        return set_error(CT_ERR_INVALID_ARG, "unknown dtype");
+    if (g->nrays == 0) return CT_OK;
+    if (!d_vol || !d_sino) return set_error(CT_ERR_INVALID_ARG, "NULL vector");
+    DeviceGuard dg(g->device);
+    CT_TRY(dg.status());
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace ws(st);
+    void *vol_t = nullptr;
+    CT_TRY(ws.alloc(&vol_t, (size_t)g->nvox * dtype_size(vol_dtype)));
+    CT_TRY(launch_transpose_typed(g->pg, d_vol, vol_t, vol_dtype, st));
+    Coef c;
+    c.alpha = alpha;
+    c.beta = beta;
+    return launch_forward_typed(g->pg, d_vol, vol_t, vol_dtype, d_sino, sino_dtype, nullptr, c,
+                                nullptr, st);
+}
+
+ct_status ct_backproject_ex(const ct_geometry *g, const void *d_sino, int32_t sino_dtype,
+                            void *d_vol, int32_t vol_dtype, float alpha, float beta,
+                            void *stream) {
+    clear_error();
+    CT_TRY(check_geom(g));
+    if (dtype_size(vol_dtype) == 0 || dtype_size(sino_dtype) == 0)
+        return set_error(CT_ERR_INVALID_ARG, "unknown dtype");
+    if (!d_vol) return set_error(CT_ERR_INVALID_ARG, "NULL vector");
+    if (g->nrays > 0 && !d_sino) return set_error(CT_ERR_INVALID_ARG, "NULL vector");
+    DeviceGuard dg(g->device);
+    CT_TRY(dg.status());
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = g->nvox;
+    Workspace ws(st);
+    Coef c;
+    c.alpha = alpha;
+    if (g->deterministic && g->nrays > 0 && alpha != 0.f) {
+        BackScratch bs;
+        CT_TRY(back_scratch_alloc(g, ws, nullptr, &bs));
+        CT_CUDA_TRY(cudaMemsetAsync(bs.q, 0, 2 * (size_t)n * sizeof(long long), st));
+        CT_TRY(launch_det_scale(d_sino, sino_dtype, nullptr, g->nrays, det_value_bound(g, 1), c,
+                                bs.part, bs.scale, bs.inv, st));
+        CT_TRY(launch_backward_typed(g->pg, d_sino, sino_dtype, nullptr, c, bs.q, bs.q + n, 1,
+                                     true, bs.scale, st));
+        return launch_combine_typed(g->pg, d_vol, vol_dtype, beta, nullptr, nullptr, bs.q, bs.inv,
+                                    st);
+    }
+    float *acc = nullptr;
+    CT_TRY(ws.alloc(&acc, 2 * (size_t)n));
+    CT_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * (size_t)n * sizeof(float), st));
+    if (g->nrays > 0 && alpha != 0.f)
+        CT_TRY(launch_backward_typed(g->pg, d_sino, sino_dtype, nullptr, c, acc, acc + n, 1, false,
+                                     nullptr, st));
+    return launch_combine_typed(g->pg, d_vol, vol_dtype, beta, acc, acc + n, nullptr, nullptr, st);
 }
 
 ct_status ct_geometry_set_deterministic(ct_geometry *g, int32_t on) {

@@ -141,6 +141,17 @@ ct_status launch_backward(const ProjGeom &pg, const float *e, const float *rho, 
 // Count the (ray, voxel) pairs with positive length into *d_count (int64).
 ct_status launch_count(const ProjGeom &pg, unsigned long long *d_count, cudaStream_t st);
 
+// Typed storage (ct_dtype): p (sdt) = alpha rho o (A vol (vdt)) + beta p.
+ct_status launch_forward_typed(const ProjGeom &pg, const void *vol, const void *vol_t, int vdt,
+                               void *p, int sdt, const float *rho, Coef c, double *partials,
+                               cudaStream_t st);
+// Typed input e (sdt); accumulators float (det = false) or int64 (det = true).
+ct_status launch_backward_typed(const ProjGeom &pg, const void *e, int sdt, const float *rho,
+                                Coef c, void *acc, void *acc_t, int power, bool det,
+                                const float *det_scale, cudaStream_t st);
+// Bytes of one element of a ct_dtype (0 if unknown).
+inline size_t dtype_size(int dt) { return dt == CT_F32 ? 4 : (dt == CT_BF16 || dt == CT_F16) ? 2 : 0; }
+
 // The same scatter accumulating rint(value * scale) in int64 (scale =
 // det_scale[0], a power of two): order-independent, hence deterministic.
 ct_status launch_backward_det(const ProjGeom &pg, const float *e, const float *rho, Coef c,
@@ -148,8 +159,8 @@ ct_status launch_backward_det(const ProjGeom &pg, const float *e, const float *r
                               const float *det_scale, cudaStream_t st);
 // scale[0] = 2^k (float) and inv[0] = 2^-k (double) with k the largest integer
 // such that |alpha| max|e rho| bound 2^k <= 2^62.  part: vec_grid(m) floats.
-ct_status launch_det_scale(const float *e, const float *rho, int64_t m, double bound, Coef c,
-                           float *part, float *scale, double *inv, cudaStream_t st);
+ct_status launch_det_scale(const void *e, int edt, const float *rho, int64_t m, double bound,
+                           Coef c, float *part, float *scale, double *inv, cudaStream_t st);
 // out = beta out + (acc + transpose(acc_t)) inv; optional partials of (w out)^2.
 ct_status launch_combine_det(const ProjGeom &pg, float *out, float beta, const long long *acc,
                              const long long *acc_t, const double *inv, const float *w,
@@ -173,6 +184,14 @@ ct_status launch_transpose(const ProjGeom &pg, const float *v, const float *w, f
 int transpose_grid_count(const ProjGeom &pg);
 ct_status launch_combine(const ProjGeom &pg, float *g, const float *acc_t, const float *w,
                          double *partials, cudaStream_t st);
+// Typed transpose: t (dt) = transpose of v (dt), [nz][ny][nx] -> [nz][nx][ny].
+ct_status launch_transpose_typed(const ProjGeom &pg, const void *v, void *t, int dt,
+                                 cudaStream_t st);
+// out (dt) = beta out + acc + transpose(acc_t) with FP32 accumulators, or
+// (when q != NULL) with int64 accumulators q, q + nvox scaled by inv[0].
+ct_status launch_combine_typed(const ProjGeom &pg, void *out, int dt, float beta, const float *acc,
+                               const float *acc_t, const long long *q, const double *inv,
+                               cudaStream_t st);
 // out = beta * out (beta == 0 writes zeros without reading)
 ct_status launch_scale(float *out, int64_t n, float beta, cudaStream_t st);
 ct_status launch_scale_dev(float *out, int64_t n, const double *beta, cudaStream_t st);

@@ -35,6 +35,7 @@
 #include <type_traits>
 
 #include "ct_internal.h"
+#include "ct_types.cuh"
 
 namespace ct {
 namespace {
@@ -298,10 +299,10 @@ __device__ __forceinline__ void coef_of(const Coef &c, float &alpha, float &beta
 }
 
 // p = alpha * rho o (A vol) + beta * p.  vol == NULL means the all-ones volume.
-template <bool HAS_RHO, bool NORM, bool UNIT_VOL>
-__global__ void __launch_bounds__(kTU *kTV, 6) k_forward(ProjGeom g, const float *__restrict__ vol,
-                                                      const float *__restrict__ vol_t,
-                                                      float *__restrict__ out,
+template <bool HAS_RHO, bool NORM, bool UNIT_VOL, class TV = float, class TS = float>
+__global__ void __launch_bounds__(kTU *kTV, 6) k_forward(ProjGeom g, const TV *__restrict__ vol,
+                                                      const TV *__restrict__ vol_t,
+                                                      TS *__restrict__ out,
                                                       const float *__restrict__ rho, Coef c,
                                                       double *__restrict__ partials) {
     __shared__ double sh[32];
@@ -311,11 +312,11 @@ __global__ void __launch_bounds__(kTU *kTV, 6) k_forward(ProjGeom g, const float
     const bool inb = (u < g.nu) && (v < g.nv);
     Ray r;
     const bool valid = inb && ray_setup(g, view, u, v, r);
-    const float *base = r.transposed ? vol_t : vol;
+    const TV *base = r.transposed ? vol_t : vol;
     float acc = 0.f;
     walk(r, valid, [&](int o, float l, bool p) {
         float val = 0.f;
-        if (p) val = UNIT_VOL ? 1.f : __ldg(base + o);
+        if (p) val = UNIT_VOL ? 1.f : ld_f(base + o);
         acc = fmaf(l, val, acc);
     });
     float alpha, beta;
@@ -326,9 +327,13 @@ __global__ void __launch_bounds__(kTU *kTV, 6) k_forward(ProjGeom g, const float
         float val = valid ? acc * r.lsig : 0.f;
         if (HAS_RHO) val *= rho[idx];
         float o = alpha * val;
-        if (beta != 0.f) o = fmaf(beta, out[idx], o);
-        out[idx] = o;
-        if (NORM) sq = (double)o * (double)o;
+        if (beta != 0.f) o = fmaf(beta, to_f(out[idx]), o);
+        const TS st = from_f<TS>(o);
+        out[idx] = st;
+        if (NORM) {
+            const double q = (double)to_f(st);  // the norm of what is stored
+            sq = q * q;
+        }
     }
     if (NORM) {
         double t = block_sum_d(sq, sh);
@@ -342,8 +347,8 @@ __global__ void __launch_bounds__(kTU *kTV, 6) k_forward(ProjGeom g, const float
 // accumulates q = rint(value * scale) in 64-bit integers (scale = a power of
 // two read from det_scale[0]): integer addition is associative, so the sums
 // do not depend on the order in which rays arrive.
-template <bool HAS_RHO, int POWER, bool DET>
-__global__ void __launch_bounds__(kTU *kTV, 6) k_backward(ProjGeom g, const float *__restrict__ e,
+template <bool HAS_RHO, int POWER, bool DET, class TS = float>
+__global__ void __launch_bounds__(kTU *kTV, 6) k_backward(ProjGeom g, const TS *__restrict__ e,
                                                        const float *__restrict__ rho, Coef c,
                                                        void *__restrict__ acc,
                                                        void *__restrict__ acc_t,
@@ -359,7 +364,7 @@ __global__ void __launch_bounds__(kTU *kTV, 6) k_backward(ProjGeom g, const floa
     float w = 0.f;
     if (valid) {
         const size_t idx = ((size_t)view * g.nv + v) * g.nu + u;
-        w = alpha * (e ? e[idx] : 1.f);
+        w = alpha * (e ? to_f(e[idx]) : 1.f);
         if (HAS_RHO) w *= rho[idx];
         if (POWER == 1) w *= r.lsig;
     }
@@ -475,6 +480,87 @@ ct_status launch_forward(const ProjGeom &pg, const float *vol, const float *vol_
 #undef CT_FWD
     CT_CHECK_LAUNCH();
     return CT_OK;
+}
+
+namespace {
+
+template <class TV, class TS>
+ct_status fwd_typed(const ProjGeom &pg, const void *vol, const void *vol_t, void *p,
+                    const float *rho, Coef c, double *partials, cudaStream_t st) {
+    dim3 gr = proj_grid(pg), bl(kTU, kTV);
+    const TV *v = static_cast<const TV *>(vol);
+    const TV *vt = static_cast<const TV *>(vol_t);
+    TS *o = static_cast<TS *>(p);
+    if (rho) {
+        if (partials) k_forward<true, true, false, TV, TS><<<gr, bl, 0, st>>>(pg, v, vt, o, rho, c, partials);
+        else          k_forward<true, false, false, TV, TS><<<gr, bl, 0, st>>>(pg, v, vt, o, rho, c, partials);
+    } else {
+        if (partials) k_forward<false, true, false, TV, TS><<<gr, bl, 0, st>>>(pg, v, vt, o, rho, c, partials);
+        else          k_forward<false, false, false, TV, TS><<<gr, bl, 0, st>>>(pg, v, vt, o, rho, c, partials);
+    }
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+template <class TV>
+ct_status fwd_typed_s(const ProjGeom &pg, const void *vol, const void *vol_t, void *p, int sdt,
+                      const float *rho, Coef c, double *partials, cudaStream_t st) {
+    switch (sdt) {
+        case CT_F32: return fwd_typed<TV, float>(pg, vol, vol_t, p, rho, c, partials, st);
+        case CT_BF16: return fwd_typed<TV, __nv_bfloat16>(pg, vol, vol_t, p, rho, c, partials, st);
+        case CT_F16: return fwd_typed<TV, __half>(pg, vol, vol_t, p, rho, c, partials, st);
+    }
+    return set_error(CT_ERR_INVALID_ARG, "unknown sinogram dtype");
+}
+
+template <class TS>
+ct_status back_typed(const ProjGeom &pg, const void *e, const float *rho, Coef c, void *acc,
+                     void *acc_t, int power, bool det, const float *det_scale, cudaStream_t st) {
+    dim3 gr = proj_grid(pg), bl(kTU, kTV);
+    const TS *et = static_cast<const TS *>(e);
+    const bool hr = rho != nullptr;
+#define CT_BWD(HR, P, D) \
+    k_backward<HR, P, D, TS><<<gr, bl, 0, st>>>(pg, et, rho, c, acc, acc_t, det_scale)
+    if (det) {
+        if (power == 2) { if (hr) CT_BWD(true, 2, true); else CT_BWD(false, 2, true); }
+        else            { if (hr) CT_BWD(true, 1, true); else CT_BWD(false, 1, true); }
+    } else {
+        if (power == 2) { if (hr) CT_BWD(true, 2, false); else CT_BWD(false, 2, false); }
+        else            { if (hr) CT_BWD(true, 1, false); else CT_BWD(false, 1, false); }
+    }
+#undef CT_BWD
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+}  // namespace
+
+ct_status launch_forward_typed(const ProjGeom &pg, const void *vol, const void *vol_t, int vdt,
+                               void *p, int sdt, const float *rho, Coef c, double *partials,
+                               cudaStream_t st) {
+    if (empty(pg)) return CT_OK;
+    switch (vdt) {
+        case CT_F32: return fwd_typed_s<float>(pg, vol, vol_t, p, sdt, rho, c, partials, st);
+        case CT_BF16:
+            return fwd_typed_s<__nv_bfloat16>(pg, vol, vol_t, p, sdt, rho, c, partials, st);
+        case CT_F16: return fwd_typed_s<__half>(pg, vol, vol_t, p, sdt, rho, c, partials, st);
+    }
+    return set_error(CT_ERR_INVALID_ARG, "unknown volume dtype");
+}
+
+ct_status launch_backward_typed(const ProjGeom &pg, const void *e, int sdt, const float *rho,
+                                Coef c, void *acc, void *acc_t, int power, bool det,
+                                const float *det_scale, cudaStream_t st) {
+    if (empty(pg)) return CT_OK;
+    switch (sdt) {
+        case CT_F32:
+            return back_typed<float>(pg, e, rho, c, acc, acc_t, power, det, det_scale, st);
+        case CT_BF16:
+            return back_typed<__nv_bfloat16>(pg, e, rho, c, acc, acc_t, power, det, det_scale, st);
+        case CT_F16:
+            return back_typed<__half>(pg, e, rho, c, acc, acc_t, power, det, det_scale, st);
+    }
+    return set_error(CT_ERR_INVALID_ARG, "unknown sinogram dtype");
 }
 
 ct_status launch_backward(const ProjGeom &pg, const float *e, const float *rho, Coef c,

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "ct_internal.h"
+#include "ct_types.cuh"
 
 namespace ct {
 namespace {
@@ -45,37 +46,58 @@ __device__ __forceinline__ double sum_partials(const double *__restrict__ p, int
 __device__ __forceinline__ double safe_div(double a, double b) { return b != 0.0 ? a / b : 0.0; }
 
 // ---- CGLS ------------------------------------------------------------------
+// zs: the direction is stored as z~ = zs z (zs a power of two, 1 in FP32
+// storage) so that it fits BF16/FP16; the step alpha then applies to z~ and
+// p~ = A z~ directly: alpha~ = NR2 zs / ||p~||^2.
 struct CglsS {
-    double nb0, nr2_old, nr2_now, np2, alpha, beta, nb, a_pend, tmp;
+    double nb0, nr2_old, nr2_now, np2, alpha, beta, nb, a_pend, tmp, zs;
 };
 
-// e = L o b; partial sums of e^2 (one per CTA).
-__global__ void k_sino_weighted_copy(float *__restrict__ e, const float *__restrict__ b,
+// e = L o b, stored as S; partial sums of the stored e^2 (one per CTA).
+template <class S>
+__global__ void k_sino_weighted_copy(S *__restrict__ e, const float *__restrict__ b,
                                      const float *__restrict__ L, int64_t n,
                                      double *__restrict__ part) {
     __shared__ double sh[32];
     double sq = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const float v = L ? L[i] * b[i] : b[i];
+        const S v = from_f<S>(L ? L[i] * b[i] : b[i]);
         e[i] = v;
-        sq = fma((double)v, (double)v, sq);
+        const double q = to_f(v);
+        sq = fma(q, q, sq);
     }
     const double t = block_sum(sq, sh);
     if (threadIdx.x == 0 && part) part[blockIdx.x] = t;
 }
 
 // e_b = e_b - alpha p_b; partial sums of e_b^2 (Algorithm 1: NB = ||e_b||).
-__global__ void k_sino_axpy(float *__restrict__ e, const float *__restrict__ p, int64_t n,
+template <class S>
+__global__ void k_sino_axpy(S *__restrict__ e, const S *__restrict__ p, int64_t n,
                             const double *__restrict__ alpha, double *__restrict__ part) {
     __shared__ double sh[32];
     const float a = (float)alpha[0];
     double sq = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const float v = fmaf(-a, p[i], e[i]);
+        const S v = from_f<S>(fmaf(-a, to_f(p[i]), to_f(e[i])));
         e[i] = v;
-        sq = fma((double)v, (double)v, sq);
+        const double q = to_f(v);
+        sq = fma(q, q, sq);
+    }
+    const double t = block_sum(sq, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// partial sums of v^2 (one per CTA)
+template <class S>
+__global__ void k_norm2_t(const S *__restrict__ v, int64_t n, double *__restrict__ part) {
+    __shared__ double sh[32];
+    double sq = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double q = to_f(v[i]);
+        sq = fma(q, q, sq);
     }
     const double t = block_sum(sq, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
@@ -83,37 +105,41 @@ __global__ void k_sino_axpy(float *__restrict__ e, const float *__restrict__ p, 
 
 // x = x + a_pend z (the x update delayed from the previous iteration), then
 // z = W^2 g + beta z (d_x = r_x + beta d_x in y-space, stored as z = W d).
-// first: z = W^2 g, neither x nor the old z is read.
-__global__ void k_vol_update(float *__restrict__ x, float *__restrict__ z,
+// first: z = W^2 g, neither x nor the old z is read.  x stays FP32; z is
+// stored as S.
+template <class S>
+__global__ void k_vol_update(float *__restrict__ x, S *__restrict__ z,
                              const float *__restrict__ g, const float *__restrict__ W, int64_t n,
                              const double *__restrict__ a_pend, const double *__restrict__ beta,
-                             int first) {
+                             const double *__restrict__ zs, int first) {
     const float a = first ? 0.f : (float)a_pend[0];
     const float b = first ? 0.f : (float)beta[0];
+    const float gs = (float)zs[0];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        float r = g[i];
+        float r = g[i] * gs;
         if (W) {
             const float w = W[i];
             r *= w * w;
         }
         if (first) {
-            z[i] = r;
+            z[i] = from_f<S>(r);
         } else {
-            const float zo = z[i];
+            const float zo = to_f(z[i]);
             if (a != 0.f) x[i] = fmaf(a, zo, x[i]);
-            z[i] = fmaf(b, zo, r);
+            z[i] = from_f<S>(fmaf(b, zo, r));
         }
     }
 }
 
-__global__ void k_vol_axpy(float *__restrict__ x, const float *__restrict__ z, int64_t n,
+template <class S>
+__global__ void k_vol_axpy(float *__restrict__ x, const S *__restrict__ z, int64_t n,
                            const double *__restrict__ a) {
     const float s = (float)a[0];
     if (s == 0.f) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        x[i] = fmaf(s, z[i], x[i]);
+        x[i] = fmaf(s, to_f(z[i]), x[i]);
 }
 
 __global__ void __launch_bounds__(1024) k_cgls_nb0(const double *__restrict__ p, int64_t n,
@@ -125,6 +151,7 @@ __global__ void __launch_bounds__(1024) k_cgls_nb0(const double *__restrict__ p,
         S->a_pend = 0.0;
         S->beta = 0.0;
         S->alpha = 0.0;
+        S->zs = 1.0;
     }
 }
 
@@ -135,15 +162,51 @@ __global__ void __launch_bounds__(1024) k_store_sum(const double *__restrict__ p
     if (threadIdx.x == 0) out[0] = t;
 }
 
-// NR2_now = ||r_x||^2; beta = NR2_now / NR2_old; NR2_old = NR2_now.
+// NR2_now = ||r_x||^2; beta = NR2_now / NR2_old; NR2_old = NR2_now.  With
+// maxpart (the block maxima of |W^2 g|), the new direction scale zs puts
+// max |zs W^2 g| in [1/2, 1) and beta absorbs the ratio to the old scale.
 __global__ void __launch_bounds__(1024) k_cgls_nr2(const double *__restrict__ p, int64_t n,
-                                                   CglsS *S, int first) {
+                                                   CglsS *S, int first,
+                                                   const float *__restrict__ maxpart, int nmax) {
     __shared__ double sh[32];
     const double t = sum_partials(p, n, sh);
     if (threadIdx.x == 0) {
+        double zs = 1.0;
+        if (maxpart) {
+            float mx = 0.f;
+            for (int i = 0; i < nmax; ++i) mx = fmaxf(mx, maxpart[i]);
+            if (mx > 0.f && mx < 3.0e38f) {
+                int ex = 0;
+                (void)frexp((double)mx, &ex);
+                zs = ldexp(1.0, -ex);
+            }
+        }
+        const double zs_old = first ? zs : S->zs;
         S->nr2_now = t;
-        S->beta = first ? 0.0 : safe_div(t, S->nr2_old);
+        S->beta = first ? 0.0 : safe_div(t, S->nr2_old) * (zs / zs_old);
         S->nr2_old = t;
+        S->zs = zs;
+    }
+}
+
+// Block maxima of |W^2 g| (W NULL: |g|).
+__global__ void k_absmax_w2g(const float *__restrict__ g, const float *__restrict__ W, int64_t n,
+                             float *__restrict__ part) {
+    __shared__ float sh[32];
+    float m = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float r = g[i];
+        if (W) r *= W[i] * W[i];
+        m = fmaxf(m, fabsf(r));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_down_sync(0xffffffffu, t, o));
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
     }
 }
 
@@ -154,7 +217,7 @@ __global__ void __launch_bounds__(1024) k_cgls_np2(const double *__restrict__ p,
     const double t = sum_partials(p, n, sh);
     if (threadIdx.x == 0) {
         S->np2 = t;
-        S->alpha = safe_div(S->nr2_old, t);
+        S->alpha = safe_div(S->nr2_old * S->zs, t);
         S->a_pend = S->alpha;
     }
 }
@@ -331,6 +394,7 @@ ct_status check_opts(const ct_geometry *g, const float *b, float *x, const ct_so
     if (o->tikhonov_lambda != 0.0)
         return set_error(CT_ERR_INVALID_ARG, "Tikhonov regularisation is not supported");
     if (o->recompute_every < 0) return set_error(CT_ERR_INVALID_ARG, "recompute_every < 0");
+    if (dtype_size(o->storage) == 0) return set_error(CT_ERR_INVALID_ARG, "unknown storage dtype");
     return CT_OK;
 }
 
@@ -373,26 +437,42 @@ struct Solve {
         ++n_fwd;
         return CT_OK;
     }
-    // gout = c * A^T (L o e), then partials of (Wg)^2 if requested; the
-    // geometry decides float-atomic or fixed-point (deterministic) sums.
-    ct_status back(const float *e, float *gout, Coef c, const float *wnorm, double *partials) {
+    // out (sdt) = c.alpha * L o (A vol (vdt)) + c.beta * out; tbuf receives the
+    // transposed copy of vol (same dtype) first.
+    ct_status forward_t(const void *vol, int vdt, void *tbuf, void *out, int sdt, Coef c,
+                        double *partials) {
+        CT_TRY(launch_transpose_typed(pg, vol, tbuf, vdt, st));
+        CT_TRY(tm.mark(tm.fwd));
+        CT_TRY(launch_forward_typed(pg, vol, tbuf, vdt, out, sdt, L, c, partials, st));
+        CT_TRY(tm.mark(tm.fwd));
+        ++n_fwd;
+        return CT_OK;
+    }
+    // gout = c * A^T (L o e) (e of dtype edt), then partials of (Wg)^2 if
+    // requested; the geometry decides float-atomic or fixed-point
+    // (deterministic) sums.
+    ct_status back_t(const void *e, int edt, float *gout, Coef c, const float *wnorm,
+                     double *partials) {
         if (!g->deterministic) {
             CT_CUDA_TRY(cudaMemsetAsync(gout, 0, (size_t)n * sizeof(float), st));
             CT_CUDA_TRY(cudaMemsetAsync(T, 0, (size_t)n * sizeof(float), st));
             CT_TRY(tm.mark(tm.back));
-            CT_TRY(launch_backward(pg, e, L, c, gout, T, 1, st));
+            CT_TRY(launch_backward_typed(pg, e, edt, L, c, gout, T, 1, false, nullptr, st));
             CT_TRY(tm.mark(tm.back));
             ++n_back;
             return launch_combine(pg, gout, T, wnorm, partials, st);
         }
         CT_CUDA_TRY(cudaMemsetAsync(bs.q, 0, 2 * (size_t)n * sizeof(long long), st));
-        CT_TRY(launch_det_scale(e, L, m, det_value_bound(g, 1), c, bs.part, bs.scale, bs.inv,
-                                st));
+        CT_TRY(launch_det_scale(e, edt, L, m, det_value_bound(g, 1), c, bs.part, bs.scale,
+                                bs.inv, st));
         CT_TRY(tm.mark(tm.back));
-        CT_TRY(launch_backward_det(pg, e, L, c, bs.q, bs.q + n, 1, bs.scale, st));
+        CT_TRY(launch_backward_typed(pg, e, edt, L, c, bs.q, bs.q + n, 1, true, bs.scale, st));
         CT_TRY(tm.mark(tm.back));
         ++n_back;
         return launch_combine_det(pg, gout, 0.f, bs.q, bs.q + n, bs.inv, wnorm, partials, st);
+    }
+    ct_status back(const float *e, float *gout, Coef c, const float *wnorm, double *partials) {
+        return back_t(e, CT_F32, gout, c, wnorm, partials);
     }
     // Is x0 nonzero?  (One reduction and one host read.)
     ct_status nonzero(const float *x, bool *out) {
@@ -431,8 +511,10 @@ ct_status read_scalars(const S *d, S *h, cudaStream_t st) {
 }
 
 
+template <class ST>
 ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_solver_opts *o,
                     ct_solver_report *rep, cudaStream_t st) {
+    const int sd = o->storage;
     const int K = o->max_iter;
     const double ERR = o->err_tol;
     Solve sv(g, st, o->timing != 0);
@@ -440,11 +522,22 @@ ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
     const int64_t n = sv.n, m = sv.m;
     const int gn = vec_grid(n), gm = vec_grid(m);
     const int64_t nfp = forward_partials(sv.pg), ncp = transpose_grid_count(sv.pg);
-    float *z = nullptr, *gv = nullptr, *e = nullptr, *p = nullptr;
+    ST *z = nullptr, *e = nullptr, *p = nullptr;
+    float *gv = nullptr;
+    void *Ts = nullptr;  // transposed copy of z (the float scratch T when ST is float)
     CglsS *S = nullptr;
     double *hist = nullptr;
     CT_TRY(sv.ws.alloc(&z, (size_t)n));
     CT_TRY(sv.ws.alloc(&gv, (size_t)n));
+    float *mxp = nullptr;  // block maxima of |W^2 g| (direction scaling, reduced storage)
+    if (sd == CT_F32) {
+        Ts = sv.T;
+    } else {
+        CT_TRY(sv.ws.alloc(&mxp, (size_t)gn));
+        ST *t = nullptr;
+        CT_TRY(sv.ws.alloc(&t, (size_t)n));
+        Ts = t;
+    }
     CT_TRY(sv.ws.alloc(&e, (size_t)std::max<int64_t>(m, 1)));
     CT_TRY(sv.ws.alloc(&p, (size_t)std::max<int64_t>(m, 1)));
     CT_TRY(sv.ws.alloc(&S, 1));
@@ -462,15 +555,20 @@ ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
     CT_CHECK_LAUNCH();
     k_cgls_nb0<<<1, 1024, 0, st>>>(sv.part, gm, S);
     CT_CHECK_LAUNCH();
-    if (x0nz) CT_TRY(sv.forward(x, false, e, sub, nullptr));
+    if (x0nz) CT_TRY(sv.forward_t(x, CT_F32, sv.T, e, sd, sub, nullptr));
     // r_x = A^T e_b; d_x = r_x; NR2_old = ||r_x||^2
-    CT_TRY(sv.back(e, gv, one, sv.W, sv.part));
-    k_cgls_nr2<<<1, 1024, 0, st>>>(sv.part, ncp, S, 1);
+    CT_TRY(sv.back_t(e, sd, gv, one, sv.W, sv.part));
+    if (mxp) {
+        k_absmax_w2g<<<gn, kVecThreads, 0, st>>>(gv, sv.W, n, mxp);
+        CT_CHECK_LAUNCH();
+    }
+    k_cgls_nr2<<<1, 1024, 0, st>>>(sv.part, ncp, S, 1, mxp, gn);
     CT_CHECK_LAUNCH();
-    k_vol_update<<<gn, kVecThreads, 0, st>>>(x, z, gv, sv.W, n, &S->a_pend, &S->beta, 1);
+    k_vol_update<<<gn, kVecThreads, 0, st>>>(x, z, gv, sv.W, n, &S->a_pend, &S->beta, &S->zs,
+                                             1);
     CT_CHECK_LAUNCH();
     // p_b = A d_x; NP2; alpha
-    CT_TRY(sv.forward(z, false, p, one, sv.part));
+    CT_TRY(sv.forward_t(z, sd, Ts, p, sd, one, sv.part));
     k_cgls_np2<<<1, 1024, 0, st>>>(sv.part, nfp, S);
     CT_CHECK_LAUNCH();
     // (x = x + alpha d_x is delayed into the next volume update)
@@ -493,14 +591,19 @@ ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
     CT_TRY(keep_going(&go));
     while (go) {
         // r_x = A^T e_b; NR2_now; beta; NR2_old = NR2_now
-        CT_TRY(sv.back(e, gv, one, sv.W, sv.part));
-        k_cgls_nr2<<<1, 1024, 0, st>>>(sv.part, ncp, S, 0);
+        CT_TRY(sv.back_t(e, sd, gv, one, sv.W, sv.part));
+        if (mxp) {
+            k_absmax_w2g<<<gn, kVecThreads, 0, st>>>(gv, sv.W, n, mxp);
+            CT_CHECK_LAUNCH();
+        }
+        k_cgls_nr2<<<1, 1024, 0, st>>>(sv.part, ncp, S, 0, mxp, gn);
         CT_CHECK_LAUNCH();
         // x = x + alpha d_x (previous iteration); d_x = r_x + beta d_x
-        k_vol_update<<<gn, kVecThreads, 0, st>>>(x, z, gv, sv.W, n, &S->a_pend, &S->beta, 0);
+        k_vol_update<<<gn, kVecThreads, 0, st>>>(x, z, gv, sv.W, n, &S->a_pend, &S->beta,
+                                                 &S->zs, 0);
         CT_CHECK_LAUNCH();
         // p_b = A d_x; NP2; alpha
-        CT_TRY(sv.forward(z, false, p, one, sv.part));
+        CT_TRY(sv.forward_t(z, sd, Ts, p, sd, one, sv.part));
         k_cgls_np2<<<1, 1024, 0, st>>>(sv.part, nfp, S);
         CT_CHECK_LAUNCH();
         // e_b = e_b - alpha p_b; NB
@@ -515,8 +618,9 @@ ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
             CT_CHECK_LAUNCH();
             k_sino_weighted_copy<<<gm, kVecThreads, 0, st>>>(e, b, sv.L, m, nullptr);
             CT_CHECK_LAUNCH();
-            CT_TRY(sv.forward(x, false, e, sub, nullptr));
-            CT_TRY(launch_norm2(e, nullptr, m, sv.part, st));
+            CT_TRY(sv.forward_t(x, CT_F32, sv.T, e, sd, sub, nullptr));
+            k_norm2_t<<<gm, kVecThreads, 0, st>>>(e, m, sv.part);
+            CT_CHECK_LAUNCH();
         }
         k_cgls_nb<<<1, 1024, 0, st>>>(sv.part, gm, S, hist, i - 1);
         CT_CHECK_LAUNCH();
@@ -636,7 +740,12 @@ ct_status ct_cgls(const ct_geometry *g, const float *d_b, float *d_x, const ct_s
     DeviceGuard dg(g->device);
     CT_TRY(dg.status());
     cudaStream_t st = (cudaStream_t)stream;
-    ct_status s = cgls_impl(g, d_b, d_x, opts, report, st);
+    ct_status s;
+    switch (opts->storage) {
+        case CT_BF16: s = cgls_impl<__nv_bfloat16>(g, d_b, d_x, opts, report, st); break;
+        case CT_F16: s = cgls_impl<__half>(g, d_b, d_x, opts, report, st); break;
+        default: s = cgls_impl<float>(g, d_b, d_x, opts, report, st);
+    }
     cudaError_t e = cudaStreamSynchronize(st);
     if (s == CT_OK && e != cudaSuccess) return cuda_error(e, "ct_cgls");
     return s;
@@ -649,6 +758,8 @@ ct_status ct_lsqr(const ct_geometry *g, const float *d_b, float *d_x, const ct_s
     DeviceGuard dg(g->device);
     CT_TRY(dg.status());
     cudaStream_t st = (cudaStream_t)stream;
+    if (opts->storage != CT_F32)
+        return set_error(CT_ERR_INVALID_ARG, "LSQR supports FP32 storage only");
     ct_status s = lsqr_impl(g, d_b, d_x, opts, report, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (s == CT_OK && e != cudaSuccess) return cuda_error(e, "ct_lsqr");

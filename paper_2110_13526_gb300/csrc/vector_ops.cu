@@ -6,6 +6,7 @@
 // and one CTA sums the partials in a fixed order, so a result never depends
 // on scheduling.
 #include "ct_internal.h"
+#include "ct_types.cuh"
 
 namespace ct {
 namespace {
@@ -234,7 +235,8 @@ ct_status launch_inv_sqrt_guarded(float *v, int64_t n, float rel, float *part, c
 namespace {
 
 // Block maxima of |e_i rho_i| (e or rho NULL: 1).
-__global__ void k_absmax_partials(const float *__restrict__ e, const float *__restrict__ rho,
+template <class TE>
+__global__ void k_absmax_partials(const TE *__restrict__ e, const float *__restrict__ rho,
                                   int64_t n, float *__restrict__ part) {
     __shared__ float sh[32];
     float m = 0.f;
@@ -243,7 +245,7 @@ __global__ void k_absmax_partials(const float *__restrict__ e, const float *__re
     } else {
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
              i += (int64_t)gridDim.x * blockDim.x)
-            m = fmaxf(m, fabsf((e ? e[i] : 1.f) * (rho ? rho[i] : 1.f)));
+            m = fmaxf(m, fabsf((e ? to_f(e[i]) : 1.f) * (rho ? rho[i] : 1.f)));
     }
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
@@ -315,10 +317,19 @@ __global__ void __launch_bounds__(256) k_combine_det(int nx, int ny, float *__re
 
 }  // namespace
 
-ct_status launch_det_scale(const float *e, const float *rho, int64_t m, double bound, Coef c,
-                           float *part, float *scale, double *inv, cudaStream_t st) {
+ct_status launch_det_scale(const void *e, int edt, const float *rho, int64_t m, double bound,
+                           Coef c, float *part, float *scale, double *inv, cudaStream_t st) {
     const int gb = vec_grid(m);
-    k_absmax_partials<<<gb, kVecThreads, 0, st>>>(e, rho, m, part);
+    switch (edt) {
+        case CT_BF16:
+            k_absmax_partials<<<gb, kVecThreads, 0, st>>>((const __nv_bfloat16 *)e, rho, m, part);
+            break;
+        case CT_F16:
+            k_absmax_partials<<<gb, kVecThreads, 0, st>>>((const __half *)e, rho, m, part);
+            break;
+        default:
+            k_absmax_partials<<<gb, kVecThreads, 0, st>>>((const float *)e, rho, m, part);
+    }
     CT_CHECK_LAUNCH();
     k_det_scale<<<1, 1, 0, st>>>(part, gb, bound, c, scale, inv);
     CT_CHECK_LAUNCH();
@@ -330,6 +341,106 @@ ct_status launch_combine_det(const ProjGeom &pg, float *out, float beta, const l
                              double *partials, cudaStream_t st) {
     dim3 gr((pg.nx + kTile - 1) / kTile, (pg.ny + kTile - 1) / kTile, pg.nz), bl(kTile, 8);
     k_combine_det<<<gr, bl, 0, st>>>(pg.nx, pg.ny, out, beta, acc, acc_t, inv, w, partials);
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+// ---- typed storage -------------------------------------------------------------
+namespace {
+
+template <class T>
+__global__ void __launch_bounds__(256) k_transpose_t(int nx, int ny, const T *__restrict__ in,
+                                                     T *__restrict__ t) {
+    __shared__ T tile[kTile][kTile + 1];
+    const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
+    const size_t zoff = (size_t)blockIdx.z * nx * ny;
+    for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
+        const int x = x0 + threadIdx.x, y = y0 + j;
+        if (x < nx && y < ny) tile[j][threadIdx.x] = in[zoff + (size_t)y * nx + x];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
+        const int y = y0 + threadIdx.x, x = x0 + j;
+        if (x < nx && y < ny) t[zoff + (size_t)x * ny + y] = tile[threadIdx.x][j];
+    }
+}
+
+// out (T) = beta out + acc + transpose(acc_t) (FP32 sums), or the int64 sums
+// q, q + nvox times inv[0] when q is set.
+template <class T>
+__global__ void __launch_bounds__(256) k_combine_t(int nx, int ny, int64_t nvox, T *__restrict__ out,
+                                                   float beta, const float *__restrict__ acc,
+                                                   const float *__restrict__ acc_t,
+                                                   const long long *__restrict__ q,
+                                                   const double *__restrict__ inv) {
+    __shared__ double tile[kTile][kTile + 1];
+    const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
+    const size_t zoff = (size_t)blockIdx.z * nx * ny;
+    for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
+        const int x = x0 + j, y = y0 + threadIdx.x;
+        if (x < nx && y < ny) {
+            const size_t it = zoff + (size_t)x * ny + y;
+            tile[j][threadIdx.x] = q ? (double)q[nvox + it] : (double)acc_t[it];
+        }
+    }
+    __syncthreads();
+    const double s = q ? inv[0] : 1.0;
+    for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
+        const int y = y0 + j, x = x0 + threadIdx.x;
+        if (x < nx && y < ny) {
+            const size_t i = zoff + (size_t)y * nx + x;
+            float val;
+            if (q) val = (float)(((double)q[i] + tile[threadIdx.x][j]) * s);
+            else   val = acc[i] + (float)tile[threadIdx.x][j];
+            if (beta != 0.f) val = fmaf(beta, to_f(out[i]), val);
+            out[i] = from_f<T>(val);
+        }
+    }
+}
+
+}  // namespace
+
+ct_status launch_transpose_typed(const ProjGeom &pg, const void *v, void *t, int dt,
+                                 cudaStream_t st) {
+    dim3 gr((pg.nx + kTile - 1) / kTile, (pg.ny + kTile - 1) / kTile, pg.nz), bl(kTile, 8);
+    switch (dt) {
+        case CT_F32:
+            k_transpose_t<float><<<gr, bl, 0, st>>>(pg.nx, pg.ny, (const float *)v, (float *)t);
+            break;
+        case CT_BF16:
+            k_transpose_t<__nv_bfloat16><<<gr, bl, 0, st>>>(
+                pg.nx, pg.ny, (const __nv_bfloat16 *)v, (__nv_bfloat16 *)t);
+            break;
+        case CT_F16:
+            k_transpose_t<__half><<<gr, bl, 0, st>>>(pg.nx, pg.ny, (const __half *)v, (__half *)t);
+            break;
+        default:
+            return set_error(CT_ERR_INVALID_ARG, "unknown dtype");
+    }
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+ct_status launch_combine_typed(const ProjGeom &pg, void *out, int dt, float beta, const float *acc,
+                               const float *acc_t, const long long *q, const double *inv,
+                               cudaStream_t st) {
+    dim3 gr((pg.nx + kTile - 1) / kTile, (pg.ny + kTile - 1) / kTile, pg.nz), bl(kTile, 8);
+    const int64_t n = (int64_t)pg.nx * pg.ny * pg.nz;
+    switch (dt) {
+        case CT_F32:
+            k_combine_t<float><<<gr, bl, 0, st>>>(pg.nx, pg.ny, n, (float *)out, beta, acc, acc_t, q, inv);
+            break;
+        case CT_BF16:
+            k_combine_t<__nv_bfloat16><<<gr, bl, 0, st>>>(pg.nx, pg.ny, n, (__nv_bfloat16 *)out,
+                                                          beta, acc, acc_t, q, inv);
+            break;
+        case CT_F16:
+            k_combine_t<__half><<<gr, bl, 0, st>>>(pg.nx, pg.ny, n, (__half *)out, beta, acc,
+                                                   acc_t, q, inv);
+            break;
+        default:
+            return set_error(CT_ERR_INVALID_ARG, "unknown dtype");
+    }
     CT_CHECK_LAUNCH();
     return CT_OK;
 }
