@@ -40,12 +40,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--iters", type=int, default=10, help="CGLS x updates per step")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="cgls", choices=["cgls", "ops", "serve"],
+    ap.add_argument("--mode", default="cgls", choices=["cgls", "ops", "serve", "precision"],
                     help="ops: time ct_project and ct_backproject alone (profiling aid); "
                          "serve: the continuous-batching request stream alone")
     ap.add_argument("--requests", type=int, default=128, help="serve mode: requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serve mode: arrivals per second")
     ap.add_argument("--slots", type=int, default=8, help="serve mode: concurrent jobs")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
+                    help="serve mode: CGLS Krylov-vector storage")
     ap.add_argument("--serve-requests", type=int, default=32,
                     help="default mode: requests of the served-latency block (0 = skip)")
     ap.add_argument("--workload", default="B256", choices=["B256", "P512"],
@@ -367,7 +369,8 @@ def run_ops(a):
     return 0
 
 
-def serve_stream(n_requests: int, rate: float, slots: int, budget_gb: float = 150.0):
+def serve_stream(n_requests: int, rate: float, slots: int, budget_gb: float = 150.0,
+                 storage: str = "f32"):
     """Serving workload: Poisson arrivals (seed 3), volumes 64..256^3, 60..360
     views, detector scaled to magnification 1.6, CGLS or LSQR to relative
     discrepancy 1e-3 or 50 updates; continuous batching over ``slots``
@@ -388,7 +391,7 @@ def serve_stream(n_requests: int, rate: float, slots: int, budget_gb: float = 15
         x = torch.from_numpy(synth.serving_phantom(s["n"], s["phantom_seed"])).cuda()
         b = ct.project(geoms[key], x)
         reqs.append(Request(s["rid"], cfg, b, s["solver"], s["arrival"], max_iter=50,
-                            err_tol=1e-3))
+                            err_tol=1e-3, storage=storage))
     torch.cuda.synchronize()
     stats = Server(slots=slots, hbm_budget_bytes=budget_gb * 1e9).run(reqs)
     iters = stats.iterations
@@ -398,16 +401,75 @@ def serve_stream(n_requests: int, rate: float, slots: int, budget_gb: float = 15
             "max_concurrent": stats.max_concurrent,
             "max_gb_in_use": stats.max_bytes_in_use / 1e9,
             "mean_iterations": iters / max(len(reqs), 1),
+            "storage": storage,
+            "mean_rel_discrepancy": float(sum(r.rel_discrepancy for r in stats.results)
+                                          / max(len(stats.results), 1)),
             "workload": "Poisson arrivals (seed 3); n in {64,128,192,256}, views in "
                         "{60,120,180,360}, detector 1.5n x 1.125n of 1.6 mm; CGLS/LSQR to "
-                        "1e-3 or 50 updates; 8-ellipsoid phantoms; FP32"}
+                        "1e-3 or 50 updates; 8-ellipsoid phantoms; CGLS Krylov storage "
+                        + storage + " (LSQR FP32)"}
+
+
+def run_precision(a):
+    """The 512^3 precision workload: 0.5 mm voxels, 768x576 detector of
+    0.75 mm pixels, 720 views; 40-ellipsoid phantom (seed 2); Poisson noise at
+    1e5 photons per ray with mu = 0.02 / mm per unit density (seed 2);
+    CGLS with FP32, BF16 and FP16 Krylov storage.  Errors: the reconstruction
+    against the FP32-storage run, and A applied to the phantom stored in each
+    type against the FP64 oracle on 16 sampled views."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2110_13526_gb300 as ct
+    import synth
+
+    torch.cuda.set_device(0)
+    cfg = synth.CONFIGS["P512"]
+    g = ct.Geometry(**cfg)
+    lo, hi = synth.box_of(cfg)
+    x_np = synth.voxelize(synth.random_ellipsoids(40, 2, lo, hi), cfg)
+    x_true = torch.from_numpy(x_np).cuda()
+    mu, i0 = 0.02, 1e5
+    ax = ct.project(g, x_true)
+    gen = torch.Generator(device="cuda").manual_seed(2)
+    counts = torch.poisson(i0 * torch.exp(-mu * ax.double()), generator=gen)
+    b = (-torch.log(torch.clamp(counts, min=1.0) / i0) / mu).float()
+    del counts, ax
+    K = a.iters
+    res = {}
+    xs = {}
+    for st in ("f32", "bf16", "f16"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, rep = ct.cgls(g, b, max_iter=K, storage=st, timing=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        xs[st] = x
+        res[st] = {"s_per_iter": dt / K, "iters_per_s": K / dt,
+                   "ms_A": rep.ms_forward / max(rep.n_forward, 1),
+                   "ms_AT": rep.ms_back / max(rep.n_back, 1),
+                   "rel_discrepancy": rep.history[-1]}
+    for st in ("bf16", "f16"):
+        res[st]["x_rel_l2_vs_f32"] = float((xs[st] - xs["f32"]).norm() / xs["f32"].norm())
+    views = [int(round(k * cfg["nviews"] / 16)) % cfg["nviews"] for k in range(16)]
+    og = oracle.OGeom(**cfg).subset(views)
+    want = oracle.project(og, x_np.astype(np.float64))
+    for st, dt in (("f32", torch.float32), ("bf16", torch.bfloat16), ("f16", torch.float16)):
+        p = ct.project(g, x_true.to(dt), out_dtype=dt)[views].double().cpu().numpy()
+        res[st]["A_rel_l2_vs_oracle_16_views"] = float(np.linalg.norm(p - want)
+                                                       / np.linalg.norm(want))
+    print(json.dumps({"mode": "precision", "workload": "P512: 512^3 (0.5 mm), 768x576 (0.75 mm), "
+                      "720 views, Poisson 1e5 photons/ray, CGLS %d updates" % K,
+                      "results": res}))
+    return 0
 
 
 def run_serve(a):
     import torch
     torch.cuda.set_device(0)
     out = {"mode": "serve"}
-    out.update(serve_stream(a.requests, a.rate, a.slots))
+    out.update(serve_stream(a.requests, a.rate, a.slots, storage=a.storage))
     print(json.dumps(out))
     return 0
 
@@ -420,6 +482,8 @@ def main():
         return run_ops(a)
     if a.mode == "serve":
         return run_serve(a)
+    if a.mode == "precision":
+        return run_precision(a)
     return run_ours(a)
 
 

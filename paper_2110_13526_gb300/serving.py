@@ -35,6 +35,7 @@ class Request:
     arrival: float = 0.0           # seconds after the start of the run
     max_iter: int = 50
     err_tol: float = 1e-3
+    storage: str = "f32"           # CGLS Krylov-vector storage ("f32", "bf16", "f16")
 
 
 @dataclass
@@ -60,7 +61,7 @@ def footprint_bytes(geometry: dict, solver: str) -> int:
     plus per-view and per-column constants and FP64 partial sums."""
     n = geometry["nx"] * geometry["ny"] * geometry["nz"]
     m = geometry["nviews"] * geometry["nu"] * geometry["nv"]
-    vols, sinos = (4, 2) if solver == "cgls" else (5, 1)
+    vols, sinos = (4, 2) if solver == "cgls" else (5, 1)   # FP32 storage (an upper bound)
     cols = geometry["nviews"] * geometry["nu"] * 36 + geometry["nviews"] * 48
     partials = 8 * (m // 256 + n // 1024 + 4096)
     return 4 * (vols * n + sinos * m) + cols + partials
@@ -122,9 +123,13 @@ class Server:
                 torch.cuda.set_device(self.device)
                 s = streams[si]
                 g = self.geometry(req.geometry)
-                fn = cgls if req.solver == "cgls" else lsqr
                 with torch.cuda.stream(s):
-                    x, rep = fn(g, req.b, max_iter=req.max_iter, err_tol=req.err_tol, stream=s)
+                    if req.solver == "cgls":
+                        x, rep = cgls(g, req.b, max_iter=req.max_iter, err_tol=req.err_tol,
+                                      stream=s, storage=req.storage)
+                    else:
+                        x, rep = lsqr(g, req.b, max_iter=req.max_iter, err_tol=req.err_tol,
+                                      stream=s)
                     s.synchronize()
                 t_end = time.perf_counter() - t0
                 res = Result(req.rid, x, rep.iterations, rep.nb / rep.nb0 if rep.nb0 else 0.0,
