@@ -262,6 +262,8 @@ ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out) {
         return set_error(CT_ERR_INVALID_ARG, "volume must hold fewer than 2^31 voxels");
     if (d.nz > 65535 || d.nviews > 65535)
         return set_error(CT_ERR_INVALID_ARG, "nz and nviews must be <= 65535");
+    if (d.nv > 65535 * 8)
+        return set_error(CT_ERR_INVALID_ARG, "nv must be <= 524280");
     if ((int64_t)d.nx * d.ny >= (int64_t(1) << 31))
         return set_error(CT_ERR_INVALID_ARG, "nx * ny too large");
     if (d.nviews > 0 && d.angles_rad) {
@@ -345,6 +347,7 @@ ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out) {
     g->pg.nx = d.nx; g->pg.ny = d.ny; g->pg.nz = d.nz;
     g->pg.nu = d.nu; g->pg.nv = d.nv; g->pg.nviews = d.nviews;
     g->pg.hx = (float)d.vx; g->pg.hy = (float)d.vy; g->pg.hz = (float)d.vz;
+    set_launch_order(g->pg);
     *out = g;
     return CT_OK;
 }

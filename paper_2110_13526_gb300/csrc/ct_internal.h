@@ -48,7 +48,14 @@ struct ProjGeom {
     int nx, ny, nz;
     int nu, nv, nviews;
     float hx, hy, hz;        // voxel pitch, mm
+    int vgroup;              // launch order of A: views per group (set_launch_order)
+    int vgroup_bt;           // launch order of A^T
+    int nvb;                 // row blocks of the projector grid
 };
+
+// Choose the order in which the projector kernels visit (view, row block)
+// tiles; call once the sizes of pg are set.
+void set_launch_order(ProjGeom &pg);
 
 }  // namespace ct
 

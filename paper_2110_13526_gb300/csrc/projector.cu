@@ -31,6 +31,7 @@
 // rays advancing along x, which therefore read a transposed copy laid out
 // [z][x][y] (y fastest).  Either way the warp's gathers (and the
 // backprojector's atomics) fall on one or two 128-byte lines.
+#include <algorithm>
 #include <climits>
 #include <type_traits>
 
@@ -42,6 +43,11 @@ namespace {
 
 constexpr int kTU = 32;  // detector columns per CTA (one warp row)
 constexpr int kTV = 8;   // detector rows per CTA
+// Launch order (set_launch_order): views visited together by A and by A^T
+// when the volume and its transposed copy take more than kL2GroupBytes.
+constexpr int64_t kL2GroupBytes = int64_t(160) << 20;
+constexpr int kWideGroupFwd = 65535;
+constexpr int kWideGroupBack = 16;
 
 struct Ray {
     int soff0 = 0, sstep = 0;   // memory offset of walk slab k: soff0 + k * sstep + i + j * bstride
@@ -288,6 +294,17 @@ __device__ __forceinline__ double block_sum_d(double x, double *sh) {
     return t;  // valid in thread (0, 0)
 }
 
+// The rays of this thread.  CTA (bx, by, bz) covers columns 32 bx .. 32 bx + 31
+// and rows 8 vb .. 8 vb + 7 of view grp * vgroup + by, where bz = grp * nvb + vb
+// (proj_grid).  The last group may run past the last view (view >= nviews).
+__device__ __forceinline__ void tile_of(const ProjGeom &g, int &u, int &v, int &view) {
+    const int grp = (int)blockIdx.z / g.nvb;
+    const int vb = (int)blockIdx.z - grp * g.nvb;
+    u = blockIdx.x * kTU + threadIdx.x;
+    v = vb * kTV + threadIdx.y;
+    view = grp * g.vgroup + (int)blockIdx.y;
+}
+
 __device__ __forceinline__ void coef_of(const Coef &c, float &alpha, float &beta) {
     if (c.dev) {
         alpha = (float)c.dev[0];
@@ -306,10 +323,9 @@ __global__ void __launch_bounds__(kTU *kTV, 6) k_forward(ProjGeom g, const TV *_
                                                       const float *__restrict__ rho, Coef c,
                                                       double *__restrict__ partials) {
     __shared__ double sh[32];
-    const int u = blockIdx.x * kTU + threadIdx.x;
-    const int v = blockIdx.y * kTV + threadIdx.y;
-    const int view = blockIdx.z;
-    const bool inb = (u < g.nu) && (v < g.nv);
+    int u, v, view;
+    tile_of(g, u, v, view);
+    const bool inb = (u < g.nu) && (v < g.nv) && (view < g.nviews);
     Ray r;
     const bool valid = inb && ray_setup(g, view, u, v, r);
     const TV *base = r.transposed ? vol_t : vol;
@@ -353,10 +369,9 @@ __global__ void __launch_bounds__(kTU *kTV, 6) k_backward(ProjGeom g, const TS *
                                                        void *__restrict__ acc,
                                                        void *__restrict__ acc_t,
                                                        const float *__restrict__ det_scale) {
-    const int u = blockIdx.x * kTU + threadIdx.x;
-    const int v = blockIdx.y * kTV + threadIdx.y;
-    const int view = blockIdx.z;
-    const bool inb = (u < g.nu) && (v < g.nv);
+    int u, v, view;
+    tile_of(g, u, v, view);
+    const bool inb = (u < g.nu) && (v < g.nv) && (view < g.nviews);
     Ray r;
     bool valid = inb && ray_setup(g, view, u, v, r);
     float alpha, beta;
@@ -391,10 +406,9 @@ __global__ void __launch_bounds__(kTU *kTV, 6) k_backward(ProjGeom g, const TS *
 __global__ void __launch_bounds__(kTU *kTV) k_count(ProjGeom g,
                                                     unsigned long long *__restrict__ count) {
     __shared__ double sh[32];
-    const int u = blockIdx.x * kTU + threadIdx.x;
-    const int v = blockIdx.y * kTV + threadIdx.y;
-    const int view = blockIdx.z;
-    const bool inb = (u < g.nu) && (v < g.nv);
+    int u, v, view;
+    tile_of(g, u, v, view);
+    const bool inb = (u < g.nu) && (v < g.nv) && (view < g.nviews);
     Ray r;
     const bool valid = inb && ray_setup(g, view, u, v, r);
     int n = 0;
@@ -414,10 +428,9 @@ __global__ void __launch_bounds__(kTU *kTV) k_forward_direct(ProjGeom g,
                                                              float beta,
                                                              double *__restrict__ partials) {
     __shared__ double sh[32];
-    const int u = blockIdx.x * kTU + threadIdx.x;
-    const int v = blockIdx.y * kTV + threadIdx.y;
-    const int view = blockIdx.z;
-    const bool inb = (u < g.nu) && (v < g.nv);
+    int u, v, view;
+    tile_of(g, u, v, view);
+    const bool inb = (u < g.nu) && (v < g.nv) && (view < g.nviews);
     Ray r;
     const bool valid = inb && ray_setup(g, view, u, v, r);
     const int nxy = g.nx * g.ny;
@@ -448,13 +461,46 @@ __global__ void __launch_bounds__(kTU *kTV) k_forward_direct(ProjGeom g,
 }
 
 dim3 proj_grid(const ProjGeom &pg) {
-    return dim3((unsigned)((pg.nu + kTU - 1) / kTU), (unsigned)((pg.nv + kTV - 1) / kTV),
-                (unsigned)pg.nviews);
+    const int ngroups = (pg.nviews + pg.vgroup - 1) / pg.vgroup;
+    return dim3((unsigned)((pg.nu + kTU - 1) / kTU), (unsigned)pg.vgroup,
+                (unsigned)(pg.nvb * ngroups));
+}
+
+// The same geometry with the launch order of A^T.
+ProjGeom back_order(const ProjGeom &pg) {
+    ProjGeom pb = pg;
+    pb.vgroup = pg.vgroup_bt;
+    return pb;
 }
 
 bool empty(const ProjGeom &pg) { return pg.nu <= 0 || pg.nv <= 0 || pg.nviews <= 0; }
 
 }  // namespace
+
+// CTAs are issued roughly in linear order, x fastest, so the tiles in flight
+// at a time are all columns of vgroup views for a few row blocks, then the
+// next row blocks of the same views.  vgroup = 1 visits a view at a time: its
+// rays are nearly disjoint (few reductions into the same voxel at once) but
+// every view sweeps the whole volume.  A large vgroup keeps the CTAs in flight
+// on a band of z slices (the rows of a few row blocks) of the volume for all
+// views of the group: for a volume that does not fit in L2 (512^3 FP32 plus
+// its transposed copy: 1 GB) that band stays resident, which takes fewer DRAM
+// reads and, in A^T, fewer L2 misses of the reductions.  Measured on 512^3
+// with 720 views: A 229 ms with one view at a time, 139 ms with all views in
+// one group; A^T 165 ms and 93 ms with groups of 16 (more views at once put
+// more reductions on the same voxels at the same time).  On 256^3 (2 x 64 MB)
+// one view at a time is best for both.
+void set_launch_order(ProjGeom &pg) {
+    pg.nvb = std::max(1, (pg.nv + kTV - 1) / kTV);
+    const int64_t vol_bytes = 2 * (int64_t)pg.nx * pg.ny * pg.nz * (int64_t)sizeof(float);
+    const bool wide = vol_bytes > kL2GroupBytes;
+    // grid z = nvb * ceil(nviews / vgroup) must stay <= 65535
+    const int max_groups = std::max(1, 65535 / pg.nvb);
+    const int need = (pg.nviews + max_groups - 1) / max_groups;
+    auto clampg = [&](int g) { return std::max(1, std::min(std::max(g, need), std::max(pg.nviews, 1))); };
+    pg.vgroup = clampg(wide ? kWideGroupFwd : 1);
+    pg.vgroup_bt = clampg(wide ? kWideGroupBack : 1);
+}
 
 int64_t forward_partials(const ProjGeom &pg) {
     if (empty(pg)) return 0;
@@ -516,11 +562,12 @@ ct_status fwd_typed_s(const ProjGeom &pg, const void *vol, const void *vol_t, vo
 template <class TS>
 ct_status back_typed(const ProjGeom &pg, const void *e, const float *rho, Coef c, void *acc,
                      void *acc_t, int power, bool det, const float *det_scale, cudaStream_t st) {
-    dim3 gr = proj_grid(pg), bl(kTU, kTV);
+    const ProjGeom pb = back_order(pg);
+    dim3 gr = proj_grid(pb), bl(kTU, kTV);
     const TS *et = static_cast<const TS *>(e);
     const bool hr = rho != nullptr;
 #define CT_BWD(HR, P, D) \
-    k_backward<HR, P, D, TS><<<gr, bl, 0, st>>>(pg, et, rho, c, acc, acc_t, det_scale)
+    k_backward<HR, P, D, TS><<<gr, bl, 0, st>>>(pb, et, rho, c, acc, acc_t, det_scale)
     if (det) {
         if (power == 2) { if (hr) CT_BWD(true, 2, true); else CT_BWD(false, 2, true); }
         else            { if (hr) CT_BWD(true, 1, true); else CT_BWD(false, 1, true); }
@@ -566,14 +613,15 @@ ct_status launch_backward_typed(const ProjGeom &pg, const void *e, int sdt, cons
 ct_status launch_backward(const ProjGeom &pg, const float *e, const float *rho, Coef c,
                           float *acc, float *acc_t, int power, cudaStream_t st) {
     if (empty(pg)) return CT_OK;
-    dim3 gr = proj_grid(pg), bl(kTU, kTV);
+    const ProjGeom pb = back_order(pg);
+    dim3 gr = proj_grid(pb), bl(kTU, kTV);
     const bool hr = (rho != nullptr);
     if (power == 2) {
-        if (hr) k_backward<true, 2, false><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t, nullptr);
-        else    k_backward<false, 2, false><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t, nullptr);
+        if (hr) k_backward<true, 2, false><<<gr, bl, 0, st>>>(pb, e, rho, c, acc, acc_t, nullptr);
+        else    k_backward<false, 2, false><<<gr, bl, 0, st>>>(pb, e, rho, c, acc, acc_t, nullptr);
     } else {
-        if (hr) k_backward<true, 1, false><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t, nullptr);
-        else    k_backward<false, 1, false><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t, nullptr);
+        if (hr) k_backward<true, 1, false><<<gr, bl, 0, st>>>(pb, e, rho, c, acc, acc_t, nullptr);
+        else    k_backward<false, 1, false><<<gr, bl, 0, st>>>(pb, e, rho, c, acc, acc_t, nullptr);
     }
     CT_CHECK_LAUNCH();
     return CT_OK;
@@ -583,14 +631,15 @@ ct_status launch_backward_det(const ProjGeom &pg, const float *e, const float *r
                               long long *acc, long long *acc_t, int power,
                               const float *det_scale, cudaStream_t st) {
     if (empty(pg)) return CT_OK;
-    dim3 gr = proj_grid(pg), bl(kTU, kTV);
+    const ProjGeom pb = back_order(pg);
+    dim3 gr = proj_grid(pb), bl(kTU, kTV);
     const bool hr = (rho != nullptr);
     if (power == 2) {
-        if (hr) k_backward<true, 2, true><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t, det_scale);
-        else    k_backward<false, 2, true><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t, det_scale);
+        if (hr) k_backward<true, 2, true><<<gr, bl, 0, st>>>(pb, e, rho, c, acc, acc_t, det_scale);
+        else    k_backward<false, 2, true><<<gr, bl, 0, st>>>(pb, e, rho, c, acc, acc_t, det_scale);
     } else {
-        if (hr) k_backward<true, 1, true><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t, det_scale);
-        else    k_backward<false, 1, true><<<gr, bl, 0, st>>>(pg, e, rho, c, acc, acc_t, det_scale);
+        if (hr) k_backward<true, 1, true><<<gr, bl, 0, st>>>(pb, e, rho, c, acc, acc_t, det_scale);
+        else    k_backward<false, 1, true><<<gr, bl, 0, st>>>(pb, e, rho, c, acc, acc_t, det_scale);
     }
     CT_CHECK_LAUNCH();
     return CT_OK;

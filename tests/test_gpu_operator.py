@@ -129,6 +129,46 @@ def test_b256_sampled_views(ct):
     assert rel(r, oracle.backproject(og, ys.astype(np.float64))) < TOL
 
 
+# Launch orders of the projector grid.  "wide": the volume and its transposed
+# copy take more than 160 MB, so A visits all 20 views together and A^T groups
+# of 16 (one full group and one of 4 with 12 idle views).  "tall": 4097 row
+# blocks leave room for 15 view groups in the grid's 65535 z blocks, so the 23
+# views go in groups of 2 (the last one holding a single view).
+ORDER_CASES = {
+    "wide": dict(nx=256, ny=256, nz=400, vx=1.0, vy=1.0, vz=1.0, nu=64, nv=48, du=8.0,
+                 dv=14.0, sid=750.0, sdd=1200.0, nviews=20),
+    "tall": dict(nx=12, ny=10, nz=9, vx=1.0, vy=1.0, vz=1.0, nu=3, nv=8 * 4096 + 5, du=8.0,
+                 dv=0.0005, sid=100.0, sdd=160.0, nviews=23),
+}
+
+
+@pytest.mark.parametrize("name", sorted(ORDER_CASES))
+def test_launch_orders(ct, name):
+    cfg = ORDER_CASES[name]
+    g, og = ct.Geometry(**cfg), oracle.OGeom(**cfg)
+    # non-negative, like attenuation: a signed field summed along rays of up
+    # to 500 voxels cancels to a small fraction of its terms, which would
+    # magnify the FP32 rounding of the sums beyond the parity bar
+    x = np.abs(synth.random_field(g.vol_shape, seed=40))
+    p = ct.project(g, torch.from_numpy(x).cuda()).cpu().numpy()
+    want = oracle.project(og, x.astype(np.float64))
+    assert np.count_nonzero(want) > 0.5 * want.size
+    assert rel(p, want) < TOL
+    y = synth.random_field(g.sino_shape, seed=41)
+    r = ct.backproject(g, torch.from_numpy(y).cuda()).cpu().numpy()
+    # A crossing position |c| voxels from the volume centre is rounded by up to
+    # 2^-24 |c| in FP32.  Along a ray the length errors telescope (adjacent
+    # segments share a crossing), but a voxel of A^T sums segments of unrelated
+    # rays, so its relative error is that of a segment length, about
+    # 2 * 2^-24 * (N / 2) for a unit segment: 2.4e-5 at z = +-200 here.
+    tol_bt = max(TOL, 2.0 * 2.0 ** -24 * max(cfg["nx"], cfg["ny"], cfg["nz"]) / 2)
+    assert rel(r, oracle.backproject(og, y.astype(np.float64))) < tol_bt
+    # the norm partials (one per CTA, idle CTAs included) sum to ||A x||^2
+    xs = torch.from_numpy(x).cuda()
+    _, n2 = ct.project_norm2(g, xs)
+    assert float(n2) == pytest.approx(float((want ** 2).sum()), rel=2 * TOL)
+
+
 def test_count_nnz_matches_oracle(ct):
     """Counts agree to 1e-3: a segment shorter than the FP32 resolution of a
     crossing position (about 1e-5 voxel) may be counted on one side only."""
@@ -163,6 +203,16 @@ def test_empty_and_missing(ct):
     g2 = ct.Geometry(nx=4, ny=4, nz=4, vx=1, vy=1, vz=1, nu=6, nv=6, du=0.1, dv=0.1, sid=50,
                      sdd=80, nviews=3, oz=30.0)
     assert float(ct.project(g2, v).abs().sum()) == 0.0
+
+
+@pytest.mark.parametrize("bad", [dict(nv=65535 * 8 + 1), dict(nviews=65536), dict(nz=65536),
+                                 dict(sdd=40.0), dict(du=0.0)])
+def test_geometry_limits_rejected(ct, bad):
+    cfg = dict(nx=4, ny=4, nz=4, vx=1, vy=1, vz=1, nu=8, nv=8, du=1, dv=1, sid=50, sdd=80,
+               nviews=2)
+    cfg.update(bad)
+    with pytest.raises(RuntimeError, match="CT_ERR_INVALID_ARG"):
+        ct.Geometry(**cfg)
 
 
 def test_host_tensors_round_trip(ct):
