@@ -347,6 +347,23 @@ ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out) {
     g->pg.nx = d.nx; g->pg.ny = d.ny; g->pg.nz = d.nz;
     g->pg.nu = d.nu; g->pg.nv = d.nv; g->pg.nviews = d.nviews;
     g->pg.hx = (float)d.vx; g->pg.hy = (float)d.vy; g->pg.hz = (float)d.vz;
+    // Column-major kernels unless some ray advances mostly along z.  The
+    // kernels compute C = fmaf(vc, C1, C0) in FP32 with vc = v - (nv - 1) / 2
+    // exact; fmaf is correctly rounded, hence monotone in vc, so the largest
+    // |C| of a column is at its first or last row and the test below is the
+    // kernels' own, bit for bit.
+    g->pg.cm = 1;
+    if (d.nv > 0) {
+        const float vlo = -0.5f * (float)(d.nv - 1), vhi = 0.5f * (float)(d.nv - 1);
+        for (size_t i = 0; i < ncol; ++i) {
+            const float c0 = std::fmaf(vlo, cola[i].w, cola[i].z);
+            const float c1 = std::fmaf(vhi, cola[i].w, cola[i].z);
+            if (!(std::fabs(c0) <= 1.f && std::fabs(c1) <= 1.f)) {
+                g->pg.cm = 0;
+                break;
+            }
+        }
+    }
     set_launch_order(g->pg);
     *out = g;
     return CT_OK;

@@ -48,6 +48,8 @@ struct ProjGeom {
     int nx, ny, nz;
     int nu, nv, nviews;
     float hx, hy, hz;        // voxel pitch, mm
+    int cm;                  // 1: column-major kernels and the [y][x][z] volume copy
+                             // (no ray advances mostly along z), 0: ray-major, [z][x][y]
     int vgroup;              // launch order of A: views per group (set_launch_order)
     int vgroup_bt;           // launch order of A^T
     int nvb;                 // row blocks of the projector grid
@@ -130,6 +132,8 @@ struct Coef {
 
 // Number of FP64 norm partials a forward launch writes (one per CTA).
 int64_t forward_partials(const ProjGeom &pg);
+// The same for launch_forward_direct (one ray per thread, ray-major grid).
+int64_t forward_direct_partials(const ProjGeom &pg);
 
 // p = alpha * rho o (A vol) + beta * p.  vol_t is the same volume in the
 // transposed layout [nz][nx][ny] (used by rays that advance mostly along x).
@@ -174,7 +178,7 @@ ct_status launch_combine_det(const ProjGeom &pg, float *out, float beta, const l
                              double *partials, cudaStream_t st);
 
 // p = alpha * A vol + beta * p reading vol in place (no transposed copy),
-// with forward_partials(pg) FP64 partial sums of p^2.
+// with forward_direct_partials(pg) FP64 partial sums of p^2.
 ct_status launch_forward_direct(const ProjGeom &pg, const float *vol, float *p, float alpha,
                                 float beta, double *partials, cudaStream_t st);
 

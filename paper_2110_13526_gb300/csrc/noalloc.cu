@@ -61,7 +61,7 @@ extern "C" ct_status ct_project_norm2_noalloc(const ct_geometry *g, const float 
         return CT_OK;
     }
     if (!d_vol || !d_sino) return set_error(CT_ERR_INVALID_ARG, "NULL vector");
-    const int64_t np = forward_partials(g->pg);
+    const int64_t np = forward_direct_partials(g->pg);
     if (np > kNoAllocMaxPartials)
         return set_error(CT_ERR_INVALID_ARG,
                          "ct_project_norm2_noalloc: geometry needs " + std::to_string(np) +

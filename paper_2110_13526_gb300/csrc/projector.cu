@@ -41,8 +41,10 @@
 namespace ct {
 namespace {
 
-constexpr int kTU = 32;  // detector columns per CTA (one warp row)
+constexpr int kTU = 32;  // ray-major tile: detector columns per CTA (one warp row)
 constexpr int kTV = 8;   // detector rows per CTA
+constexpr int kCU = 8;   // column-major tile: detector columns per CTA (one per warp)
+constexpr int kCV = 32;  // detector rows per CTA (one per lane)
 // Launch order (set_launch_order): views visited together by A and by A^T
 // when the volume and its transposed copy take more than kL2GroupBytes.
 constexpr int64_t kL2GroupBytes = int64_t(160) << 20;
@@ -460,10 +462,309 @@ __global__ void __launch_bounds__(kTU *kTV) k_forward_direct(ProjGeom g,
         partials[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = t;
 }
 
+// ---- column-major kernels ---------------------------------------------------
+// The rays of one detector column share their projection onto the xy plane:
+// slab axis, direction, lateral slope A and lateral plane crossings depend on
+// the column only; the detector row changes only the z part (C, ze0).  In the
+// column-major kernels the 32 lanes of a warp are 32 consecutive rows v of
+// one column u, so the in-plane walk (slab bounds, lateral crossings) is the
+// same in every lane and its branch is warp-uniform; only the z crossing is
+// per lane.  The volume is read from (and A^T accumulates into) a copy laid
+// out [y][x][z], z fastest, in which the lanes of a warp, about one z row
+// apart, touch consecutive words whichever axis the column advances along.
+// A slab costs two gathers per lane (the second only where the lane crosses
+// a z plane) plus one where the column crosses a lateral plane, with no vote
+// and no per-lane lateral state.  Rays advancing mostly along z (|C| > 1) do
+// not fit this scheme; geometries that have any use the ray-major kernels
+// above instead (ProjGeom::cm).
+
+__device__ __forceinline__ void tile_of_cm(const ProjGeom &g, int &u, int &v, int &view) {
+    const int grp = (int)blockIdx.z / g.nvb;
+    const int vb = (int)blockIdx.z - grp * g.nvb;
+    u = blockIdx.x * kCU + threadIdx.y;
+    v = vb * kCV + threadIdx.x;
+    view = grp * g.vgroup + (int)blockIdx.y;
+}
+
+// One warp's column (the same in all lanes) and one lane's row of it.
+struct CmRay {
+    float lo = 0.f, hi = 0.f;        // w range of the column inside the volume's xy extent
+    float A = 0.f, xi0 = 0.f, invA = 0.f;
+    int Ns = 0, Na = 0, Nb = 0, cs = 0, ca = 0, cb = 0;
+    int sstride = 0, astride = 0;    // [y][x][z] strides of the slab and lateral axes
+    bool rev = false;                // walk runs towards decreasing slab index
+    float C = 0.f, ze0 = 0.f, invC = 0.f;
+    float w_in = 0.f, w_out = 0.f;   // w range of this lane's ray inside the volume
+    int k_first = INT_MAX, k_last = -1;
+    float lsig = 0.f;                // mm of ray per unit w
+};
+
+// Set up ray (u, v) of a column-major warp; returns whether it crosses the
+// volume.  col_live (u and view in range) must be warp-uniform.  The clip is
+// the one of ray_clip, so a ray's w range is the same as in the ray-major
+// kernels.
+__device__ __forceinline__ bool cm_setup(const ProjGeom &g, int view, int u, int v, bool col_live,
+                                         CmRay &r) {
+    if (!col_live) return false;
+    const size_t ci = (size_t)view * g.nu + u;
+    const float4 pa = __ldg(g.col_a + ci);
+    const float4 pb = __ldg(g.col_b + ci);
+    const int fl = __ldg(g.col_flags + ci);
+    float hs, ha;
+    if (fl & 1) {      // slabs along x, lateral y
+        r.Ns = g.nx; r.Na = g.ny; r.sstride = g.nz; r.astride = g.nx * g.nz; hs = g.hx; ha = g.hy;
+    } else {           // slabs along y, lateral x
+        r.Ns = g.ny; r.Na = g.nx; r.sstride = g.nx * g.nz; r.astride = g.nz; hs = g.hy; ha = g.hx;
+    }
+    r.Nb = g.nz;
+    r.rev = (fl & 2) != 0;
+    r.cs = r.Ns / 2;
+    r.ca = r.Na / 2;
+    r.cb = r.Nb / 2;
+    r.A = pa.x;
+    r.xi0 = pa.y;
+    r.invA = 1.f / r.A;
+    bool ok = true;
+    float lo = fmaxf((float)(-r.cs), pb.z), hi = fminf((float)(r.Ns - r.cs), pb.w);
+    if (r.A != 0.f) {
+        const float t0 = ((float)(-r.ca) - r.xi0) * r.invA;
+        const float t1 = ((float)(r.Na - r.ca) - r.xi0) * r.invA;
+        lo = fmaxf(lo, fminf(t0, t1));
+        hi = fminf(hi, fmaxf(t0, t1));
+    } else if (!(r.xi0 >= (float)(-r.ca) && r.xi0 < (float)(r.Na - r.ca))) {
+        ok = false;
+    }
+    r.lo = lo;
+    r.hi = hi;
+    const float vc = (float)v - 0.5f * (float)(g.nv - 1);
+    r.C = fmaf(vc, pa.w, pa.z);
+    r.ze0 = fmaf(vc, pb.y, pb.x);
+    r.invC = 1.f / r.C;
+    ok = ok && (v < g.nv) && fabsf(r.C) <= 1.f;
+    float w_in = lo, w_out = hi;
+    if (r.C != 0.f) {
+        const float t0 = ((float)(-r.cb) - r.ze0) * r.invC;
+        const float t1 = ((float)(r.Nb - r.cb) - r.ze0) * r.invC;
+        w_in = fmaxf(w_in, fminf(t0, t1));
+        w_out = fminf(w_out, fmaxf(t0, t1));
+    } else if (!(r.ze0 >= (float)(-r.cb) && r.ze0 < (float)(r.Nb - r.cb))) {
+        ok = false;
+    }
+    ok = ok && (w_in < w_out);
+    r.k_first = max(0, (int)floorf(w_in) + r.cs);
+    r.k_last = min(r.Ns - 1, (int)ceilf(w_out) - 1 + r.cs);
+    ok = ok && (r.k_first <= r.k_last);
+    r.w_in = ok ? w_in : 0.f;   // an empty range clips every length to zero
+    r.w_out = ok ? w_out : 0.f;
+    const float la = r.A * (ha / hs), lb = r.C * (g.hz / hs);
+    r.lsig = hs * sqrtf(fmaf(la, la, fmaf(lb, lb, 1.f)));
+    return ok;
+}
+
+// Column-major slab walk; fn(offset, w_length, p) with the contract of
+// walk().  Must be called by all 32 lanes of the warp, which hold rows of one
+// column.
+//
+// The slab bounds and the lateral crossing come from warp-uniform values, so
+// they are equal in all lanes.  Per lane a slab holds the current voxel, the
+// voxel after the lane's z crossing (if it crosses) and, when the column
+// crosses a lateral plane, one more.  In the entry and exit slabs (and in
+// every slab of a warp where some lane has no ray) each length is clipped to
+// the lane's own range and a voxel is touched only if its clipped length is
+// positive: outside its range a lane's z index may leave the volume.  The
+// interior slabs, inside every lane's range, skip the clip.
+template <class Fn>
+__device__ __forceinline__ void walk_cm(const CmRay &r, bool ok, Fn &&fn) {
+    const unsigned full = 0xffffffffu;
+    const int kb = __reduce_min_sync(full, ok ? r.k_first : INT_MAX);
+    const int ke = __reduce_max_sync(full, ok ? r.k_last : -1);
+    if (kb > ke) return;
+    int k_mid0 = __reduce_max_sync(full, ok ? r.k_first : INT_MAX) + 1;
+    int k_mid1 = __reduce_min_sync(full, ok ? r.k_last : -1) - 1;
+    if (!__all_sync(full, ok) || k_mid0 > k_mid1) {
+        k_mid0 = ke + 1;
+        k_mid1 = ke;
+    }
+    const float lo = r.lo, hi = r.hi, w_in = r.w_in, w_out = r.w_out;
+    // lateral state at the start of the warp's first slab (uniform)
+    const float w_s = fminf(fmaxf((float)(kb - r.cs), lo), hi);
+    const float fi = fminf(fmaxf(floorf(fmaf(w_s, r.A, r.xi0)), (float)(-r.ca)),
+                           (float)(r.Na - 1 - r.ca));
+    const bool neg_a = r.A < 0.f;
+    const float sa = neg_a ? -1.f : 1.f;
+    const int astep = neg_a ? -r.astride : r.astride;
+    const float xi0 = r.xi0, invA = r.invA;
+    float px = neg_a ? fi : fi + 1.f;
+    float w_nx = (r.A != 0.f) ? (px - xi0) * invA : INFINITY;
+    const int sstep = r.rev ? -r.sstride : r.sstride;
+    int off = (r.rev ? (r.Ns - 1) * r.sstride : 0) + kb * sstep + ((int)fi + r.ca) * r.astride;
+    // this lane's z state; before its entry the index is clamped into the
+    // volume, and the next plane in the direction of travel then lies after
+    // the entry point
+    const float fk = fminf(fmaxf(floorf(fmaf(w_s, r.C, r.ze0)), (float)(-r.cb)),
+                           (float)(r.Nb - 1 - r.cb));
+    const bool neg_b = r.C < 0.f;
+    const float sb = neg_b ? -1.f : 1.f;
+    const int dz = neg_b ? -1 : 1;
+    const float ze0 = r.ze0, invC = r.invC;
+    float pz = neg_b ? fk : fk + 1.f;
+    float w_nz = (ok && r.C != 0.f) ? (pz - ze0) * invC : INFINITY;
+    int zo = ok ? (int)fk + r.cb : 0;
+    float wk = (float)(kb - r.cs);
+    float w_lo = w_s;
+    auto slab = [&](auto clamp) {
+        constexpr bool CL = decltype(clamp)::value;
+        wk += 1.f;
+        const float w_hi = CL ? fminf(fmaxf(wk, lo), hi) : wk;
+        const bool cz = w_nz < w_hi;
+        const float sz = fminf(w_nz, w_hi);
+        // clipped length of [a, b]
+        auto len = [&](float a, float b) {
+            return CL ? fminf(fmaxf(b, w_in), w_out) - fminf(fmaxf(a, w_in), w_out) : b - a;
+        };
+        const int o = off + zo;
+        if (!(w_nx < w_hi)) {   // no lateral crossing (warp-uniform)
+            const float l1 = len(w_lo, sz), l2 = len(sz, w_hi);
+            fn(o, l1, CL ? l1 > 0.f : true);
+            fn(o + dz, l2, CL ? l2 > 0.f : cz);
+        } else {
+            const float sx = w_nx;
+            const float s1 = fminf(sx, sz), s2 = fmaxf(sx, sz);
+            const float l1 = len(w_lo, s1), l2 = len(s1, s2), l3 = len(s2, w_hi);
+            fn(o, l1, CL ? l1 > 0.f : true);
+            fn(o + (sx <= sz ? astep : dz), l2, CL ? l2 > 0.f : true);
+            fn(o + astep + (cz ? dz : 0), l3, CL ? l3 > 0.f : cz);
+            off += astep;
+            px += sa;
+            w_nx = (px - xi0) * invA;
+        }
+        if (cz) {
+            zo += dz;
+            pz += sb;
+            w_nz = (pz - ze0) * invC;
+        }
+        off += sstep;
+        w_lo = w_hi;
+    };
+    using clamped = std::integral_constant<bool, true>;
+    using interior = std::integral_constant<bool, false>;
+    int k = kb;
+    for (; k < k_mid0; ++k) slab(clamped{});
+#pragma unroll 2
+    for (; k <= k_mid1; ++k) slab(interior{});
+    for (; k <= ke; ++k) slab(clamped{});
+}
+
+// p = alpha * rho o (A vol) + beta * p from the [y][x][z] copy vol_z (NULL:
+// the all-ones volume).
+template <bool HAS_RHO, bool NORM, bool UNIT_VOL, class TV = float, class TS = float>
+__global__ void __launch_bounds__(kCU *kCV, 5) k_forward_cm(ProjGeom g,
+                                                         const TV *__restrict__ vol_z,
+                                                         TS *__restrict__ out,
+                                                         const float *__restrict__ rho, Coef c,
+                                                         double *__restrict__ partials) {
+    __shared__ double sh[32];
+    int u, v, view;
+    tile_of_cm(g, u, v, view);
+    const bool col_live = (u < g.nu) && (view < g.nviews);
+    CmRay r;
+    const bool ok = cm_setup(g, view, u, v, col_live, r);
+    float acc = 0.f;
+    if (col_live) {
+        walk_cm(r, ok, [&](int o, float l, bool p) {
+            float val = 0.f;
+            if (p) val = UNIT_VOL ? 1.f : ld_f(vol_z + o);
+            acc = fmaf(l, val, acc);
+        });
+    }
+    float alpha, beta;
+    coef_of(c, alpha, beta);
+    double sq = 0.0;
+    if (col_live && v < g.nv) {
+        const size_t idx = ((size_t)view * g.nv + v) * g.nu + u;
+        float val = ok ? acc * r.lsig : 0.f;
+        if (HAS_RHO) val *= rho[idx];
+        float o = alpha * val;
+        if (beta != 0.f) o = fmaf(beta, to_f(out[idx]), o);
+        const TS st = from_f<TS>(o);
+        out[idx] = st;
+        if (NORM) {
+            const double q = (double)to_f(st);  // the norm of what is stored
+            sq = q * q;
+        }
+    }
+    if (NORM) {
+        double t = block_sum_d(sq, sh);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            partials[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = t;
+    }
+}
+
+// acc_z ([y][x][z]) += the k_backward contributions of the column-major rays.
+template <bool HAS_RHO, int POWER, bool DET, class TS = float>
+__global__ void __launch_bounds__(kCU *kCV, 5) k_backward_cm(ProjGeom g,
+                                                          const TS *__restrict__ e,
+                                                          const float *__restrict__ rho, Coef c,
+                                                          void *__restrict__ acc_z,
+                                                          const float *__restrict__ det_scale) {
+    int u, v, view;
+    tile_of_cm(g, u, v, view);
+    const bool col_live = (u < g.nu) && (view < g.nviews);
+    if (!col_live) return;   // warp-uniform; no CTA-wide synchronisation follows
+    CmRay r;
+    const bool ok = cm_setup(g, view, u, v, col_live, r);
+    float alpha, beta;
+    coef_of(c, alpha, beta);
+    float w = 0.f;
+    if (ok) {
+        const size_t idx = ((size_t)view * g.nv + v) * g.nu + u;
+        w = alpha * (e ? to_f(e[idx]) : 1.f);
+        if (HAS_RHO) w *= rho[idx];
+        if (POWER == 1) w *= r.lsig;
+    }
+    const bool nz = (w != 0.f);
+    const float ls = r.lsig;
+    if constexpr (DET) {
+        const float scale = __ldg(det_scale);
+        unsigned long long *base = static_cast<unsigned long long *>(acc_z);
+        walk_cm(r, ok, [&](int o, float l, bool p) {
+            const float lm = l * ls;
+            const float val = POWER == 1 ? w * l : w * lm * lm;
+            red_add_u64_if(base + o, __float2ll_rn(val * scale), p && nz);
+        });
+    } else {
+        float *base = static_cast<float *>(acc_z);
+        walk_cm(r, ok, [&](int o, float l, bool p) {
+            const float lm = l * ls;
+            red_add_if(base + o, POWER == 1 ? w * l : w * lm * lm, p && nz);
+        });
+    }
+}
+
+// Grid of the projector kernels (column-major tiles when pg.cm, else
+// ray-major ones); see set_launch_order for the order.
 dim3 proj_grid(const ProjGeom &pg) {
     const int ngroups = (pg.nviews + pg.vgroup - 1) / pg.vgroup;
-    return dim3((unsigned)((pg.nu + kTU - 1) / kTU), (unsigned)pg.vgroup,
+    const int tu = pg.cm ? kCU : kTU;
+    return dim3((unsigned)((pg.nu + tu - 1) / tu), (unsigned)pg.vgroup,
                 (unsigned)(pg.nvb * ngroups));
+}
+
+// View groups that keep grid z = nvb * ceil(nviews / vgroup) <= 65535.
+int min_view_group(int nviews, int nvb) {
+    const int max_groups = std::max(1, 65535 / nvb);
+    return (nviews + max_groups - 1) / max_groups;
+}
+
+// The ray-major order used by the nnz counter and the direct forward
+// projection, whatever pg.cm says: one view at a time.
+ProjGeom rays_order(const ProjGeom &pg) {
+    ProjGeom pr = pg;
+    pr.cm = 0;
+    pr.nvb = std::max(1, (pg.nv + kTV - 1) / kTV);
+    pr.vgroup = std::max(1, std::min(min_view_group(pg.nviews, pr.nvb), std::max(pg.nviews, 1)));
+    pr.vgroup_bt = pr.vgroup;
+    return pr;
 }
 
 // The same geometry with the launch order of A^T.
@@ -491,12 +792,11 @@ bool empty(const ProjGeom &pg) { return pg.nu <= 0 || pg.nv <= 0 || pg.nviews <=
 // more reductions on the same voxels at the same time).  On 256^3 (2 x 64 MB)
 // one view at a time is best for both.
 void set_launch_order(ProjGeom &pg) {
-    pg.nvb = std::max(1, (pg.nv + kTV - 1) / kTV);
+    const int tv = pg.cm ? kCV : kTV;
+    pg.nvb = std::max(1, (pg.nv + tv - 1) / tv);
     const int64_t vol_bytes = 2 * (int64_t)pg.nx * pg.ny * pg.nz * (int64_t)sizeof(float);
     const bool wide = vol_bytes > kL2GroupBytes;
-    // grid z = nvb * ceil(nviews / vgroup) must stay <= 65535
-    const int max_groups = std::max(1, 65535 / pg.nvb);
-    const int need = (pg.nviews + max_groups - 1) / max_groups;
+    const int need = min_view_group(pg.nviews, pg.nvb);
     auto clampg = [&](int g) { return std::max(1, std::min(std::max(g, need), std::max(pg.nviews, 1))); };
     pg.vgroup = clampg(wide ? kWideGroupFwd : 1);
     pg.vgroup_bt = clampg(wide ? kWideGroupBack : 1);
@@ -508,14 +808,25 @@ int64_t forward_partials(const ProjGeom &pg) {
     return (int64_t)gr.x * gr.y * gr.z;
 }
 
+int64_t forward_direct_partials(const ProjGeom &pg) {
+    if (empty(pg)) return 0;
+    dim3 gr = proj_grid(rays_order(pg));
+    return (int64_t)gr.x * gr.y * gr.z;
+}
+
 ct_status launch_forward(const ProjGeom &pg, const float *vol, const float *vol_t, float *p,
                          const float *rho, Coef c, double *partials, cudaStream_t st) {
     if (empty(pg)) return CT_OK;
-    dim3 gr = proj_grid(pg), bl(kTU, kTV);
+    dim3 gr = proj_grid(pg), bl(32, 8);
     const bool unit = (vol == nullptr);
     const bool hr = (rho != nullptr), nm = (partials != nullptr);
-#define CT_FWD(HR, NM, UV) \
-    k_forward<HR, NM, UV><<<gr, bl, 0, st>>>(pg, vol, vol_t, p, rho, c, partials)
+#define CT_FWD(HR, NM, UV)                                                             \
+    do {                                                                               \
+        if (pg.cm)                                                                     \
+            k_forward_cm<HR, NM, UV><<<gr, bl, 0, st>>>(pg, vol_t, p, rho, c, partials);  \
+        else                                                                           \
+            k_forward<HR, NM, UV><<<gr, bl, 0, st>>>(pg, vol, vol_t, p, rho, c, partials); \
+    } while (0)
     if (unit) {
         if (hr) { if (nm) CT_FWD(true, true, true); else CT_FWD(true, false, true); }
         else    { if (nm) CT_FWD(false, true, true); else CT_FWD(false, false, true); }
@@ -533,17 +844,25 @@ namespace {
 template <class TV, class TS>
 ct_status fwd_typed(const ProjGeom &pg, const void *vol, const void *vol_t, void *p,
                     const float *rho, Coef c, double *partials, cudaStream_t st) {
-    dim3 gr = proj_grid(pg), bl(kTU, kTV);
+    dim3 gr = proj_grid(pg), bl(32, 8);
     const TV *v = static_cast<const TV *>(vol);
     const TV *vt = static_cast<const TV *>(vol_t);
     TS *o = static_cast<TS *>(p);
+#define CT_FWDT(HR, NM)                                                                         \
+    do {                                                                                        \
+        if (pg.cm)                                                                              \
+            k_forward_cm<HR, NM, false, TV, TS><<<gr, bl, 0, st>>>(pg, vt, o, rho, c, partials);  \
+        else                                                                                    \
+            k_forward<HR, NM, false, TV, TS><<<gr, bl, 0, st>>>(pg, v, vt, o, rho, c, partials); \
+    } while (0)
     if (rho) {
-        if (partials) k_forward<true, true, false, TV, TS><<<gr, bl, 0, st>>>(pg, v, vt, o, rho, c, partials);
-        else          k_forward<true, false, false, TV, TS><<<gr, bl, 0, st>>>(pg, v, vt, o, rho, c, partials);
+        if (partials) CT_FWDT(true, true);
+        else          CT_FWDT(true, false);
     } else {
-        if (partials) k_forward<false, true, false, TV, TS><<<gr, bl, 0, st>>>(pg, v, vt, o, rho, c, partials);
-        else          k_forward<false, false, false, TV, TS><<<gr, bl, 0, st>>>(pg, v, vt, o, rho, c, partials);
+        if (partials) CT_FWDT(false, true);
+        else          CT_FWDT(false, false);
     }
+#undef CT_FWDT
     CT_CHECK_LAUNCH();
     return CT_OK;
 }
@@ -563,11 +882,16 @@ template <class TS>
 ct_status back_typed(const ProjGeom &pg, const void *e, const float *rho, Coef c, void *acc,
                      void *acc_t, int power, bool det, const float *det_scale, cudaStream_t st) {
     const ProjGeom pb = back_order(pg);
-    dim3 gr = proj_grid(pb), bl(kTU, kTV);
+    dim3 gr = proj_grid(pb), bl(32, 8);
     const TS *et = static_cast<const TS *>(e);
     const bool hr = rho != nullptr;
-#define CT_BWD(HR, P, D) \
-    k_backward<HR, P, D, TS><<<gr, bl, 0, st>>>(pb, et, rho, c, acc, acc_t, det_scale)
+#define CT_BWD(HR, P, D)                                                                      \
+    do {                                                                                      \
+        if (pg.cm)                                                                            \
+            k_backward_cm<HR, P, D, TS><<<gr, bl, 0, st>>>(pb, et, rho, c, acc_t, det_scale);  \
+        else                                                                                  \
+            k_backward<HR, P, D, TS><<<gr, bl, 0, st>>>(pb, et, rho, c, acc, acc_t, det_scale); \
+    } while (0)
     if (det) {
         if (power == 2) { if (hr) CT_BWD(true, 2, true); else CT_BWD(false, 2, true); }
         else            { if (hr) CT_BWD(true, 1, true); else CT_BWD(false, 1, true); }
@@ -613,42 +937,21 @@ ct_status launch_backward_typed(const ProjGeom &pg, const void *e, int sdt, cons
 ct_status launch_backward(const ProjGeom &pg, const float *e, const float *rho, Coef c,
                           float *acc, float *acc_t, int power, cudaStream_t st) {
     if (empty(pg)) return CT_OK;
-    const ProjGeom pb = back_order(pg);
-    dim3 gr = proj_grid(pb), bl(kTU, kTV);
-    const bool hr = (rho != nullptr);
-    if (power == 2) {
-        if (hr) k_backward<true, 2, false><<<gr, bl, 0, st>>>(pb, e, rho, c, acc, acc_t, nullptr);
-        else    k_backward<false, 2, false><<<gr, bl, 0, st>>>(pb, e, rho, c, acc, acc_t, nullptr);
-    } else {
-        if (hr) k_backward<true, 1, false><<<gr, bl, 0, st>>>(pb, e, rho, c, acc, acc_t, nullptr);
-        else    k_backward<false, 1, false><<<gr, bl, 0, st>>>(pb, e, rho, c, acc, acc_t, nullptr);
-    }
-    CT_CHECK_LAUNCH();
-    return CT_OK;
+    return back_typed<float>(pg, e, rho, c, acc, acc_t, power, false, nullptr, st);
 }
 
 ct_status launch_backward_det(const ProjGeom &pg, const float *e, const float *rho, Coef c,
                               long long *acc, long long *acc_t, int power,
                               const float *det_scale, cudaStream_t st) {
     if (empty(pg)) return CT_OK;
-    const ProjGeom pb = back_order(pg);
-    dim3 gr = proj_grid(pb), bl(kTU, kTV);
-    const bool hr = (rho != nullptr);
-    if (power == 2) {
-        if (hr) k_backward<true, 2, true><<<gr, bl, 0, st>>>(pb, e, rho, c, acc, acc_t, det_scale);
-        else    k_backward<false, 2, true><<<gr, bl, 0, st>>>(pb, e, rho, c, acc, acc_t, det_scale);
-    } else {
-        if (hr) k_backward<true, 1, true><<<gr, bl, 0, st>>>(pb, e, rho, c, acc, acc_t, det_scale);
-        else    k_backward<false, 1, true><<<gr, bl, 0, st>>>(pb, e, rho, c, acc, acc_t, det_scale);
-    }
-    CT_CHECK_LAUNCH();
-    return CT_OK;
+    return back_typed<float>(pg, e, rho, c, acc, acc_t, power, true, det_scale, st);
 }
 
 ct_status launch_count(const ProjGeom &pg, unsigned long long *d_count, cudaStream_t st) {
     CT_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st));
     if (empty(pg)) return CT_OK;
-    k_count<<<proj_grid(pg), dim3(kTU, kTV), 0, st>>>(pg, d_count);
+    const ProjGeom pr = rays_order(pg);
+    k_count<<<proj_grid(pr), dim3(kTU, kTV), 0, st>>>(pr, d_count);
     CT_CHECK_LAUNCH();
     return CT_OK;
 }
@@ -656,7 +959,8 @@ ct_status launch_count(const ProjGeom &pg, unsigned long long *d_count, cudaStre
 ct_status launch_forward_direct(const ProjGeom &pg, const float *vol, float *p, float alpha,
                                 float beta, double *partials, cudaStream_t st) {
     if (empty(pg)) return CT_OK;
-    k_forward_direct<<<proj_grid(pg), dim3(kTU, kTV), 0, st>>>(pg, vol, p, alpha, beta,
+    const ProjGeom pr = rays_order(pg);
+    k_forward_direct<<<proj_grid(pr), dim3(kTU, kTV), 0, st>>>(pr, vol, p, alpha, beta,
                                                                partials);
     CT_CHECK_LAUNCH();
     return CT_OK;

@@ -5,6 +5,8 @@
 // notes the package relies on double precision): each CTA writes one partial,
 // and one CTA sums the partials in a fixed order, so a result never depends
 // on scheduling.
+#include <algorithm>
+
 #include "ct_internal.h"
 #include "ct_types.cuh"
 
@@ -125,6 +127,110 @@ __global__ void __launch_bounds__(1024) k_sum(const double *__restrict__ partial
 
 }  // namespace
 
+// ---- [y][x][z] copies of the column-major kernels ----------------------------
+// Each CTA transposes one 32 x 32 tile of the (z, x) plane of y = blockIdx.z,
+// blockIdx.z + gridDim.z, ... (gridDim.z <= 65535 whatever ny is), reading
+// and writing along the fastest axis of each layout.
+namespace {
+
+dim3 zfast_grid(const ProjGeom &pg) {
+    return dim3((unsigned)((pg.nx + kTile - 1) / kTile), (unsigned)((pg.nz + kTile - 1) / kTile),
+                (unsigned)std::min(pg.ny, 65535));
+}
+
+// in [nz][ny][nx] -> t [ny][nx][nz]; optionally scaled by w (FP32 only) and
+// optionally writing the scaled volume in the original layout too.
+template <class T>
+__global__ void __launch_bounds__(256) k_to_zfast(int nx, int ny, int nz, const T *__restrict__ in,
+                                                  const float *__restrict__ w, T *__restrict__ t,
+                                                  T *__restrict__ plain) {
+    __shared__ T tile[kTile][kTile + 1];
+    const int x0 = blockIdx.x * kTile, z0 = blockIdx.y * kTile;
+    for (int y = blockIdx.z; y < ny; y += gridDim.z) {
+        for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
+            const int x = x0 + threadIdx.x, z = z0 + j;
+            if (x < nx && z < nz) {
+                const size_t i = ((size_t)z * ny + y) * nx + x;
+                T val = in[i];
+                if (w) val = from_f<T>(to_f(val) * w[i]);
+                if (plain) plain[i] = val;
+                tile[j][threadIdx.x] = val;
+            }
+        }
+        __syncthreads();
+        for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
+            const int z = z0 + threadIdx.x, x = x0 + j;
+            if (x < nx && z < nz) t[((size_t)y * nx + x) * nz + z] = tile[threadIdx.x][j];
+        }
+        __syncthreads();
+    }
+}
+
+// A [y][x][z] accumulator: FP32 sums f, or int64 sums q worth q * inv[0]
+// (inv: device pointer to the exact inverse of the fixed-point scale).
+struct ZAcc {
+    const float *f;
+    const long long *q;
+    const double *inv;
+};
+
+// out[z][y][x] = beta out + acc[y][x][z] (stored as T); int64 sums are scaled
+// in FP64 and rounded once to FP32.  Optional FP64 partial per CTA of
+// sum (w out)^2 over the stored values.
+template <class T>
+__global__ void __launch_bounds__(256) k_from_zfast(int nx, int ny, int nz, T *__restrict__ out,
+                                                    float beta, ZAcc acc,
+                                                    const float *__restrict__ w,
+                                                    double *__restrict__ partials) {
+    __shared__ double tile[kTile][kTile + 1];
+    __shared__ double sh[32];
+    const int x0 = blockIdx.x * kTile, z0 = blockIdx.y * kTile;
+    const double s = acc.q ? acc.inv[0] : 1.0;
+    double sq = 0.0;
+    for (int y = blockIdx.z; y < ny; y += gridDim.z) {
+        for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
+            const int x = x0 + j, z = z0 + threadIdx.x;
+            if (x < nx && z < nz) {
+                const size_t it = ((size_t)y * nx + x) * nz + z;
+                tile[j][threadIdx.x] = acc.q ? (double)acc.q[it] * s : (double)acc.f[it];
+            }
+        }
+        __syncthreads();
+        for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
+            const int z = z0 + j, x = x0 + threadIdx.x;
+            if (x < nx && z < nz) {
+                const size_t i = ((size_t)z * ny + y) * nx + x;
+                float val = (float)tile[threadIdx.x][j];
+                if (beta != 0.f) val = fmaf(beta, to_f(out[i]), val);  // beta 1: a plain add
+                const T st = from_f<T>(val);
+                out[i] = st;
+                if (partials) {
+                    const float vs = to_f(st);
+                    const double qq = w ? (double)(w[i] * vs) : (double)vs;
+                    sq = fma(qq, qq, sq);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (partials) {
+        const double t = block_sum_1d(sq, sh);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            partials[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = t;
+    }
+}
+
+template <class T>
+ct_status from_zfast(const ProjGeom &pg, T *out, float beta, ZAcc acc, const float *w,
+                     double *partials, cudaStream_t st) {
+    k_from_zfast<T><<<zfast_grid(pg), dim3(kTile, 8), 0, st>>>(pg.nx, pg.ny, pg.nz, out, beta,
+                                                               acc, w, partials);
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+}  // namespace
+
 int vec_grid(int64_t n) {
     int64_t b = (n + kVecThreads * 4 - 1) / (kVecThreads * 4);
     if (b < 1) b = 1;
@@ -133,11 +239,21 @@ int vec_grid(int64_t n) {
 }
 
 int transpose_grid_count(const ProjGeom &pg) {
+    if (pg.cm) {
+        const dim3 g = zfast_grid(pg);
+        return (int)(g.x * g.y * g.z);
+    }
     return ((pg.nx + kTile - 1) / kTile) * ((pg.ny + kTile - 1) / kTile) * pg.nz;
 }
 
 ct_status launch_transpose(const ProjGeom &pg, const float *v, const float *w, float *t,
                            float *out_plain, cudaStream_t st) {
+    if (pg.cm) {
+        k_to_zfast<float><<<zfast_grid(pg), dim3(kTile, 8), 0, st>>>(pg.nx, pg.ny, pg.nz, v, w, t,
+                                                                     out_plain);
+        CT_CHECK_LAUNCH();
+        return CT_OK;
+    }
     dim3 gr((pg.nx + kTile - 1) / kTile, (pg.ny + kTile - 1) / kTile, pg.nz), bl(kTile, 8);
     k_transpose<<<gr, bl, 0, st>>>(pg.nx, pg.ny, v, w, t, out_plain);
     CT_CHECK_LAUNCH();
@@ -146,6 +262,7 @@ ct_status launch_transpose(const ProjGeom &pg, const float *v, const float *w, f
 
 ct_status launch_combine(const ProjGeom &pg, float *g, const float *acc_t, const float *w,
                          double *partials, cudaStream_t st) {
+    if (pg.cm) return from_zfast<float>(pg, g, 1.f, ZAcc{acc_t, nullptr, nullptr}, w, partials, st);
     dim3 gr((pg.nx + kTile - 1) / kTile, (pg.ny + kTile - 1) / kTile, pg.nz), bl(kTile, 8);
     k_combine<<<gr, bl, 0, st>>>(pg.nx, pg.ny, g, acc_t, w, partials);
     CT_CHECK_LAUNCH();
@@ -339,6 +456,7 @@ ct_status launch_det_scale(const void *e, int edt, const float *rho, int64_t m, 
 ct_status launch_combine_det(const ProjGeom &pg, float *out, float beta, const long long *acc,
                              const long long *acc_t, const double *inv, const float *w,
                              double *partials, cudaStream_t st) {
+    if (pg.cm) return from_zfast<float>(pg, out, beta, ZAcc{nullptr, acc_t, inv}, w, partials, st);
     dim3 gr((pg.nx + kTile - 1) / kTile, (pg.ny + kTile - 1) / kTile, pg.nz), bl(kTile, 8);
     k_combine_det<<<gr, bl, 0, st>>>(pg.nx, pg.ny, out, beta, acc, acc_t, inv, w, partials);
     CT_CHECK_LAUNCH();
@@ -402,6 +520,28 @@ __global__ void __launch_bounds__(256) k_combine_t(int nx, int ny, int64_t nvox,
 
 ct_status launch_transpose_typed(const ProjGeom &pg, const void *v, void *t, int dt,
                                  cudaStream_t st) {
+    if (pg.cm) {
+        const dim3 gz = zfast_grid(pg), bz(kTile, 8);
+        switch (dt) {
+            case CT_F32:
+                k_to_zfast<float><<<gz, bz, 0, st>>>(pg.nx, pg.ny, pg.nz, (const float *)v,
+                                                     nullptr, (float *)t, nullptr);
+                break;
+            case CT_BF16:
+                k_to_zfast<__nv_bfloat16><<<gz, bz, 0, st>>>(pg.nx, pg.ny, pg.nz,
+                                                             (const __nv_bfloat16 *)v, nullptr,
+                                                             (__nv_bfloat16 *)t, nullptr);
+                break;
+            case CT_F16:
+                k_to_zfast<__half><<<gz, bz, 0, st>>>(pg.nx, pg.ny, pg.nz, (const __half *)v,
+                                                      nullptr, (__half *)t, nullptr);
+                break;
+            default:
+                return set_error(CT_ERR_INVALID_ARG, "unknown dtype");
+        }
+        CT_CHECK_LAUNCH();
+        return CT_OK;
+    }
     dim3 gr((pg.nx + kTile - 1) / kTile, (pg.ny + kTile - 1) / kTile, pg.nz), bl(kTile, 8);
     switch (dt) {
         case CT_F32:
@@ -424,8 +564,20 @@ ct_status launch_transpose_typed(const ProjGeom &pg, const void *v, void *t, int
 ct_status launch_combine_typed(const ProjGeom &pg, void *out, int dt, float beta, const float *acc,
                                const float *acc_t, const long long *q, const double *inv,
                                cudaStream_t st) {
-    dim3 gr((pg.nx + kTile - 1) / kTile, (pg.ny + kTile - 1) / kTile, pg.nz), bl(kTile, 8);
     const int64_t n = (int64_t)pg.nx * pg.ny * pg.nz;
+    if (pg.cm) {
+        // the column-major backprojection accumulates into the second half
+        const ZAcc za{acc_t, q ? q + n : nullptr, inv};
+        switch (dt) {
+            case CT_F32: return from_zfast<float>(pg, (float *)out, beta, za, nullptr, nullptr, st);
+            case CT_BF16:
+                return from_zfast<__nv_bfloat16>(pg, (__nv_bfloat16 *)out, beta, za, nullptr,
+                                                 nullptr, st);
+            case CT_F16: return from_zfast<__half>(pg, (__half *)out, beta, za, nullptr, nullptr, st);
+            default: return set_error(CT_ERR_INVALID_ARG, "unknown dtype");
+        }
+    }
+    dim3 gr((pg.nx + kTile - 1) / kTile, (pg.ny + kTile - 1) / kTile, pg.nz), bl(kTile, 8);
     switch (dt) {
         case CT_F32:
             k_combine_t<float><<<gr, bl, 0, st>>>(pg.nx, pg.ny, n, (float *)out, beta, acc, acc_t, q, inv);
