@@ -23,14 +23,21 @@
 // detector column only.  Anchoring rays at the source (hundreds of voxels
 // away) in FP32 instead costs an order of magnitude in accuracy.
 //
-// Coherence.  The 32 lanes of a warp are 32 adjacent detector columns u of
-// one detector row, and the slab loop is warp-synchronous (the loop index is
-// the same physical slab for all lanes), so at every step the lanes touch 32
-// neighbouring voxels along the lateral axis that varies with u.  That axis
-// is x for rays advancing along y (layout [z][y][x], x fastest) and y for
-// rays advancing along x, which therefore read a transposed copy laid out
-// [z][x][y] (y fastest).  Either way the warp's gathers (and the
-// backprojector's atomics) fall on one or two 128-byte lines.
+// Coherence.  The slab loop is warp-synchronous (the loop index is the same
+// physical slab for all lanes), and a warp's 32 rays are neighbours on the
+// detector, so at every step its lanes touch neighbouring voxels along one
+// axis, laid out contiguously.  Two mappings:
+//  * column-major (the default): the lanes are 32 consecutive rows of one
+//    detector column; they share the in-plane walk and differ in z, and read
+//    a copy of the volume laid out [y][x][z] (z fastest).  See the column-
+//    major section below.
+//  * ray-major (geometries with rays that advance mostly along z): the lanes
+//    are 32 adjacent columns of one row and differ along the lateral axis
+//    that varies with u: x for rays advancing along y (the caller's layout
+//    [z][y][x]) and y for rays advancing along x, which read a copy laid out
+//    [z][x][y].
+// Either way the warp's gathers (and the backprojector's reductions) fall on
+// one or two 128-byte lines.
 #include <algorithm>
 #include <climits>
 #include <type_traits>
@@ -46,7 +53,8 @@ constexpr int kTV = 8;   // detector rows per CTA
 constexpr int kCU = 8;   // column-major tile: detector columns per CTA (one per warp)
 constexpr int kCV = 32;  // detector rows per CTA (one per lane)
 // Launch order (set_launch_order): views visited together by A and by A^T
-// when the volume and its transposed copy take more than kL2GroupBytes.
+// (ray-major A^T: kWideGroupBack) when the volume and its transposed copy take
+// more than kL2GroupBytes.
 constexpr int64_t kL2GroupBytes = int64_t(160) << 20;
 constexpr int kWideGroupFwd = 65535;
 constexpr int kWideGroupBack = 16;
@@ -650,7 +658,7 @@ __device__ __forceinline__ void walk_cm(const CmRay &r, bool ok, Fn &&fn) {
     using interior = std::integral_constant<bool, false>;
     int k = kb;
     for (; k < k_mid0; ++k) slab(clamped{});
-#pragma unroll 2
+#pragma unroll 4
     for (; k <= k_mid1; ++k) slab(interior{});
     for (; k <= ke; ++k) slab(clamped{});
 }
@@ -787,10 +795,12 @@ bool empty(const ProjGeom &pg) { return pg.nu <= 0 || pg.nv <= 0 || pg.nviews <=
 // views of the group: for a volume that does not fit in L2 (512^3 FP32 plus
 // its transposed copy: 1 GB) that band stays resident, which takes fewer DRAM
 // reads and, in A^T, fewer L2 misses of the reductions.  Measured on 512^3
-// with 720 views: A 229 ms with one view at a time, 139 ms with all views in
-// one group; A^T 165 ms and 93 ms with groups of 16 (more views at once put
-// more reductions on the same voxels at the same time).  On 256^3 (2 x 64 MB)
-// one view at a time is best for both.
+// with 720 views (ray-major kernels): A 229 ms with one view at a time,
+// 139 ms with all views in one group; A^T 264 ms with one view, 165 ms with
+// groups of 16 and 169 ms with all views (more views at once put more
+// reductions on the same voxels at the same time).  The column-major A^T
+// takes 145 ms with groups of 16 and 142.5 ms with all views.  On 256^3
+// (2 x 64 MB) one view at a time is best for both.
 void set_launch_order(ProjGeom &pg) {
     const int tv = pg.cm ? kCV : kTV;
     pg.nvb = std::max(1, (pg.nv + tv - 1) / tv);
@@ -799,7 +809,7 @@ void set_launch_order(ProjGeom &pg) {
     const int need = min_view_group(pg.nviews, pg.nvb);
     auto clampg = [&](int g) { return std::max(1, std::min(std::max(g, need), std::max(pg.nviews, 1))); };
     pg.vgroup = clampg(wide ? kWideGroupFwd : 1);
-    pg.vgroup_bt = clampg(wide ? kWideGroupBack : 1);
+    pg.vgroup_bt = clampg(wide ? (pg.cm ? kWideGroupFwd : kWideGroupBack) : 1);
 }
 
 int64_t forward_partials(const ProjGeom &pg) {
