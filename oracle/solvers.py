@@ -11,6 +11,13 @@ algorithm it follows.
   runs the printed form, only to show that it is wrong).  Optional diagonal
   preconditioning: the algorithm is run unchanged on L A W with right-hand
   side L b (left weights L on rays, right weights W on voxels), x = x0 + W y.
+  ``tikhonov = lam > 0`` (Software section: Tikhonov regularisation) runs
+  the same steps on the stacked system [L A; sqrt(lam) I] x ~ [L b; 0], that
+  is it minimises ||L (A x - b)||^2 + lam ||x||^2 (with x = x0 + W y the
+  regulariser acts on x itself).  Written out: the gradient is
+  r = W (A^T L e - lam x), NP2 = ||L A z||^2 + lam ||z||^2 for the x-space
+  direction z = W d, and NB stays the data discrepancy ||L (b - A x)||, so the
+  stopping test keeps its meaning.
 * ``lsqr``  -- Paige & Saunders (1982) LSQR, cited in Materials and Methods,
   in its standard published form, on the same preconditioned operator.
 * ``sirt`` / ``psirt`` -- the classical comparison methods of the Software
@@ -81,7 +88,7 @@ def rowcol_weights(g, threads=None):
 
 def cgls(op, b, x0=None, K: int = 20, err: float = 0.0, left=None, right=None,
          literal_update: bool = False, recompute_every: int = 0,
-         keep_iterates: bool = False) -> SolveResult:
+         keep_iterates: bool = False, tikhonov: float = 0.0) -> SolveResult:
     """Algorithm 1, CGLS with delayed residual computation.
 
     Returns x, the iteration count i (number of x updates, the first one
@@ -89,7 +96,11 @@ def cgls(op, b, x0=None, K: int = 20, err: float = 0.0, left=None, right=None,
     With ``left``/``right`` the same steps run on L A W (see module doc).
     ``recompute_every = k > 0`` replaces the updated discrepancy by b - A x
     every k updates (the reorthogonalisation the Discussion describes).
+    ``tikhonov = lam`` adds lam ||x||^2 to the objective (module doc).
     """
+    lam = float(tikhonov)
+    if lam < 0:
+        raise ValueError("tikhonov must be >= 0")
     b = np.asarray(b, dtype=np.float64)
     Lw = None if left is None else np.asarray(left, dtype=np.float64).reshape(b.shape)
 
@@ -112,13 +123,13 @@ def cgls(op, b, x0=None, K: int = 20, err: float = 0.0, left=None, right=None,
         e = lmul(b).copy()                                # p_b = A x0 = 0 (call skipped)
     else:
         e = lmul(b) - A(x0a)                              # p_b = A x ; e_b = b - p_b
-    r = AT_w(e)                                           # r_x = A^T e_b
-    x = np.zeros_like(r) if x0a is None else x0a.reshape(r.shape).copy()   # x = x0
+    x = np.zeros(op.g.vol_shape) if x0a is None else x0a.reshape(op.g.vol_shape).copy()  # x = x0
+    r = AT_w(e) - lam * wmul(x)                           # r_x = A^T e_b (- lam W x)
     d = r.copy()                                          # d_x = r_x
     z = wmul(d)                                           # direction in x-space, W d
     NR2_old = float(np.sum(r * r))                        # NR2_old = ||r_x||^2
     p = A(z)                                              # p_b = A d_x
-    NP2 = float(np.sum(p * p))                            # NP2 = ||p_b||^2
+    NP2 = float(np.sum(p * p)) + lam * float(np.sum(z * z))  # NP2 = ||p_b||^2 (+ lam ||z||^2)
     alpha = NR2_old / NP2 if NP2 > 0 else 0.0             # alpha = NR2_old / NP2
     x = x + alpha * z                                     # x = x + alpha d_x
     e = e - alpha * p                                     # e_b = e_b - alpha p_b
@@ -128,7 +139,7 @@ def cgls(op, b, x0=None, K: int = 20, err: float = 0.0, left=None, right=None,
     if keep_iterates:
         res.iterates.append(x.copy())
     while (NB / NB0 > err if NB0 > 0 else False) and i < K:
-        r = AT_w(e)                                       # r_x = A^T e_b
+        r = AT_w(e) - lam * wmul(x)                       # r_x = A^T e_b (- lam W x)
         NR2_now = float(np.sum(r * r))                    # NR2_now = ||r_x||^2
         beta = NR2_now / NR2_old if NR2_old > 0 else 0.0  # beta = NR2_now / NR2_old
         if literal_update:
@@ -138,7 +149,7 @@ def cgls(op, b, x0=None, K: int = 20, err: float = 0.0, left=None, right=None,
         z = wmul(d)
         NR2_old = NR2_now                                 # NR2_old = NR2_now
         p = A(z)                                          # p_b = A d_x
-        NP2 = float(np.sum(p * p))                        # NP2 = ||p_b||^2
+        NP2 = float(np.sum(p * p)) + lam * float(np.sum(z * z))  # NP2 (+ lam ||z||^2)
         alpha = NR2_old / NP2 if NP2 > 0 else 0.0         # alpha = NR2_old / NP2
         x = x + alpha * z                                 # x = x + alpha d_x
         e = e - alpha * p                                 # e_b = e_b - alpha p_b

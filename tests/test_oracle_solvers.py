@@ -189,3 +189,40 @@ def test_preconditioner_vectors_match_dense_and_guard_zeros():
     assert np.all(np.isfinite(W)) and np.all(np.isfinite(L)) and np.all(np.isfinite(C))
     assert np.any(R == 0) and np.all(L.ravel()[R == 0] == 0)   # rays that miss: weight 0
     assert inv_sqrt_guarded(np.array([0.0, 1e-9, 4.0])).tolist() == [0.0, 0.0, 0.5]
+
+
+def test_tikhonov_cgls_reaches_regularised_normal_equations():
+    """Software section (Tikhonov regularisation): CGLS with lam > 0 converges
+    to the solution of (A^T L^2 A + lam I) x = A^T L^2 b, written here with
+    numpy.linalg.solve: plain, from x0 != 0, right-scaled (Jacobi; the
+    regulariser acts on x, so the minimiser is unchanged) and left-scaled.
+    lam = 0 is the plain run bit for bit, and the first iterate is one exact
+    line-search step on the regularised normal equations."""
+    g, A, b = tiny_problem(5)
+    op = DenseOperator(A, g.vol_shape, g.sino_shape)
+    lam, n = 0.7, A.shape[1]
+    x_reg = np.linalg.solve(A.T @ A + lam * np.eye(n), A.T @ b.ravel())
+    xls = np.linalg.lstsq(A, b.ravel(), rcond=None)[0]
+    assert rel(x_reg, xls) > 1e-2                     # the regulariser matters here
+    assert rel(cgls(op, b, K=64, tikhonov=lam).x, x_reg) < 1e-8
+    x0 = np.random.default_rng(6).standard_normal(g.vol_shape)
+    assert rel(cgls(op, b, x0=x0, K=64, tikhonov=lam).x, x_reg) < 1e-8
+    Wj = inv_sqrt_guarded((A * A).sum(axis=0)).reshape(g.vol_shape)
+    assert np.all(Wj > 0)
+    assert rel(cgls(op, b, K=64, right=Wj, tikhonov=lam).x, x_reg) < 1e-8
+    L = inv_sqrt_guarded(A.sum(axis=1))
+    AL = L[:, None] * A
+    x_regl = np.linalg.solve(AL.T @ AL + lam * np.eye(n), AL.T @ (L * b.ravel()))
+    assert rel(cgls(op, b, K=64, left=L.reshape(g.sino_shape), tikhonov=lam).x, x_regl) < 1e-8
+    # lam = 0: the unregularised iterates, bit for bit
+    r0, r1 = cgls(op, b, K=7), cgls(op, b, K=7, tikhonov=0.0)
+    assert np.array_equal(r0.x, r1.x) and r0.history == r1.history
+    # first iterate: x1 = a r0, r0 = A^T b, a = ||r0||^2 / (||A r0||^2 + lam ||r0||^2)
+    g0 = A.T @ b.ravel()
+    x1 = (g0 @ g0) / (np.sum((A @ g0) ** 2) + lam * (g0 @ g0)) * g0
+    assert rel(cgls(op, b, K=1, tikhonov=lam).x, x1) < 1e-13
+    # NB stays the data discrepancy ||b - A x||
+    r = cgls(op, b, K=9, tikhonov=lam)
+    assert r.nb == pytest.approx(np.linalg.norm(b.ravel() - A @ r.x.ravel()), rel=1e-10)
+    with pytest.raises(ValueError):
+        cgls(op, b, K=2, tikhonov=-1.0)
