@@ -188,7 +188,12 @@ typedef struct {
     int32_t max_iter;        /* K >= 1: number of x updates at most            */
     double err_tol;          /* ERR >= 0: stop once NB / NB0 <= ERR            */
     int32_t precond;         /* a ct_precond value                            */
-    double tikhonov_lambda;  /* must be 0 (Tikhonov regularisation: not built) */
+    double tikhonov_lambda;  /* lam >= 0 (Software section: Tikhonov
+                                regularisation).  CGLS minimises
+                                ||L (A x - b)||^2 + lam ||x||^2 (L: ROWCOL
+                                row weights, else 1); NB and the stopping
+                                test stay on the data term ||L (b - A x)||.
+                                LSQR: must be 0. */
     int32_t recompute_every; /* k > 0: e_b = b - A x every k updates (CGLS)    */
     int32_t timing;          /* nonzero: time every A and A^T with CUDA events */
     int32_t storage;         /* ct_dtype of the Krylov vectors d_x, e_b, p_b
@@ -224,6 +229,27 @@ ct_status ct_cgls(const ct_geometry *g, const float *d_b, float *d_x, const ct_s
  * 2K + 1 operator calls (+1 with a nonzero x0).  Same arguments as ct_cgls;
  * recompute_every is ignored.  Blocks until done. */
 ct_status ct_lsqr(const ct_geometry *g, const float *d_b, float *d_x, const ct_solver_opts *opts,
+                  ct_solver_report *report, void *stream);
+
+/* SIRT options (ct_sirt). */
+typedef struct {
+    int32_t max_iter;   /* K >= 1: number of x updates at most                 */
+    double err_tol;     /* ERR >= 0: stop once ||b - A x|| / ||b|| <= ERR      */
+    double relax;       /* step lam in (0, 2): 1 = SIRT, 1.5 = PSIRT           */
+    int32_t timing;     /* nonzero: time every A and A^T with CUDA events      */
+} ct_sirt_opts;
+
+/* SIRT and its over-relaxed PSIRT reading, the classical comparison methods
+ * of the Software and Results sections (the paper gives no formula):
+ *   x = x + relax * C^-1 A^T R^-1 (b - A x),  R = A 1, C = A^T 1,
+ * with row or column sums <= 1e-6 of their maximum given weight 0 (no data
+ * there).  PSIRT is read as relax = 2 / (1 + eps) with eps = 1/3, i.e. 1.5.
+ * d_b: sinogram (device, read only); d_x: in = x0, out = x (device).  Each
+ * update costs one A^T and one A (the discrepancy b - A x is recomputed, so
+ * NB in the report is ||b - A x|| of the returned x, NB0 = ||b||).  The
+ * report's history holds NB / NB0 after each update.  Device workspace:
+ * 2 volumes + 2 sinograms + the weights.  Blocks until done. */
+ct_status ct_sirt(const ct_geometry *g, const float *d_b, float *d_x, const ct_sirt_opts *opts,
                   ct_solver_report *report, void *stream);
 
 /* Message of the calling thread's last failed call ("" if none). */

@@ -39,7 +39,7 @@ EXPORTS = ("ct_geometry_create", "ct_geometry_destroy", "ct_geometry_sizes", "ct
            "ct_backproject", "ct_project_norm2", "ct_count_nnz", "ct_precond_weights",
            "ct_cgls", "ct_lsqr", "ct_last_error", "ct_version", "ct_kernel_launches",
            "ct_project_norm2_noalloc", "ct_geometry_set_deterministic", "ct_project_ex",
-           "ct_backproject_ex")
+           "ct_backproject_ex", "ct_sirt")
 
 
 class CTError(RuntimeError):
@@ -59,6 +59,11 @@ class _Desc(ctypes.Structure):
                 ("sid", ctypes.c_double), ("sdd", ctypes.c_double),
                 ("nviews", ctypes.c_int32),
                 ("angles_rad", ctypes.POINTER(ctypes.c_double))]
+
+
+class SirtOpts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("err_tol", ctypes.c_double),
+                ("relax", ctypes.c_double), ("timing", ctypes.c_int32)]
 
 
 class SolverOpts(ctypes.Structure):
@@ -114,6 +119,7 @@ def lib():
             "ct_precond_weights": ([vp, ctypes.c_int32, vp, vp, vp], ctypes.c_int),
             "ct_cgls": ([vp, vp, vp, P(SolverOpts), P(_Report), vp], ctypes.c_int),
             "ct_lsqr": ([vp, vp, vp, P(SolverOpts), P(_Report), vp], ctypes.c_int),
+            "ct_sirt": ([vp, vp, vp, P(SirtOpts), P(_Report), vp], ctypes.c_int),
             "ct_last_error": ([], ctypes.c_char_p),
             "ct_version": ([], ctypes.c_char_p),
             "ct_kernel_launches": ([], ctypes.c_int64),
@@ -315,14 +321,14 @@ def precond_weights(g: Geometry, kind, stream=None):
 
 
 def _solve(fn, g: Geometry, b, x0, max_iter, err_tol, precond, recompute_every, timing,
-           stream, storage="f32"):
+           stream, storage="f32", tikhonov=0.0):
     host = not b.is_cuda
     bd = _dev(b, g.sino_shape, "b", g.device)
     if x0 is None:
         x = torch.zeros(g.vol_shape, dtype=torch.float32, device=g.device)
     else:
         x = _dev(x0, g.vol_shape, "x0", g.device).clone()
-    opts = SolverOpts(int(max_iter), float(err_tol), _PRECOND[precond], 0.0,
+    opts = SolverOpts(int(max_iter), float(err_tol), _PRECOND[precond], float(tikhonov),
                       int(recompute_every), 1 if timing else 0,
                       DTYPES[_torch_dtype(storage)])
     hist = (ctypes.c_double * int(max_iter))()
@@ -337,13 +343,36 @@ def _solve(fn, g: Geometry, b, x0, max_iter, err_tol, precond, recompute_every, 
 
 def cgls(g: Geometry, b: torch.Tensor, x0: Optional[torch.Tensor] = None, max_iter: int = 20,
          err_tol: float = 0.0, precond="none", recompute_every: int = 0, timing: bool = False,
-         stream=None, storage="f32"):
+         stream=None, storage="f32", tikhonov: float = 0.0):
     """CGLS with delayed residual computation (Algorithm 1) -> (x, SolveReport).
 
     storage ("f32", "bf16", "f16") types the Krylov vectors d_x, e_b, p_b; x,
-    the backprojection sums and the FP64 scalars keep their precision."""
+    the backprojection sums and the FP64 scalars keep their precision.
+    tikhonov = lam >= 0 minimises ||L (A x - b)||^2 + lam ||x||^2 (NB stays
+    the data discrepancy)."""
     return _solve(lib().ct_cgls, g, b, x0, max_iter, err_tol, precond, recompute_every, timing,
-                  stream, storage)
+                  stream, storage, tikhonov)
+
+
+def sirt(g: Geometry, b: torch.Tensor, x0: Optional[torch.Tensor] = None, max_iter: int = 20,
+         err_tol: float = 0.0, relax: float = 1.0, timing: bool = False, stream=None):
+    """SIRT (relax = 1) or PSIRT (relax = 1.5) -> (x, SolveReport) (ct_sirt):
+    x += relax C^-1 A^T R^-1 (b - A x); NB = ||b - A x|| of the returned x."""
+    host = not b.is_cuda
+    bd = _dev(b, g.sino_shape, "b", g.device)
+    if x0 is None:
+        x = torch.zeros(g.vol_shape, dtype=torch.float32, device=g.device)
+    else:
+        x = _dev(x0, g.vol_shape, "x0", g.device).clone()
+    opts = SirtOpts(int(max_iter), float(err_tol), float(relax), 1 if timing else 0)
+    hist = (ctypes.c_double * max(int(max_iter), 1))()
+    rep = _Report(0, 0.0, 0.0, ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)),
+                  max(int(max_iter), 1), 0, 0, 0.0, 0.0)
+    _check(lib().ct_sirt(g.handle, _ptr(bd), _ptr(x), ctypes.byref(opts), ctypes.byref(rep),
+                         _stream(stream)))
+    r = SolveReport(rep.iterations, rep.nb0, rep.nb, list(hist[:rep.iterations]),
+                    rep.n_forward, rep.n_back, rep.ms_forward, rep.ms_back)
+    return (x.cpu() if host else x), r
 
 
 def lsqr(g: Geometry, b: torch.Tensor, x0: Optional[torch.Tensor] = None, max_iter: int = 20,

@@ -107,14 +107,19 @@ __global__ void k_norm2_t(const S *__restrict__ v, int64_t n, double *__restrict
 // z = W^2 g + beta z (d_x = r_x + beta d_x in y-space, stored as z = W d).
 // first: z = W^2 g, neither x nor the old z is read.  x stays FP32; z is
 // stored as S.
+// zpart (may be NULL): partial sums of the stored z^2, one per CTA (the
+// lam ||z||^2 term of NP2 with Tikhonov regularisation).
 template <class S>
 __global__ void k_vol_update(float *__restrict__ x, S *__restrict__ z,
                              const float *__restrict__ g, const float *__restrict__ W, int64_t n,
                              const double *__restrict__ a_pend, const double *__restrict__ beta,
-                             const double *__restrict__ zs, int first) {
+                             const double *__restrict__ zs, int first,
+                             double *__restrict__ zpart) {
+    __shared__ double sh[32];
     const float a = first ? 0.f : (float)a_pend[0];
     const float b = first ? 0.f : (float)beta[0];
     const float gs = (float)zs[0];
+    double sq = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         float r = g[i] * gs;
@@ -122,14 +127,50 @@ __global__ void k_vol_update(float *__restrict__ x, S *__restrict__ z,
             const float w = W[i];
             r *= w * w;
         }
+        S zn;
         if (first) {
-            z[i] = from_f<S>(r);
+            zn = from_f<S>(r);
         } else {
             const float zo = to_f(z[i]);
             if (a != 0.f) x[i] = fmaf(a, zo, x[i]);
-            z[i] = from_f<S>(fmaf(b, zo, r));
+            zn = from_f<S>(fmaf(b, zo, r));
+        }
+        z[i] = zn;
+        if (zpart) {
+            const double q = to_f(zn);
+            sq = fma(q, q, sq);
         }
     }
+    if (zpart) {
+        const double t = block_sum(sq, sh);
+        if (threadIdx.x == 0) zpart[blockIdx.x] = t;
+    }
+}
+
+// Tikhonov term of the gradient: g = g - lam x_cur, x_cur = x + a_pend z (the
+// x update still pending from the previous iteration, exactly as
+// k_vol_update will apply it; first: x_cur = x and z is not read), with
+// partial sums of (W g)^2 (NR2).
+template <class S>
+__global__ void k_tikhonov_grad(float *__restrict__ g, const float *__restrict__ x,
+                                const S *__restrict__ z, const float *__restrict__ W, int64_t n,
+                                const double *__restrict__ a_pend, double lam, int first,
+                                double *__restrict__ part) {
+    __shared__ double sh[32];
+    const float a = first ? 0.f : (float)a_pend[0];
+    const float l = (float)lam;
+    double sq = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float xc = x[i];
+        if (!first && a != 0.f) xc = fmaf(a, to_f(z[i]), xc);
+        const float gi = fmaf(-l, xc, g[i]);
+        g[i] = gi;
+        const double q = W ? (double)(W[i] * gi) : (double)gi;
+        sq = fma(q, q, sq);
+    }
+    const double t = block_sum(sq, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 template <class S>
@@ -210,11 +251,18 @@ __global__ void k_absmax_w2g(const float *__restrict__ g, const float *__restric
     }
 }
 
-// NP2 = ||p_b||^2; alpha = NR2_old / NP2 (also the pending x step).
+// NP2 = ||p_b||^2 (+ lam ||z||^2 from zp, the partials of z^2, with
+// Tikhonov regularisation); alpha = NR2_old / NP2 (also the pending x step).
 __global__ void __launch_bounds__(1024) k_cgls_np2(const double *__restrict__ p, int64_t n,
-                                                   CglsS *S) {
+                                                   CglsS *S, const double *__restrict__ zp,
+                                                   int64_t nz, double lam) {
     __shared__ double sh[32];
-    const double t = sum_partials(p, n, sh);
+    double t = sum_partials(p, n, sh);
+    if (zp) {
+        __syncthreads();   // sh is reused
+        const double tz = sum_partials(zp, nz, sh);
+        t += lam * tz;
+    }
     if (threadIdx.x == 0) {
         S->np2 = t;
         S->alpha = safe_div(S->nr2_old * S->zs, t);
@@ -234,6 +282,22 @@ __global__ void __launch_bounds__(1024) k_cgls_nb(const double *__restrict__ p, 
 }
 
 __global__ void k_set_zero(double *p) { p[0] = 0.0; }
+
+// ---- SIRT / PSIRT --------------------------------------------------------------
+// v = v * v (guarded R^-1/2 -> R^-1; zeros stay zero).
+__global__ void k_square(float *__restrict__ v, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = v[i] * v[i];
+}
+
+// x = x + relax * Cinv o g.
+__global__ void k_sirt_update(float *__restrict__ x, const float *__restrict__ g,
+                              const float *__restrict__ cinv, int64_t n, float relax) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = fmaf(relax * cinv[i], g[i], x[i]);
+}
 
 // ---- LSQR ------------------------------------------------------------------
 struct LsqrS {
@@ -391,8 +455,8 @@ ct_status check_opts(const ct_geometry *g, const float *b, float *x, const ct_so
     if (o->precond != CT_PRECOND_NONE && o->precond != CT_PRECOND_JACOBI &&
         o->precond != CT_PRECOND_ROWCOL)
         return set_error(CT_ERR_INVALID_ARG, "unknown precond");
-    if (o->tikhonov_lambda != 0.0)
-        return set_error(CT_ERR_INVALID_ARG, "Tikhonov regularisation is not supported");
+    if (!std::isfinite(o->tikhonov_lambda) || o->tikhonov_lambda < 0.0)
+        return set_error(CT_ERR_INVALID_ARG, "tikhonov_lambda must be finite and >= 0");
     if (o->recompute_every < 0) return set_error(CT_ERR_INVALID_ARG, "recompute_every < 0");
     if (dtype_size(o->storage) == 0) return set_error(CT_ERR_INVALID_ARG, "unknown storage dtype");
     return CT_OK;
@@ -543,6 +607,25 @@ ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
     CT_TRY(sv.ws.alloc(&S, 1));
     CT_TRY(sv.ws.alloc(&hist, (size_t)K));
     CT_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(CglsS), st));
+    // Tikhonov regularisation (Software section): minimise
+    // ||L (A x - b)||^2 + lam ||x||^2, Algorithm 1 on [L A W; sqrt(lam) W]
+    const double lam = o->tikhonov_lambda;
+    double *zpart = nullptr;               // partials of ||z||^2 for NP2
+    if (lam > 0.0) CT_TRY(sv.ws.alloc(&zpart, (size_t)gn));
+    // r_x = A^T e_b into gv, NR2 partials into sv.part (count returned)
+    auto gradient = [&](int first, int64_t *np) -> ct_status {
+        if (lam == 0.0) {
+            CT_TRY(sv.back_t(e, sd, gv, Coef(), sv.W, sv.part));
+            *np = ncp;
+            return CT_OK;
+        }
+        CT_TRY(sv.back_t(e, sd, gv, Coef(), sv.W, nullptr));
+        k_tikhonov_grad<<<gn, kVecThreads, 0, st>>>(gv, x, z, sv.W, n, &S->a_pend, lam, first,
+                                                    sv.part);
+        CT_CHECK_LAUNCH();
+        *np = gn;
+        return CT_OK;
+    };
     Coef one;                              // (1, 0)
     Coef sub;                              // (-1, 1): e = e - L A x
     sub.alpha = -1.f;
@@ -556,20 +639,21 @@ ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
     k_cgls_nb0<<<1, 1024, 0, st>>>(sv.part, gm, S);
     CT_CHECK_LAUNCH();
     if (x0nz) CT_TRY(sv.forward_t(x, CT_F32, sv.T, e, sd, sub, nullptr));
-    // r_x = A^T e_b; d_x = r_x; NR2_old = ||r_x||^2
-    CT_TRY(sv.back_t(e, sd, gv, one, sv.W, sv.part));
+    // r_x = A^T e_b (- lam x); d_x = r_x; NR2_old = ||r_x||^2
+    int64_t nrp = 0;
+    CT_TRY(gradient(1, &nrp));
     if (mxp) {
         k_absmax_w2g<<<gn, kVecThreads, 0, st>>>(gv, sv.W, n, mxp);
         CT_CHECK_LAUNCH();
     }
-    k_cgls_nr2<<<1, 1024, 0, st>>>(sv.part, ncp, S, 1, mxp, gn);
+    k_cgls_nr2<<<1, 1024, 0, st>>>(sv.part, nrp, S, 1, mxp, gn);
     CT_CHECK_LAUNCH();
     k_vol_update<<<gn, kVecThreads, 0, st>>>(x, z, gv, sv.W, n, &S->a_pend, &S->beta, &S->zs,
-                                             1);
+                                             1, zpart);
     CT_CHECK_LAUNCH();
-    // p_b = A d_x; NP2; alpha
+    // p_b = A d_x; NP2 (+ lam ||d_x||^2); alpha
     CT_TRY(sv.forward_t(z, sd, Ts, p, sd, one, sv.part));
-    k_cgls_np2<<<1, 1024, 0, st>>>(sv.part, nfp, S);
+    k_cgls_np2<<<1, 1024, 0, st>>>(sv.part, nfp, S, zpart, gn, lam);
     CT_CHECK_LAUNCH();
     // (x = x + alpha d_x is delayed into the next volume update)
     // e_b = e_b - alpha p_b; NB = ||e_b||
@@ -590,21 +674,21 @@ ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
     bool go = false;
     CT_TRY(keep_going(&go));
     while (go) {
-        // r_x = A^T e_b; NR2_now; beta; NR2_old = NR2_now
-        CT_TRY(sv.back_t(e, sd, gv, one, sv.W, sv.part));
+        // r_x = A^T e_b (- lam x); NR2_now; beta; NR2_old = NR2_now
+        CT_TRY(gradient(0, &nrp));
         if (mxp) {
             k_absmax_w2g<<<gn, kVecThreads, 0, st>>>(gv, sv.W, n, mxp);
             CT_CHECK_LAUNCH();
         }
-        k_cgls_nr2<<<1, 1024, 0, st>>>(sv.part, ncp, S, 0, mxp, gn);
+        k_cgls_nr2<<<1, 1024, 0, st>>>(sv.part, nrp, S, 0, mxp, gn);
         CT_CHECK_LAUNCH();
         // x = x + alpha d_x (previous iteration); d_x = r_x + beta d_x
         k_vol_update<<<gn, kVecThreads, 0, st>>>(x, z, gv, sv.W, n, &S->a_pend, &S->beta,
-                                                 &S->zs, 0);
+                                                 &S->zs, 0, zpart);
         CT_CHECK_LAUNCH();
-        // p_b = A d_x; NP2; alpha
+        // p_b = A d_x; NP2 (+ lam ||d_x||^2); alpha
         CT_TRY(sv.forward_t(z, sd, Ts, p, sd, one, sv.part));
-        k_cgls_np2<<<1, 1024, 0, st>>>(sv.part, nfp, S);
+        k_cgls_np2<<<1, 1024, 0, st>>>(sv.part, nfp, S, zpart, gn, lam);
         CT_CHECK_LAUNCH();
         // e_b = e_b - alpha p_b; NB
         k_sino_axpy<<<gm, kVecThreads, 0, st>>>(e, p, m, &S->alpha, sv.part);
@@ -726,6 +810,85 @@ ct_status lsqr_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
     return CT_OK;
 }
 
+
+// SIRT / PSIRT (Software and Results sections; no formula in the paper):
+// x += relax C^-1 A^T R^-1 (b - A x), R = A 1, C = A^T 1 with the guarded
+// inverses of the row/column-sum preconditioner (sums <= 1e-6 max: weight 0).
+// Per update one A^T (rays weighted by R^-1) and one A recomputing
+// e = b - A x, whose FP64 norm gives NB and the history.
+ct_status sirt_impl(const ct_geometry *g, const float *b, float *x, const ct_sirt_opts *o,
+                    ct_solver_report *rep, cudaStream_t st) {
+    const int K = o->max_iter;
+    const double ERR = o->err_tol;
+    Solve sv(g, st, o->timing != 0);
+    CT_TRY(sv.init(CT_PRECOND_ROWCOL));     // L = R^-1/2, W = C^-1/2
+    const int64_t n = sv.n, m = sv.m;
+    const int gn = vec_grid(n), gm = vec_grid(m);
+    const int64_t nfp = forward_partials(sv.pg);
+    k_square<<<gm, kVecThreads, 0, st>>>(sv.L, m);            // R^-1
+    CT_CHECK_LAUNCH();
+    k_square<<<gn, kVecThreads, 0, st>>>(sv.W, n);            // C^-1
+    CT_CHECK_LAUNCH();
+    float *e = nullptr, *gv = nullptr;
+    CglsS *S = nullptr;
+    double *hist = nullptr;
+    CT_TRY(sv.ws.alloc(&e, (size_t)std::max<int64_t>(m, 1)));
+    CT_TRY(sv.ws.alloc(&gv, (size_t)n));
+    CT_TRY(sv.ws.alloc(&S, 1));
+    CT_TRY(sv.ws.alloc(&hist, (size_t)K));
+    CT_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(CglsS), st));
+    Coef sub;                               // e = b - A x
+    sub.alpha = -1.f;
+    sub.beta = 1.f;
+    // e = b (with partials of ||b||^2 when requested); the forward calls below
+    // then subtract A x without row weights
+    auto copy_b = [&](double *partials) -> ct_status {
+        k_sino_weighted_copy<<<gm, kVecThreads, 0, st>>>(e, b, nullptr, m, partials);
+        CT_CHECK_LAUNCH();
+        return CT_OK;
+    };
+    bool x0nz = false;
+    CT_TRY(sv.nonzero(x, &x0nz));
+    CT_TRY(copy_b(sv.part));                // NB0 = ||b||
+    k_cgls_nb0<<<1, 1024, 0, st>>>(sv.part, gm, S);
+    CT_CHECK_LAUNCH();
+    auto project_residual = [&](double *partials) -> ct_status {
+        CT_TRY(launch_transpose(sv.pg, x, nullptr, sv.T, nullptr, st));
+        CT_TRY(sv.tm.mark(sv.tm.fwd));
+        CT_TRY(launch_forward(sv.pg, x, sv.T, e, nullptr, sub, partials, st));
+        CT_TRY(sv.tm.mark(sv.tm.fwd));
+        ++sv.n_fwd;
+        return CT_OK;
+    };
+    if (x0nz) CT_TRY(project_residual(nullptr));
+    Coef one;
+    int i = 0;
+    CglsS hs{};
+    bool go = K > 0;
+    while (go) {
+        // x = x + relax C^-1 A^T R^-1 e
+        CT_TRY(sv.back(e, gv, one, nullptr, nullptr));
+        k_sirt_update<<<gn, kVecThreads, 0, st>>>(x, gv, sv.W, n, (float)o->relax);
+        CT_CHECK_LAUNCH();
+        // e = b - A x; NB = ||e||
+        CT_TRY(copy_b(nullptr));
+        CT_TRY(project_residual(sv.part));
+        k_cgls_nb<<<1, 1024, 0, st>>>(sv.part, nfp, S, hist, i);
+        CT_CHECK_LAUNCH();
+        ++i;
+        go = i < K;
+        if (go && ERR > 0.0) {
+            CT_TRY(read_scalars(S, &hs, st));
+            go = hs.nb0 > 0.0 && hs.nb / hs.nb0 > ERR;
+        }
+    }
+    std::vector<double> h((size_t)K, 0.0);
+    CT_CUDA_TRY(cudaMemcpyAsync(h.data(), hist, sizeof(double) * (size_t)i,
+                                cudaMemcpyDeviceToHost, st));
+    CT_TRY(read_scalars(S, &hs, st));
+    sv.report(rep, i, hs.nb0, hs.nb, h);
+    return CT_OK;
+}
 }  // namespace
 }  // namespace ct
 
@@ -755,6 +918,8 @@ ct_status ct_lsqr(const ct_geometry *g, const float *d_b, float *d_x, const ct_s
                   ct_solver_report *report, void *stream) {
     clear_error();
     CT_TRY(check_opts(g, d_b, d_x, opts));
+    if (opts->tikhonov_lambda != 0.0)
+        return set_error(CT_ERR_INVALID_ARG, "LSQR: tikhonov_lambda must be 0 (use ct_cgls)");
     DeviceGuard dg(g->device);
     CT_TRY(dg.status());
     cudaStream_t st = (cudaStream_t)stream;
@@ -763,6 +928,26 @@ ct_status ct_lsqr(const ct_geometry *g, const float *d_b, float *d_x, const ct_s
     ct_status s = lsqr_impl(g, d_b, d_x, opts, report, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (s == CT_OK && e != cudaSuccess) return cuda_error(e, "ct_lsqr");
+    return s;
+}
+
+ct_status ct_sirt(const ct_geometry *g, const float *d_b, float *d_x, const ct_sirt_opts *opts,
+                  ct_solver_report *report, void *stream) {
+    clear_error();
+    if (!g) return set_error(CT_ERR_INVALID_ARG, "geometry is NULL");
+    if (!opts) return set_error(CT_ERR_INVALID_ARG, "opts is NULL");
+    if (!d_x || (g->nrays > 0 && !d_b)) return set_error(CT_ERR_INVALID_ARG, "NULL vector");
+    if (opts->max_iter < 1) return set_error(CT_ERR_INVALID_ARG, "max_iter must be >= 1");
+    if (!std::isfinite(opts->err_tol) || opts->err_tol < 0.0)
+        return set_error(CT_ERR_INVALID_ARG, "err_tol must be finite and >= 0");
+    if (!std::isfinite(opts->relax) || !(opts->relax > 0.0) || !(opts->relax < 2.0))
+        return set_error(CT_ERR_INVALID_ARG, "relax must lie in (0, 2)");
+    DeviceGuard dg(g->device);
+    CT_TRY(dg.status());
+    cudaStream_t st = (cudaStream_t)stream;
+    const ct_status s = sirt_impl(g, d_b, d_x, opts, report, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (s == CT_OK && e != cudaSuccess) return cuda_error(e, "ct_sirt");
     return s;
 }
 

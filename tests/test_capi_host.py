@@ -59,6 +59,20 @@ def test_bad_geometry_rejected_before_cuda(built_lib):
     assert b"sid" in L.ct_last_error()
     d = ct._Desc(8, 8, 8, -1, 1, 1, 0, 0, 0, 8, 8, 1, 1, 0, 0, 750, 1200, 4, None)
     assert L.ct_geometry_create(ctypes.byref(d), ctypes.byref(h)) == 1
+    # grid limits: nv <= 65535 * 8, nviews and nz <= 65535
+    d = ct._Desc(8, 8, 8, 1, 1, 1, 0, 0, 0, 8, 65535 * 8 + 1, 1, 1, 0, 0, 750, 1200, 4, None)
+    assert L.ct_geometry_create(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert b"nv" in L.ct_last_error()
+    d = ct._Desc(8, 8, 8, 1, 1, 1, 0, 0, 0, 8, 8, 1, 1, 0, 0, 750, 1200, 65536, None)
+    assert L.ct_geometry_create(ctypes.byref(d), ctypes.byref(h)) == 1
+
+
+def test_solver_options_rejected_before_cuda(built_lib):
+    import paper_2110_13526_gb300 as ct
+    L = ct.lib()
+    so = ct.SirtOpts(5, 0.0, 1.0, 0)
+    assert L.ct_sirt(None, None, None, ctypes.byref(so), None, None) == 1
+    assert b"geometry" in L.ct_last_error()
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

@@ -10,6 +10,7 @@ import oracle
 import synth
 from oracle.solvers import cgls as ocgls
 from oracle.solvers import jacobi_weights, lsqr as olsqr, rowcol_weights
+from oracle.solvers import sirt as osirt
 
 pytestmark = pytest.mark.gpu
 
@@ -192,3 +193,78 @@ def test_deterministic_solvers_bitwise_and_parity(ct, small, precond):
         left, right = (None, None) if precond == "none" else rowcol_weights(og)
         ref = osolver(oracle.Operator(og), b.astype(np.float64), K=12, left=left, right=right)
         assert rel(x1.cpu().numpy(), ref.x) < TOL_X
+
+
+@pytest.mark.parametrize("precond", ["none", "jacobi", "rowcol"])
+def test_cgls_tikhonov(ct, small, precond):
+    """Tikhonov-regularised CGLS (Software section): ||L (A x - b)||^2 +
+    lam ||x||^2 against the oracle; lam = a tenth of the mean of diag(A^T A),
+    large enough to change the result.  The unweighted case starts from a
+    nonzero x0.  FP16 Krylov storage keeps its usual bound."""
+    cfg, og, _, b = small
+    g = ct.Geometry(**cfg)
+    lam = 0.1 * float(oracle.backproject(og, np.ones(og.sino_shape), power=2).mean())
+    left = right = None
+    if precond == "jacobi":
+        right = jacobi_weights(og)
+    elif precond == "rowcol":
+        left, right = rowcol_weights(og)
+    x0 = synth.random_field(g.vol_shape, seed=7) * 0.05 if precond == "none" else None
+    op, b64 = oracle.Operator(og), b.astype(np.float64)
+    ref = ocgls(op, b64, x0=None if x0 is None else x0.astype(np.float64), K=12, left=left,
+                right=right, tikhonov=lam)
+    ref0 = ocgls(op, b64, x0=None if x0 is None else x0.astype(np.float64), K=12, left=left,
+                 right=right)
+    assert rel(ref.x, ref0.x) > 1e-2
+    bd = torch.from_numpy(b).cuda()
+    x0d = None if x0 is None else torch.from_numpy(x0).cuda()
+    x, rep = ct.cgls(g, bd, x0=x0d, max_iter=12, precond=precond, tikhonov=lam)
+    assert rel(x.cpu().numpy(), ref.x) < TOL_X
+    np.testing.assert_allclose(rep.history, ref.history, rtol=TOL_X)
+    xh, _ = ct.cgls(g, bd, x0=x0d, max_iter=12, precond=precond, tikhonov=lam, storage="f16")
+    assert rel(xh.cpu().numpy(), ref.x) < 3e-3
+    with pytest.raises(RuntimeError, match="CT_ERR_INVALID_ARG"):
+        ct.cgls(g, bd, max_iter=2, tikhonov=-1.0)
+
+
+@pytest.mark.parametrize("relax", [1.0, 1.5])
+def test_sirt_psirt(ct, small, relax):
+    """SIRT (relax 1) and the PSIRT reading (relax 1.5) against the oracle:
+    iterates, the recomputed discrepancy history, operator calls (one A and
+    one A^T per update, one more A for a nonzero x0) and the ERR stop."""
+    cfg, og, _, b = small
+    g = ct.Geometry(**cfg)
+    op, b64 = oracle.Operator(og), b.astype(np.float64)
+    bd = torch.from_numpy(b).cuda()
+    ref = osirt(op, b64, K=8, lam=relax)
+    x, rep = ct.sirt(g, bd, max_iter=8, relax=relax)
+    assert rep.iterations == 8 and (rep.n_forward, rep.n_back) == (8, 8)
+    assert rel(x.cpu().numpy(), ref.x) < TOL_X
+    np.testing.assert_allclose(rep.history, ref.history, rtol=TOL_X)
+    assert rep.nb0 == pytest.approx(ref.nb0, rel=1e-7)
+    assert rep.nb == pytest.approx(ref.nb, rel=TOL_X)
+    x0 = synth.random_field(g.vol_shape, seed=8) * 0.05
+    ref = osirt(op, b64, K=5, lam=relax, x0=x0.astype(np.float64))
+    x, rep = ct.sirt(g, bd, x0=torch.from_numpy(x0).cuda(), max_iter=5, relax=relax)
+    assert (rep.n_forward, rep.n_back) == (6, 5)
+    assert rel(x.cpu().numpy(), ref.x) < TOL_X
+    full = osirt(op, b64, K=20, lam=relax)
+    err = 0.5 * (full.history[9] + full.history[10])    # met at the 11th update
+    _, rep = ct.sirt(g, bd, max_iter=20, err_tol=err, relax=relax)
+    assert rep.iterations == 11 and rep.nb / rep.nb0 <= err
+    for bad in (0.0, 2.0, -1.0):
+        with pytest.raises(RuntimeError, match="CT_ERR_INVALID_ARG"):
+            ct.sirt(g, bd, max_iter=2, relax=bad)
+
+
+def test_cgls_beats_sirt_and_psirt_on_pr1(ct, pr1):
+    """Results section: at equal numbers of projections and backprojections
+    CGLS reaches a far smaller discrepancy than SIRT/PSIRT (GPU runs)."""
+    cfg, _, _, b = pr1
+    g = ct.Geometry(**cfg)
+    bd = torch.from_numpy(b).cuda()
+    _, rc = ct.cgls(g, bd, max_iter=20)
+    _, rs = ct.sirt(g, bd, max_iter=20, relax=1.0)
+    _, rp = ct.sirt(g, bd, max_iter=20, relax=1.5)
+    assert rc.history[-1] < 0.5 * min(rs.history[-1], rp.history[-1])
+    assert all(rs.history[k + 1] <= rs.history[k] * (1 + 1e-6) for k in range(19))
