@@ -758,6 +758,10 @@ dim3 proj_grid(const ProjGeom &pg) {
                 (unsigned)(pg.nvb * ngroups));
 }
 
+// CTA shape of the projector kernels: kCV lanes x kCU warps (column-major)
+// or kTU x kTV (ray-major).
+dim3 proj_block(const ProjGeom &pg) { return pg.cm ? dim3(kCV, kCU) : dim3(kTU, kTV); }
+
 // View groups that keep grid z = nvb * ceil(nviews / vgroup) <= 65535.
 int min_view_group(int nviews, int nvb) {
     const int max_groups = std::max(1, 65535 / nvb);
@@ -827,7 +831,7 @@ int64_t forward_direct_partials(const ProjGeom &pg) {
 ct_status launch_forward(const ProjGeom &pg, const float *vol, const float *vol_t, float *p,
                          const float *rho, Coef c, double *partials, cudaStream_t st) {
     if (empty(pg)) return CT_OK;
-    dim3 gr = proj_grid(pg), bl(32, 8);
+    dim3 gr = proj_grid(pg), bl = proj_block(pg);
     const bool unit = (vol == nullptr);
     const bool hr = (rho != nullptr), nm = (partials != nullptr);
 #define CT_FWD(HR, NM, UV)                                                             \
@@ -854,7 +858,7 @@ namespace {
 template <class TV, class TS>
 ct_status fwd_typed(const ProjGeom &pg, const void *vol, const void *vol_t, void *p,
                     const float *rho, Coef c, double *partials, cudaStream_t st) {
-    dim3 gr = proj_grid(pg), bl(32, 8);
+    dim3 gr = proj_grid(pg), bl = proj_block(pg);
     const TV *v = static_cast<const TV *>(vol);
     const TV *vt = static_cast<const TV *>(vol_t);
     TS *o = static_cast<TS *>(p);
@@ -892,7 +896,7 @@ template <class TS>
 ct_status back_typed(const ProjGeom &pg, const void *e, const float *rho, Coef c, void *acc,
                      void *acc_t, int power, bool det, const float *det_scale, cudaStream_t st) {
     const ProjGeom pb = back_order(pg);
-    dim3 gr = proj_grid(pb), bl(32, 8);
+    dim3 gr = proj_grid(pb), bl = proj_block(pb);
     const TS *et = static_cast<const TS *>(e);
     const bool hr = rho != nullptr;
 #define CT_BWD(HR, P, D)                                                                      \
