@@ -14,7 +14,18 @@ thread_local std::string g_last_error;
 std::atomic<long long> g_launches{0};
 }
 
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+namespace {
+thread_local long long t_launches = 0;
+}
+
+void note_launch() {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    ++t_launches;
+}
+
+long long thread_launches() { return t_launches; }
+
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 ct_status set_error(ct_status st, const std::string &msg) {
     g_last_error = msg;

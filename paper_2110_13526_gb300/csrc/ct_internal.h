@@ -95,6 +95,10 @@ void clear_error();
 // Counts one kernel launch of this library (ct_kernel_launches) and checks
 // that it was accepted.
 void note_launch();
+// Kernels this thread has launched (or captured into a graph) so far.
+long long thread_launches();
+// Adds n to the process-wide count (graph replays; negative: undo a capture).
+void note_launches(long long n);
 #define CT_CHECK_LAUNCH()                               \
     do {                                                \
         ::ct::note_launch();                            \

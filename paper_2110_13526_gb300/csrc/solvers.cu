@@ -51,6 +51,7 @@ __device__ __forceinline__ double safe_div(double a, double b) { return b != 0.0
 // p~ = A z~ directly: alpha~ = NR2 zs / ||p~||^2.
 struct CglsS {
     double nb0, nr2_old, nr2_now, np2, alpha, beta, nb, a_pend, tmp, zs;
+    int it;   // next history slot (k_cgls_nb with i < 0)
 };
 
 // e = L o b, stored as S; partial sums of the stored e^2 (one per CTA).
@@ -277,7 +278,8 @@ __global__ void __launch_bounds__(1024) k_cgls_nb(const double *__restrict__ p, 
     const double t = sum_partials(p, n, sh);
     if (threadIdx.x == 0) {
         S->nb = sqrt(t);
-        hist[i] = safe_div(S->nb, S->nb0);
+        const int k = i >= 0 ? i : S->it++;   // i < 0: the slot counter on the device
+        hist[k] = safe_div(S->nb, S->nb0);
     }
 }
 
@@ -575,6 +577,57 @@ ct_status read_scalars(const S *d, S *h, cudaStream_t st) {
 }
 
 
+// One solver update as a CUDA graph: captured once on a private stream
+// (the caller's stream may be the legacy default stream, which cannot
+// capture), then replayed on the solve's stream, one graph launch per update.
+struct UpdateGraph {
+    cudaStream_t cs = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t last = nullptr;  // stream of the last replay
+    long long nk = 0;             // kernels per replay (ct_kernel_launches)
+    UpdateGraph() = default;
+    UpdateGraph(const UpdateGraph &) = delete;
+    UpdateGraph &operator=(const UpdateGraph &) = delete;
+    ~UpdateGraph() {
+        if (last) cudaStreamSynchronize(last);   // replays finish before the graph goes
+        if (exec) cudaGraphExecDestroy(exec);
+        if (g) cudaGraphDestroy(g);
+        if (cs) cudaStreamDestroy(cs);
+    }
+    // body() enqueues one update on *sref, which points at the capture stream
+    // meanwhile.  Nothing runs during capture, so the kernels it counted are
+    // taken back from ct_kernel_launches and added again per replay.
+    template <class F>
+    ct_status capture(F &&body, cudaStream_t *sref) {
+        CT_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        const long long k0 = thread_launches();
+        CT_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        const cudaStream_t saved = *sref;
+        *sref = cs;
+        const ct_status sb = body();
+        *sref = saved;
+        cudaGraph_t gr = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(cs, &gr);
+        nk = thread_launches() - k0;
+        note_launches(-nk);
+        if (sb != CT_OK) {
+            if (gr) cudaGraphDestroy(gr);
+            return sb;
+        }
+        if (ec != cudaSuccess) return cuda_error(ec, "cudaStreamEndCapture");
+        g = gr;
+        CT_CUDA_TRY(cudaGraphInstantiate(&exec, g, 0));
+        return CT_OK;
+    }
+    ct_status launch(cudaStream_t st) {
+        CT_CUDA_TRY(cudaGraphLaunch(exec, st));
+        last = st;
+        note_launches(nk);
+        return CT_OK;
+    }
+};
+
 template <class ST>
 ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_solver_opts *o,
                     ct_solver_report *rep, cudaStream_t st) {
@@ -620,8 +673,8 @@ ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
             return CT_OK;
         }
         CT_TRY(sv.back_t(e, sd, gv, Coef(), sv.W, nullptr));
-        k_tikhonov_grad<<<gn, kVecThreads, 0, st>>>(gv, x, z, sv.W, n, &S->a_pend, lam, first,
-                                                    sv.part);
+        k_tikhonov_grad<<<gn, kVecThreads, 0, sv.st>>>(gv, x, z, sv.W, n, &S->a_pend, lam,
+                                                       first, sv.part);
         CT_CHECK_LAUNCH();
         *np = gn;
         return CT_OK;
@@ -659,7 +712,7 @@ ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
     // e_b = e_b - alpha p_b; NB = ||e_b||
     k_sino_axpy<<<gm, kVecThreads, 0, st>>>(e, p, m, &S->alpha, sv.part);
     CT_CHECK_LAUNCH();
-    k_cgls_nb<<<1, 1024, 0, st>>>(sv.part, gm, S, hist, 0);
+    k_cgls_nb<<<1, 1024, 0, st>>>(sv.part, gm, S, hist, -1);
     CT_CHECK_LAUNCH();
     int i = 1;
     CglsS hs{};
@@ -671,28 +724,66 @@ ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
         }
         return CT_OK;
     };
-    bool go = false;
-    CT_TRY(keep_going(&go));
-    while (go) {
+    // One x update after the first, enqueued on sv.st; ends with NB in
+    // sv.part (k_cgls_nb reads it).
+    auto update = [&]() -> ct_status {
+        const cudaStream_t s = sv.st;
         // r_x = A^T e_b (- lam x); NR2_now; beta; NR2_old = NR2_now
         CT_TRY(gradient(0, &nrp));
         if (mxp) {
-            k_absmax_w2g<<<gn, kVecThreads, 0, st>>>(gv, sv.W, n, mxp);
+            k_absmax_w2g<<<gn, kVecThreads, 0, s>>>(gv, sv.W, n, mxp);
             CT_CHECK_LAUNCH();
         }
-        k_cgls_nr2<<<1, 1024, 0, st>>>(sv.part, nrp, S, 0, mxp, gn);
+        k_cgls_nr2<<<1, 1024, 0, s>>>(sv.part, nrp, S, 0, mxp, gn);
         CT_CHECK_LAUNCH();
         // x = x + alpha d_x (previous iteration); d_x = r_x + beta d_x
-        k_vol_update<<<gn, kVecThreads, 0, st>>>(x, z, gv, sv.W, n, &S->a_pend, &S->beta,
-                                                 &S->zs, 0, zpart);
+        k_vol_update<<<gn, kVecThreads, 0, s>>>(x, z, gv, sv.W, n, &S->a_pend, &S->beta,
+                                                &S->zs, 0, zpart);
         CT_CHECK_LAUNCH();
         // p_b = A d_x; NP2 (+ lam ||d_x||^2); alpha
         CT_TRY(sv.forward_t(z, sd, Ts, p, sd, one, sv.part));
-        k_cgls_np2<<<1, 1024, 0, st>>>(sv.part, nfp, S, zpart, gn, lam);
+        k_cgls_np2<<<1, 1024, 0, s>>>(sv.part, nfp, S, zpart, gn, lam);
         CT_CHECK_LAUNCH();
         // e_b = e_b - alpha p_b; NB
-        k_sino_axpy<<<gm, kVecThreads, 0, st>>>(e, p, m, &S->alpha, sv.part);
+        k_sino_axpy<<<gm, kVecThreads, 0, s>>>(e, p, m, &S->alpha, sv.part);
         CT_CHECK_LAUNCH();
+        return CT_OK;
+    };
+    auto finish = [&]() -> ct_status {
+        k_cgls_nb<<<1, 1024, 0, sv.st>>>(sv.part, gm, S, hist, -1);
+        CT_CHECK_LAUNCH();
+        return CT_OK;
+    };
+    // Without per-operator timing or recomputation every update enqueues the
+    // same launches with the same arguments (the scalars live on the device),
+    // so the first one is captured as a CUDA graph and replayed: one launch
+    // per update instead of a dozen.
+    UpdateGraph graph;
+    const bool use_graph = !o->timing && o->recompute_every == 0 && K > 2;
+    bool go = false;
+    CT_TRY(keep_going(&go));
+    int dfwd = 0, dback = 0;               // operator calls per replayed update
+    if (go && use_graph) {
+        const int f0 = sv.n_fwd, b0 = sv.n_back;
+        CT_TRY(graph.capture([&]() -> ct_status {
+            CT_TRY(update());
+            return finish();
+        }, &sv.st));
+        dfwd = sv.n_fwd - f0;
+        dback = sv.n_back - b0;
+        sv.n_fwd = f0;
+        sv.n_back = b0;
+    }
+    while (go) {
+        if (graph.exec) {
+            CT_TRY(graph.launch(st));
+            sv.n_fwd += dfwd;
+            sv.n_back += dback;
+            ++i;
+            CT_TRY(keep_going(&go));
+            continue;
+        }
+        CT_TRY(update());
         ++i;
         if (o->recompute_every > 0 && i % o->recompute_every == 0) {
             // discrepancy recomputed from the solution (Discussion)
@@ -706,8 +797,7 @@ ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
             k_norm2_t<<<gm, kVecThreads, 0, st>>>(e, m, sv.part);
             CT_CHECK_LAUNCH();
         }
-        k_cgls_nb<<<1, 1024, 0, st>>>(sv.part, gm, S, hist, i - 1);
-        CT_CHECK_LAUNCH();
+        CT_TRY(finish());
         CT_TRY(keep_going(&go));
     }
     // the last pending x = x + alpha d_x

@@ -268,3 +268,22 @@ def test_cgls_beats_sirt_and_psirt_on_pr1(ct, pr1):
     _, rp = ct.sirt(g, bd, max_iter=20, relax=1.5)
     assert rc.history[-1] < 0.5 * min(rs.history[-1], rp.history[-1])
     assert all(rs.history[k + 1] <= rs.history[k] * (1 + 1e-6) for k in range(19))
+
+
+def test_cgls_graph_replay_equals_direct_launches(ct, small):
+    """Without per-operator timing CGLS captures one update as a CUDA graph
+    and replays it; with timing it launches every kernel directly.  With
+    fixed-point backprojection both give bitwise the same iterates, and the
+    launch counter counts the replayed kernels like direct ones."""
+    cfg, _, _, b = small
+    g = ct.Geometry(**cfg, deterministic=True)
+    bd = torch.from_numpy(b).cuda()
+    for kw in (dict(), dict(precond="jacobi"), dict(tikhonov=0.05), dict(storage="bf16")):
+        l0 = ct.kernel_launches()
+        x1, r1 = ct.cgls(g, bd, max_iter=9, **kw)
+        l1 = ct.kernel_launches()
+        x2, r2 = ct.cgls(g, bd, max_iter=9, timing=True, **kw)
+        l2 = ct.kernel_launches()
+        assert torch.equal(x1, x2), kw
+        assert r1.history == r2.history and r1.iterations == r2.iterations == 9
+        assert l1 - l0 == l2 - l1 > 0
