@@ -306,6 +306,7 @@ struct LsqrS {
     double nb0, alpha, beta, inv_beta, inv_alpha, rhobar, phibar, x_step, w_step, tmp;
     double coef_fwd[2];   // projector epilogue: u = 1 * L A t - alpha / beta_old * u
     double coef_back[2];  // backprojector scale: 1 / beta
+    int it;               // next history slot (k_lsqr_rot with i < 0)
 };
 
 __global__ void __launch_bounds__(1024) k_lsqr_nb0(const double *__restrict__ p, int64_t n,
@@ -399,7 +400,8 @@ __global__ void __launch_bounds__(1024) k_lsqr_rot(const double *__restrict__ p,
         S->w_step = safe_div(theta, rho);
         S->alpha = alpha;
         S->inv_alpha = safe_div(1.0, alpha);
-        hist[i] = safe_div(S->phibar, S->nb0);
+        const int k = i >= 0 ? i : S->it++;   // i < 0: the slot counter on the device
+        hist[k] = safe_div(S->phibar, S->nb0);
     }
 }
 
@@ -864,26 +866,49 @@ ct_status lsqr_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
         CT_TRY(read_scalars(S, &hs, st));
         go = hs.nb0 > 0.0 && hs.phibar / hs.nb0 > ERR;
     }
-    while (go) {
+    // One LSQR iteration, enqueued on sv.st (captured and replayed as a CUDA
+    // graph like the CGLS update, see UpdateGraph).
+    auto update = [&]() -> ct_status {
+        const cudaStream_t s = sv.st;
         // beta u = L A W v - alpha u
         const float *tin = v;
         if (sv.W) {
-            CT_TRY(launch_transpose(sv.pg, v, sv.W, sv.T, t, st));
+            CT_TRY(launch_transpose(sv.pg, v, sv.W, sv.T, t, s));
             tin = t;
         }
-        k_lsqr_coef_fwd<<<1, 1, 0, st>>>(S);
+        k_lsqr_coef_fwd<<<1, 1, 0, s>>>(S);
         CT_CHECK_LAUNCH();
         CT_TRY(sv.forward(tin, sv.W != nullptr, u, cf, sv.part));
-        k_lsqr_beta<<<1, 1024, 0, st>>>(sv.part, nfp, S);
+        k_lsqr_beta<<<1, 1024, 0, s>>>(sv.part, nfp, S);
         CT_CHECK_LAUNCH();
         // alpha v = W A^T L u - beta v
         CT_TRY(sv.back(u, gv, cb, nullptr, nullptr));
-        k_lsqr_v<<<gn, kVecThreads, 0, st>>>(v, gv, sv.W, n, S, sv.part);
+        k_lsqr_v<<<gn, kVecThreads, 0, s>>>(v, gv, sv.W, n, S, sv.part);
         CT_CHECK_LAUNCH();
-        k_lsqr_rot<<<1, 1024, 0, st>>>(sv.part, gn, S, hist, i);
+        k_lsqr_rot<<<1, 1024, 0, s>>>(sv.part, gn, S, hist, -1);
         CT_CHECK_LAUNCH();
-        k_lsqr_update<<<gn, kVecThreads, 0, st>>>(x, v, wv, sv.W, n, S);
+        k_lsqr_update<<<gn, kVecThreads, 0, s>>>(x, v, wv, sv.W, n, S);
         CT_CHECK_LAUNCH();
+        return CT_OK;
+    };
+    UpdateGraph graph;
+    int dfwd = 0, dback = 0;
+    if (go && !o->timing && K > 2) {
+        const int f0 = sv.n_fwd, b0 = sv.n_back;
+        CT_TRY(graph.capture(update, &sv.st));
+        dfwd = sv.n_fwd - f0;
+        dback = sv.n_back - b0;
+        sv.n_fwd = f0;
+        sv.n_back = b0;
+    }
+    while (go) {
+        if (graph.exec) {
+            CT_TRY(graph.launch(st));
+            sv.n_fwd += dfwd;
+            sv.n_back += dback;
+        } else {
+            CT_TRY(update());
+        }
         ++i;
         go = i < K;
         if (go && ERR > 0.0) {

@@ -270,11 +270,12 @@ def test_cgls_beats_sirt_and_psirt_on_pr1(ct, pr1):
     assert all(rs.history[k + 1] <= rs.history[k] * (1 + 1e-6) for k in range(19))
 
 
-def test_cgls_graph_replay_equals_direct_launches(ct, small):
-    """Without per-operator timing CGLS captures one update as a CUDA graph
-    and replays it; with timing it launches every kernel directly.  With
+def test_graph_replay_equals_direct_launches(ct, small):
+    """Without per-operator timing CGLS and LSQR capture one update as a CUDA
+    graph and replay it; with timing they launch every kernel directly.  With
     fixed-point backprojection both give bitwise the same iterates, and the
-    launch counter counts the replayed kernels like direct ones."""
+    launch and operator-call counters count the replayed work like direct
+    launches."""
     cfg, _, _, b = small
     g = ct.Geometry(**cfg, deterministic=True)
     bd = torch.from_numpy(b).cuda()
@@ -287,3 +288,8 @@ def test_cgls_graph_replay_equals_direct_launches(ct, small):
         assert torch.equal(x1, x2), kw
         assert r1.history == r2.history and r1.iterations == r2.iterations == 9
         assert l1 - l0 == l2 - l1 > 0
+    for kw in (dict(), dict(precond="rowcol")):
+        x1, r1 = ct.lsqr(g, bd, max_iter=9, **kw)
+        x2, r2 = ct.lsqr(g, bd, max_iter=9, timing=True, **kw)
+        assert torch.equal(x1, x2), kw
+        assert r1.history == r2.history and (r1.n_forward, r1.n_back) == (r2.n_forward, r2.n_back)
