@@ -52,6 +52,8 @@ def parse():
                     help="default mode: requests of the served-latency block (0 = skip)")
     ap.add_argument("--workload", default="B256", choices=["B256", "P512"],
                     help="ops mode only: 256^3 (default) or the 512^3, 720-view workload")
+    ap.add_argument("--projector", default="siddon", choices=["siddon", "sf_tr", "sf_tt"],
+                    help="ops mode only: Siddon rays or separable footprints (TR, TT)")
     ap.add_argument("--cpu-sample-views", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -164,9 +166,9 @@ def traffic_for(kernel: str):
 PHANTOM_SEED = {"B256": 1, "P512": 2}
 
 
-def make_problem(ct, torch, synth, dev, workload="B256"):
+def make_problem(ct, torch, synth, dev, workload="B256", projector="siddon"):
     cfg = synth.CONFIGS[workload]
-    g = ct.Geometry(**cfg)
+    g = ct.Geometry(**cfg, projector=projector)
     lo, hi = synth.box_of(cfg)
     x_true = torch.from_numpy(synth.voxelize(synth.random_ellipsoids(40, PHANTOM_SEED[workload],
                                                                      lo, hi), cfg)).to(dev)
@@ -343,7 +345,8 @@ def run_ops(a):
     import synth
 
     torch.cuda.set_device(0)
-    cfg, g, x_true, b = make_problem(ct, torch, synth, torch.device("cuda", 0), a.workload)
+    cfg, g, x_true, b = make_problem(ct, torch, synth, torch.device("cuda", 0), a.workload,
+                                     a.projector)
     nnz = ct.count_nnz(g)
     r = torch.empty(g.vol_shape, device="cuda")
     p = torch.empty(g.sino_shape, device="cuda")
@@ -363,7 +366,8 @@ def run_ops(a):
         tf.append(e[0].elapsed_time(e[1]))
         tb.append(e[1].elapsed_time(e[2]))
     mf, mb = statistics.median(tf), statistics.median(tb)
-    print(json.dumps({"mode": "ops", "config": {"workload": a.workload, "nnz": nnz},
+    print(json.dumps({"mode": "ops", "config": {"workload": a.workload, "nnz": nnz,
+                                                "projector": a.projector},
                       "ms_project": mf, "ms_backproject": mb,
                       "gray_voxel_per_s": {"A": nnz / mf / 1e6, "AT": nnz / mb / 1e6},
                       "note": "ct_project / ct_backproject calls, including the transpose "

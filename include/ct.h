@@ -103,6 +103,28 @@ void ct_geometry_destroy(ct_geometry *g);
  * while no call on this geometry is in flight. */
 ct_status ct_geometry_set_deterministic(ct_geometry *g, int32_t on);
 
+/* Projector of a geometry (Materials and Methods names Siddon, the TT
+ * footprint projector of Long et al. 2010 and cutting voxels).
+ *   CT_PROJ_SIDDON: A_ij = length in mm of the pixel-centre ray i in voxel j
+ *                   (the default).
+ *   CT_PROJ_SF_TR / CT_PROJ_SF_TT: separable footprints averaged over the
+ *                   detector cell: A_ij = l_j Fbar_u Fbar_v, with the
+ *                   transaxial footprint the trapezoid of the voxel's four
+ *                   projected vertical edges, the axial one a rectangle (TR)
+ *                   or the trapezoid of the z faces projected at the nearest
+ *                   and farthest corner depths (TT), and l_j the chord of the
+ *                   ray through the voxel centre across its x and y faces.
+ * The same matrix serves ct_project, ct_backproject (exactly adjoint), the
+ * solvers and the preconditioner weights.  The footprint projectors need
+ * FP32 storage (CT_ERR_INVALID_ARG for BF16/FP16 in ct_project_ex,
+ * ct_backproject_ex and the solvers' storage), cannot be combined with
+ * deterministic accumulation (their forward projection scatters with float
+ * atomics; their backprojection gathers and is deterministic anyway), and
+ * need ny <= 524280.  Change the projector only while no call on this
+ * geometry is in flight. */
+typedef enum { CT_PROJ_SIDDON = 0, CT_PROJ_SF_TR = 1, CT_PROJ_SF_TT = 2 } ct_projector;
+ct_status ct_geometry_set_projector(ct_geometry *g, int32_t kind);
+
 /* Sizes of the geometry: voxels (n = nx ny nz) and rays (m = nviews nv nu). */
 ct_status ct_geometry_sizes(const ct_geometry *g, int64_t *n_vox, int64_t *n_rays);
 

@@ -30,6 +30,8 @@ LIB_PATH = os.path.join(_PKG, "_build", "libct_gb300.so")
 
 CT_OK = 0
 CT_PRECOND_NONE, CT_PRECOND_JACOBI, CT_PRECOND_ROWCOL = 0, 1, 2
+# ct_projector: Siddon pixel-centre rays, separable footprints (TR, TT)
+PROJECTORS = {"siddon": 0, "sf_tr": 1, "sf_tt": 2}
 _PRECOND = {"none": 0, None: 0, "jacobi": 1, "rowcol": 2, 0: 0, 1: 1, 2: 2}
 _STATUS = {0: "CT_OK", 1: "CT_ERR_INVALID_ARG", 2: "CT_ERR_CUDA", 3: "CT_ERR_OOM",
            4: "CT_ERR_TIMEOUT", 5: "CT_ERR_INTERNAL"}
@@ -39,7 +41,7 @@ EXPORTS = ("ct_geometry_create", "ct_geometry_destroy", "ct_geometry_sizes", "ct
            "ct_backproject", "ct_project_norm2", "ct_count_nnz", "ct_precond_weights",
            "ct_cgls", "ct_lsqr", "ct_last_error", "ct_version", "ct_kernel_launches",
            "ct_project_norm2_noalloc", "ct_geometry_set_deterministic", "ct_project_ex",
-           "ct_backproject_ex", "ct_sirt")
+           "ct_backproject_ex", "ct_sirt", "ct_geometry_set_projector")
 
 
 class CTError(RuntimeError):
@@ -120,6 +122,7 @@ def lib():
             "ct_cgls": ([vp, vp, vp, P(SolverOpts), P(_Report), vp], ctypes.c_int),
             "ct_lsqr": ([vp, vp, vp, P(SolverOpts), P(_Report), vp], ctypes.c_int),
             "ct_sirt": ([vp, vp, vp, P(SirtOpts), P(_Report), vp], ctypes.c_int),
+            "ct_geometry_set_projector": ([vp, ctypes.c_int32], ctypes.c_int),
             "ct_last_error": ([], ctypes.c_char_p),
             "ct_version": ([], ctypes.c_char_p),
             "ct_kernel_launches": ([], ctypes.c_int64),
@@ -156,12 +159,14 @@ class Geometry:
 
     Lengths in mm.  ``angles`` (radians) defaults to 2 pi k / nviews.
     Volume tensors are float32 [nz, ny, nx]; sinograms float32 [nviews, nv, nu].
+    ``projector``: "siddon" (pixel-centre rays), "sf_tr" or "sf_tt" (separable
+    footprints averaged over detector cells; ct_geometry_set_projector).
     """
 
     def __init__(self, nx, ny, nz, vx, vy, vz, nu, nv, du, dv, sid, sdd, nviews,
                  ox=0.0, oy=0.0, oz=0.0, det_off_u=0.0, det_off_v=0.0,
                  angles: Optional[Sequence[float]] = None, device=None,
-                 deterministic: bool = False):
+                 deterministic: bool = False, projector: str = "siddon"):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.nu, self.nv, self.nviews = int(nu), int(nv), int(nviews)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
@@ -178,6 +183,11 @@ class Geometry:
             _check(lib().ct_geometry_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
         self.deterministic = bool(deterministic)
+        if projector not in PROJECTORS:
+            raise ValueError("projector must be one of %s" % sorted(PROJECTORS))
+        self.projector = projector
+        if PROJECTORS[projector] != 0:
+            _check(lib().ct_geometry_set_projector(h, PROJECTORS[projector]))
         if deterministic:
             _check(lib().ct_geometry_set_deterministic(h, 1))
 

@@ -358,6 +358,10 @@ ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out) {
     g->pg.nx = d.nx; g->pg.ny = d.ny; g->pg.nz = d.nz;
     g->pg.nu = d.nu; g->pg.nv = d.nv; g->pg.nviews = d.nviews;
     g->pg.hx = (float)d.vx; g->pg.hy = (float)d.vy; g->pg.hz = (float)d.vz;
+    g->pg.proj = CT_PROJ_SIDDON;
+    g->pg.sf_view = nullptr;
+    g->pg.sf_ku = g->pg.sf_kv = g->pg.sf_cu = g->pg.sf_cv = g->pg.sf_oz = 0.f;
+    g->d_sf = nullptr;
     // Column-major kernels unless some ray advances mostly along z.  The
     // kernels compute C = fmaf(vc, C1, C0) in FP32 with vc = v - (nv - 1) / 2
     // exact; fmaf is correctly rounded, hence monotone in vc, so the largest
@@ -382,10 +386,11 @@ ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out) {
 
 void ct_geometry_destroy(ct_geometry *g) {
     if (!g) return;
-    if (g->d_views || g->d_cols) {
+    if (g->d_views || g->d_cols || g->d_sf) {
         DeviceGuard dg(g->device);
         if (g->d_views) cudaFree(g->d_views);
         if (g->d_cols) cudaFree(g->d_cols);
+        if (g->d_sf) cudaFree(g->d_sf);
     }
     delete g;
 }
@@ -525,7 +530,49 @@ ct_status ct_backproject_ex(const ct_geometry *g, const void *d_sino, int32_t si
 ct_status ct_geometry_set_deterministic(ct_geometry *g, int32_t on) {
     clear_error();
     CT_TRY(check_geom(g));
+    if (on && g->pg.proj != CT_PROJ_SIDDON)
+        return set_error(CT_ERR_INVALID_ARG,
+                         "deterministic mode needs the Siddon projector (the footprint "
+                         "projectors scatter their forward projection with float atomics)");
     g->deterministic = on ? 1 : 0;
+    return CT_OK;
+}
+
+ct_status ct_geometry_set_projector(ct_geometry *g, int32_t kind) {
+    clear_error();
+    CT_TRY(check_geom(g));
+    if (kind != CT_PROJ_SIDDON && kind != CT_PROJ_SF_TR && kind != CT_PROJ_SF_TT)
+        return set_error(CT_ERR_INVALID_ARG, "unknown projector");
+    if (kind != CT_PROJ_SIDDON) {
+        if (g->deterministic)
+            return set_error(CT_ERR_INVALID_ARG,
+                             "footprint projectors cannot run in deterministic mode");
+        if (g->desc.ny > 65535 * 8)
+            return set_error(CT_ERR_INVALID_ARG, "footprint projectors need ny <= 524280");
+        if (!g->d_sf && g->desc.nviews > 0) {
+            DeviceGuard dg(g->device);
+            CT_TRY(dg.status());
+            std::vector<float4> sv;
+            float scal[5];
+            sf_view_constants(g->desc, g->angles, sv, scal);
+            float4 *d = nullptr;
+            CT_CUDA_TRY(cudaMalloc(&d, sv.size() * sizeof(float4)));
+            const cudaError_t e =
+                cudaMemcpy(d, sv.data(), sv.size() * sizeof(float4), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                cudaFree(d);
+                return cuda_error(e, "footprint constants upload");
+            }
+            g->d_sf = d;
+            g->pg.sf_ku = scal[0];
+            g->pg.sf_kv = scal[1];
+            g->pg.sf_cu = scal[2];
+            g->pg.sf_cv = scal[3];
+            g->pg.sf_oz = scal[4];
+        }
+        g->pg.sf_view = g->d_sf;
+    }
+    g->pg.proj = kind;
     return CT_OK;
 }
 

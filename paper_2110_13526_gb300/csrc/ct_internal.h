@@ -50,6 +50,9 @@ struct ProjGeom {
     float hx, hy, hz;        // voxel pitch, mm
     int cm;                  // 1: column-major kernels and the [y][x][z] volume copy
                              // (no ray advances mostly along z), 0: ray-major, [z][x][y]
+    int proj;                // ct_projector
+    const float4 *sf_view;   // footprint projectors: 2 float4 per view (sf_view_constants)
+    float sf_ku, sf_kv, sf_cu, sf_cv, sf_oz;
     int vgroup;              // launch order of A: views per group (set_launch_order)
     int vgroup_bt;           // launch order of A^T
     int nvb;                 // row blocks of the projector grid
@@ -70,6 +73,7 @@ struct ct_geometry {
     void *d_cols;                // device: col_a, col_b, col_flags in one allocation
     ct::ProjGeom pg;
     int deterministic;           // backprojections accumulate in int64 fixed point
+    float4 *d_sf;                // device: footprint-projector view constants (or NULL)
     double det_bound;            // bound on (rays through one voxel) * lsig_max
 };
 
@@ -186,6 +190,23 @@ ct_status launch_combine_det(const ProjGeom &pg, float *out, float beta, const l
 ct_status launch_forward_direct(const ProjGeom &pg, const float *vol, float *p, float alpha,
                                 float beta, double *partials, cudaStream_t st);
 
+// ---- separable-footprint projectors (footprint.cu) -----------------------------
+// Per-view constants (2 float4 per view) and the global scalars
+// scal[5] = {SDD/du, SDD/dv, cu, cv, off_z}, FP64 on the host.
+void sf_view_constants(const ct_geometry_desc &d, const std::vector<double> &ang,
+                       std::vector<float4> &out, float *scal);
+// p = alpha rho o (A x) + beta p (vol NULL: all ones) with the FP64 partials
+// of ||p||^2 (sf_forward_partials of them) when partials is set.
+ct_status sf_forward(const ProjGeom &pg, const float *vol, float *p, const float *rho, Coef c,
+                     double *partials, cudaStream_t st);
+int64_t sf_forward_partials(const ProjGeom &pg);
+// acc += alpha (A o ...)^T (rho o e), power 1 or 2 (e NULL: e = 1), caller's layout.
+ct_status sf_backward(const ProjGeom &pg, const float *e, const float *rho, Coef c, float *acc,
+                      int power, cudaStream_t st);
+ct_status sf_count(const ProjGeom &pg, unsigned long long *d_count, cudaStream_t st);
+// out = beta out + acc
+ct_status sf_axpby(float *out, const float *acc, int64_t n, float beta, cudaStream_t st);
+
 // ---- volume / sinogram kernels (vector_ops.cu) ------------------------------
 int vec_grid(int64_t n);  // CTAs of a streaming kernel (also its partial count)
 constexpr int kVecThreads = 256;
@@ -209,6 +230,8 @@ ct_status launch_combine_typed(const ProjGeom &pg, void *out, int dt, float beta
                                cudaStream_t st);
 // out = beta * out (beta == 0 writes zeros without reading)
 ct_status launch_scale(float *out, int64_t n, float beta, cudaStream_t st);
+// out = v o w (elementwise).
+ct_status launch_mul(float *out, const float *v, const float *w, int64_t n, cudaStream_t st);
 ct_status launch_scale_dev(float *out, int64_t n, const double *beta, cudaStream_t st);
 // Sum of partials[0..n) in a fixed order into *out (FP64, deterministic).
 ct_status launch_sum(const double *partials, int64_t n, double *out, cudaStream_t st);

@@ -1,0 +1,385 @@
+// Separable-footprint projector pair (SF-TR / SF-TT) for sm_103a.
+//
+// Materials and Methods computes the paper's results with the "TT" footprint
+// projector of Long, Fessler and Balter (2010), which the paper names without
+// writing it out.  Read here as follows (conventions of include/ct.h):
+//   * a point P projects to detector pixel-index coordinates
+//       u = (SDD / du) s_u(P) / t(P) + cu,   v = (SDD / dv) z(P) / t(P) + cv,
+//     with t the depth along the central ray and s_u the coordinate along e_u;
+//   * transaxial footprint: the unit trapezoid whose breakpoints are the
+//     sorted u of the voxel's four vertical edges (u does not depend on z);
+//   * axial footprint: TR -- the unit rectangle between the v of the two z
+//     faces at the depth of the voxel centre; TT -- the unit trapezoid of the
+//     v of the two z faces at the smallest and largest depth of the corners;
+//   * amplitude: the chord of the ray through the voxel centre across the x
+//     and y faces, l = |d| min(hx / |d_x|, hy / |d_y|), d = centre - source;
+//   * a detector cell averages the footprint:
+//       A_ij = l * Fbar_u(k) * Fbar_v(l),  Fbar(k) = integral over [k-1/2, k+1/2].
+// A^T uses the same entries, so the pair is exactly adjoint.
+//
+// Kernels.  A is voxel-driven: one thread per voxel column (i, j) and view
+// computes the transaxial footprint once and walks the column in z, adding
+// its contributions to the detector cells with float reductions (the 32
+// lanes of a warp are 32 neighbouring columns, whose footprints are
+// neighbouring cells).  A^T gathers: one thread per column segment of kSfZ
+// voxels loops over all views and sums the cells under each voxel's
+// footprint, so every voxel is written once, without reductions.
+// Coordinates are relative to the volume centre (per-view constants computed
+// in FP64 on the host), which keeps the FP32 breakpoints accurate.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "ct_internal.h"
+
+namespace ct {
+namespace {
+
+constexpr int kSfKU = 8;   // transaxial cells kept in registers per pass
+constexpr int kSfZ = 8;    // voxels per A^T thread (one column segment)
+
+struct SfColumn {
+    float tau[4];          // sorted transaxial breakpoints (pixel index units)
+    float qa, qb;          // SDD / (dv t) at the two axial depths (TR: both the centre's)
+    float m;               // min(hx / |d_x|, hy / |d_y|)
+    float dxy2;            // d_x^2 + d_y^2
+    int ku0, ku1;          // cells overlapping the footprint, clipped to the detector
+};
+
+__device__ __forceinline__ void sort4(float &a, float &b, float &c, float &d) {
+    float t;
+#define CT_CSWAP(x, y) \
+    if (y < x) {       \
+        t = x;         \
+        x = y;         \
+        y = t;         \
+    }
+    CT_CSWAP(a, b);
+    CT_CSWAP(c, d);
+    CT_CSWAP(a, c);
+    CT_CSWAP(b, d);
+    CT_CSWAP(b, c);
+#undef CT_CSWAP
+}
+
+// Integral of the unit trapezoid t0 <= t1 <= t2 <= t3 over [a, b], summed
+// piece by piece (no difference of large antiderivatives).
+__device__ __forceinline__ float trap_cell(float t0, float t1, float t2, float t3, float a,
+                                           float b) {
+    float r = 0.f;
+    float x1 = fmaxf(a, t0), x2 = fminf(b, t1);
+    if (x2 > x1) r += (x2 - x1) * (x2 + x1 - 2.f * t0) / (2.f * (t1 - t0));
+    x1 = fmaxf(a, t1);
+    x2 = fminf(b, t2);
+    if (x2 > x1) r += x2 - x1;
+    x1 = fmaxf(a, t2);
+    x2 = fminf(b, t3);
+    if (x2 > x1) r += (x2 - x1) * (2.f * t3 - x1 - x2) / (2.f * (t3 - t2));
+    return r;
+}
+
+// Column (i, j) of view `view`: transaxial footprint, axial depths, amplitude.
+template <bool TT>
+__device__ __forceinline__ bool sf_column(const ProjGeom &g, int view, int i, int j, SfColumn &c) {
+    const float4 a = __ldg(g.sf_view + 2 * view);      // s0, t0, eux, euy
+    const float4 b = __ldg(g.sf_view + 2 * view + 1);  // ecx, ecy, dx0, dy0
+    const float rx = ((float)i - 0.5f * (float)(g.nx - 1)) * g.hx;
+    const float ry = ((float)j - 0.5f * (float)(g.ny - 1)) * g.hy;
+    const float hx = 0.5f * g.hx, hy = 0.5f * g.hy;
+    float u[4], t[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float px = rx + ((q & 1) ? hx : -hx);
+        const float py = ry + ((q & 2) ? hy : -hy);
+        const float su = fmaf(px, a.z, fmaf(py, a.w, a.x));
+        t[q] = fmaf(px, b.x, fmaf(py, b.y, a.y));
+        u[q] = fmaf(g.sf_ku, su / t[q], g.sf_cu);
+    }
+    c.tau[0] = u[0];
+    c.tau[1] = u[1];
+    c.tau[2] = u[2];
+    c.tau[3] = u[3];
+    sort4(c.tau[0], c.tau[1], c.tau[2], c.tau[3]);
+    if (TT) {
+        const float tmin = fminf(fminf(t[0], t[1]), fminf(t[2], t[3]));
+        const float tmax = fmaxf(fmaxf(t[0], t[1]), fmaxf(t[2], t[3]));
+        c.qa = g.sf_kv / tmin;
+        c.qb = g.sf_kv / tmax;
+    } else {
+        const float tc = fmaf(rx, b.x, fmaf(ry, b.y, a.y));
+        c.qa = c.qb = g.sf_kv / tc;
+    }
+    const float dx = b.z + rx, dy = b.w + ry;
+    const float mx = dx != 0.f ? g.hx / fabsf(dx) : INFINITY;
+    const float my = dy != 0.f ? g.hy / fabsf(dy) : INFINITY;
+    c.m = fminf(mx, my);
+    c.dxy2 = fmaf(dx, dx, dy * dy);
+    c.ku0 = max(0, (int)floorf(c.tau[0] + 0.5f));
+    c.ku1 = min(g.nu - 1, (int)floorf(c.tau[3] + 0.5f));
+    return c.ku0 <= c.ku1;
+}
+
+// Axial footprint and amplitude of voxel k of the column.
+template <bool TT>
+__device__ __forceinline__ void sf_axial(const ProjGeom &g, const SfColumn &c, int k, float *vb,
+                                         float &amp) {
+    const float rz = ((float)k - 0.5f * (float)(g.nz - 1)) * g.hz;
+    const float z = g.sf_oz + rz;
+    const float zlo = z - 0.5f * g.hz, zhi = z + 0.5f * g.hz;
+    if (TT) {
+        vb[0] = fmaf(zlo, c.qa, g.sf_cv);
+        vb[1] = fmaf(zlo, c.qb, g.sf_cv);
+        vb[2] = fmaf(zhi, c.qa, g.sf_cv);
+        vb[3] = fmaf(zhi, c.qb, g.sf_cv);
+        sort4(vb[0], vb[1], vb[2], vb[3]);
+    } else {
+        const float p = fmaf(zlo, c.qa, g.sf_cv), q = fmaf(zhi, c.qa, g.sf_cv);
+        vb[0] = vb[1] = fminf(p, q);
+        vb[2] = vb[3] = fmaxf(p, q);
+    }
+    amp = c.m * sqrtf(fmaf(z, z, c.dxy2));
+}
+
+__device__ __forceinline__ void coef_sf(const Coef &c, float &alpha) {
+    alpha = c.dev ? (float)c.dev[0] : c.alpha;
+}
+
+// out[view][v][u] += alpha * rho * A x over the columns (i, j) of one view.
+template <bool HAS_RHO, bool UNIT_VOL, bool TT>
+__global__ void __launch_bounds__(256) k_sf_forward(ProjGeom g, const float *__restrict__ vol,
+                                                    float *__restrict__ out,
+                                                    const float *__restrict__ rho, Coef cf) {
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    const int view = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    SfColumn c;
+    if (!sf_column<TT>(g, view, i, j, c)) return;
+    float alpha;
+    coef_sf(cf, alpha);
+    const size_t vbase = (size_t)view * g.nv * g.nu;
+    const size_t plane = (size_t)g.nx * g.ny;
+    for (int k0 = c.ku0; k0 <= c.ku1; k0 += kSfKU) {
+        float fu[kSfKU];
+        const int nk = min(kSfKU, c.ku1 - k0 + 1);
+#pragma unroll
+        for (int q = 0; q < kSfKU; ++q)
+            fu[q] = q < nk ? trap_cell(c.tau[0], c.tau[1], c.tau[2], c.tau[3],
+                                       (float)(k0 + q) - 0.5f, (float)(k0 + q) + 0.5f)
+                           : 0.f;
+        for (int k = 0; k < g.nz; ++k) {
+            const float xv = UNIT_VOL ? 1.f : vol[(size_t)k * plane + (size_t)j * g.nx + i];
+            if (xv == 0.f) continue;
+            float vb[4], amp;
+            sf_axial<TT>(g, c, k, vb, amp);
+            const int kv0 = max(0, (int)floorf(vb[0] + 0.5f));
+            const int kv1 = min(g.nv - 1, (int)floorf(vb[3] + 0.5f));
+            for (int l = kv0; l <= kv1; ++l) {
+                const float fv = trap_cell(vb[0], vb[1], vb[2], vb[3], (float)l - 0.5f,
+                                           (float)l + 0.5f);
+                if (fv == 0.f) continue;
+                const float base = alpha * amp * fv * xv;
+                const size_t row = vbase + (size_t)l * g.nu;
+#pragma unroll
+                for (int q = 0; q < kSfKU; ++q) {
+                    if (q < nk && fu[q] != 0.f) {
+                        float val = base * fu[q];
+                        if (HAS_RHO) val *= rho[row + k0 + q];
+                        atomicAdd(out + row + k0 + q, val);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// acc[z][y][x] += alpha * sum over views and cells of A_ij^POWER rho_i e_i
+// (e == NULL: e = 1) for kSfZ voxels of one column.
+template <bool HAS_RHO, int POWER, bool TT>
+__global__ void __launch_bounds__(256) k_sf_backward(ProjGeom g, const float *__restrict__ e,
+                                                     const float *__restrict__ rho, Coef cf,
+                                                     float *__restrict__ acc) {
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    const int kz0 = blockIdx.z * kSfZ;
+    if (i >= g.nx || j >= g.ny) return;
+    float sum[kSfZ];
+#pragma unroll
+    for (int q = 0; q < kSfZ; ++q) sum[q] = 0.f;
+    const int nz = min(kSfZ, g.nz - kz0);
+    for (int view = 0; view < g.nviews; ++view) {
+        SfColumn c;
+        if (!sf_column<TT>(g, view, i, j, c)) continue;
+        const size_t vbase = (size_t)view * g.nv * g.nu;
+        for (int k0 = c.ku0; k0 <= c.ku1; k0 += kSfKU) {
+            float fu[kSfKU];
+            const int nk = min(kSfKU, c.ku1 - k0 + 1);
+#pragma unroll
+            for (int q = 0; q < kSfKU; ++q)
+                fu[q] = q < nk ? trap_cell(c.tau[0], c.tau[1], c.tau[2], c.tau[3],
+                                           (float)(k0 + q) - 0.5f, (float)(k0 + q) + 0.5f)
+                               : 0.f;
+#pragma unroll
+            for (int dz = 0; dz < kSfZ; ++dz) {
+                if (dz >= nz) break;
+                float vb[4], amp;
+                sf_axial<TT>(g, c, kz0 + dz, vb, amp);
+                const int kv0 = max(0, (int)floorf(vb[0] + 0.5f));
+                const int kv1 = min(g.nv - 1, (int)floorf(vb[3] + 0.5f));
+                float s = 0.f;
+                for (int l = kv0; l <= kv1; ++l) {
+                    const float fv = trap_cell(vb[0], vb[1], vb[2], vb[3], (float)l - 0.5f,
+                                               (float)l + 0.5f);
+                    if (fv == 0.f) continue;
+                    const size_t row = vbase + (size_t)l * g.nu;
+                    float su = 0.f;
+#pragma unroll
+                    for (int q = 0; q < kSfKU; ++q) {
+                        if (q < nk && fu[q] != 0.f) {
+                            float w = e ? e[row + k0 + q] : 1.f;
+                            if (HAS_RHO) w *= rho[row + k0 + q];
+                            su = POWER == 1 ? fmaf(fu[q], w, su) : fmaf(fu[q] * fu[q], w, su);
+                        }
+                    }
+                    s = POWER == 1 ? fmaf(fv, su, s) : fmaf(fv * fv, su, s);
+                }
+                sum[dz] = POWER == 1 ? fmaf(amp, s, sum[dz]) : fmaf(amp * amp, s, sum[dz]);
+            }
+        }
+    }
+    float alpha;
+    coef_sf(cf, alpha);
+    const size_t plane = (size_t)g.nx * g.ny;
+#pragma unroll
+    for (int q = 0; q < kSfZ; ++q)
+        if (q < nz) {
+            const size_t idx = (size_t)(kz0 + q) * plane + (size_t)j * g.nx + i;
+            acc[idx] = fmaf(alpha, sum[q], acc[idx]);
+        }
+}
+
+// Number of (ray, voxel) pairs with A_ij > 0.
+template <bool TT>
+__global__ void __launch_bounds__(256) k_sf_count(ProjGeom g, unsigned long long *__restrict__ n) {
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    const int view = blockIdx.z;
+    unsigned long long cnt = 0;
+    if (i < g.nx && j < g.ny) {
+        SfColumn c;
+        if (sf_column<TT>(g, view, i, j, c)) {
+            int nu_nz = 0;
+            for (int k = c.ku0; k <= c.ku1; ++k)
+                nu_nz += trap_cell(c.tau[0], c.tau[1], c.tau[2], c.tau[3], (float)k - 0.5f,
+                                   (float)k + 0.5f) > 0.f;
+            for (int k = 0; k < g.nz; ++k) {
+                float vb[4], amp;
+                sf_axial<TT>(g, c, k, vb, amp);
+                const int kv0 = max(0, (int)floorf(vb[0] + 0.5f));
+                const int kv1 = min(g.nv - 1, (int)floorf(vb[3] + 0.5f));
+                int nv_nz = 0;
+                for (int l = kv0; l <= kv1; ++l)
+                    nv_nz += trap_cell(vb[0], vb[1], vb[2], vb[3], (float)l - 0.5f,
+                                       (float)l + 0.5f) > 0.f;
+                cnt += (unsigned long long)(nu_nz * nv_nz);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(n, cnt);
+}
+
+// out = beta * out + acc (volumes in the caller's layout).
+__global__ void k_sf_axpby(float *__restrict__ out, const float *__restrict__ acc, int64_t n,
+                           float beta) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = beta != 0.f ? fmaf(beta, out[i], acc[i]) : acc[i];
+}
+
+dim3 sf_cols_grid(const ProjGeom &pg, int z) {
+    return dim3((unsigned)((pg.nx + 31) / 32), (unsigned)((pg.ny + 7) / 8), (unsigned)z);
+}
+
+}  // namespace
+
+void sf_view_constants(const ct_geometry_desc &d, const std::vector<double> &ang,
+                       std::vector<float4> &out, float *scal) {
+    // scal: ku = SDD / du, kv = SDD / dv, cu, cv, oz
+    out.resize(2 * ang.size());
+    const double O[3] = {d.off_x, d.off_y, d.off_z};
+    for (size_t k = 0; k < ang.size(); ++k) {
+        const double c = std::cos(ang[k]), s = std::sin(ang[k]);
+        const double src[3] = {d.sid * c, d.sid * s, 0.0};
+        const double eu[2] = {-s, c}, ec[2] = {-c, -s};
+        const double r0[2] = {O[0] - src[0], O[1] - src[1]};
+        const double s0 = r0[0] * eu[0] + r0[1] * eu[1];
+        const double t0 = r0[0] * ec[0] + r0[1] * ec[1];
+        out[2 * k] = make_float4((float)s0, (float)t0, (float)eu[0], (float)eu[1]);
+        out[2 * k + 1] = make_float4((float)ec[0], (float)ec[1], (float)r0[0], (float)r0[1]);
+    }
+    scal[0] = (float)(d.sdd / d.du);
+    scal[1] = (float)(d.sdd / d.dv);
+    scal[2] = (float)(0.5 * (d.nu - 1) - d.det_off_u / d.du);
+    scal[3] = (float)(0.5 * (d.nv - 1) - d.det_off_v / d.dv);
+    scal[4] = (float)d.off_z;
+}
+
+int64_t sf_forward_partials(const ProjGeom &pg) {
+    return (int64_t)vec_grid((int64_t)pg.nviews * pg.nv * pg.nu);
+}
+
+ct_status sf_forward(const ProjGeom &pg, const float *vol, float *p, const float *rho, Coef c,
+                     double *partials, cudaStream_t st) {
+    const int64_t m = (int64_t)pg.nviews * pg.nv * pg.nu;
+    if (c.dev) CT_TRY(launch_scale_dev(p, m, c.dev + 1, st));
+    else CT_TRY(launch_scale(p, m, c.beta, st));
+    const dim3 gr = sf_cols_grid(pg, pg.nviews), bl(32, 8);
+    const bool tt = pg.proj == CT_PROJ_SF_TT, hr = rho != nullptr, unit = vol == nullptr;
+#define CT_SFF(HR, UV, TT_) k_sf_forward<HR, UV, TT_><<<gr, bl, 0, st>>>(pg, vol, p, rho, c)
+    if (tt) {
+        if (hr) { if (unit) CT_SFF(true, true, true); else CT_SFF(true, false, true); }
+        else    { if (unit) CT_SFF(false, true, true); else CT_SFF(false, false, true); }
+    } else {
+        if (hr) { if (unit) CT_SFF(true, true, false); else CT_SFF(true, false, false); }
+        else    { if (unit) CT_SFF(false, true, false); else CT_SFF(false, false, false); }
+    }
+#undef CT_SFF
+    CT_CHECK_LAUNCH();
+    if (partials) CT_TRY(launch_norm2(p, nullptr, m, partials, st));
+    return CT_OK;
+}
+
+ct_status sf_backward(const ProjGeom &pg, const float *e, const float *rho, Coef c, float *acc,
+                      int power, cudaStream_t st) {
+    const dim3 gr = sf_cols_grid(pg, (pg.nz + kSfZ - 1) / kSfZ), bl(32, 8);
+    const bool tt = pg.proj == CT_PROJ_SF_TT, hr = rho != nullptr;
+#define CT_SFB(HR, P, TT_) k_sf_backward<HR, P, TT_><<<gr, bl, 0, st>>>(pg, e, rho, c, acc)
+    if (tt) {
+        if (power == 2) { if (hr) CT_SFB(true, 2, true); else CT_SFB(false, 2, true); }
+        else            { if (hr) CT_SFB(true, 1, true); else CT_SFB(false, 1, true); }
+    } else {
+        if (power == 2) { if (hr) CT_SFB(true, 2, false); else CT_SFB(false, 2, false); }
+        else            { if (hr) CT_SFB(true, 1, false); else CT_SFB(false, 1, false); }
+    }
+#undef CT_SFB
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+ct_status sf_count(const ProjGeom &pg, unsigned long long *d_count, cudaStream_t st) {
+    const dim3 gr = sf_cols_grid(pg, pg.nviews), bl(32, 8);
+    if (pg.proj == CT_PROJ_SF_TT) k_sf_count<true><<<gr, bl, 0, st>>>(pg, d_count);
+    else k_sf_count<false><<<gr, bl, 0, st>>>(pg, d_count);
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+ct_status sf_axpby(float *out, const float *acc, int64_t n, float beta, cudaStream_t st) {
+    if (n <= 0) return CT_OK;
+    k_sf_axpby<<<vec_grid(n), kVecThreads, 0, st>>>(out, acc, n, beta);
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+}  // namespace ct

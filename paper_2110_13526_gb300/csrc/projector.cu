@@ -818,12 +818,14 @@ void set_launch_order(ProjGeom &pg) {
 
 int64_t forward_partials(const ProjGeom &pg) {
     if (empty(pg)) return 0;
+    if (pg.proj != CT_PROJ_SIDDON) return sf_forward_partials(pg);
     dim3 gr = proj_grid(pg);
     return (int64_t)gr.x * gr.y * gr.z;
 }
 
 int64_t forward_direct_partials(const ProjGeom &pg) {
     if (empty(pg)) return 0;
+    if (pg.proj != CT_PROJ_SIDDON) return sf_forward_partials(pg);
     dim3 gr = proj_grid(rays_order(pg));
     return (int64_t)gr.x * gr.y * gr.z;
 }
@@ -831,6 +833,7 @@ int64_t forward_direct_partials(const ProjGeom &pg) {
 ct_status launch_forward(const ProjGeom &pg, const float *vol, const float *vol_t, float *p,
                          const float *rho, Coef c, double *partials, cudaStream_t st) {
     if (empty(pg)) return CT_OK;
+    if (pg.proj != CT_PROJ_SIDDON) return sf_forward(pg, vol, p, rho, c, partials, st);
     dim3 gr = proj_grid(pg), bl = proj_block(pg);
     const bool unit = (vol == nullptr);
     const bool hr = (rho != nullptr), nm = (partials != nullptr);
@@ -924,6 +927,12 @@ ct_status launch_forward_typed(const ProjGeom &pg, const void *vol, const void *
                                void *p, int sdt, const float *rho, Coef c, double *partials,
                                cudaStream_t st) {
     if (empty(pg)) return CT_OK;
+    if (pg.proj != CT_PROJ_SIDDON) {
+        if (vdt != CT_F32 || sdt != CT_F32)
+            return set_error(CT_ERR_INVALID_ARG, "footprint projectors need FP32 storage");
+        return sf_forward(pg, static_cast<const float *>(vol), static_cast<float *>(p), rho, c,
+                          partials, st);
+    }
     switch (vdt) {
         case CT_F32: return fwd_typed_s<float>(pg, vol, vol_t, p, sdt, rho, c, partials, st);
         case CT_BF16:
@@ -937,6 +946,13 @@ ct_status launch_backward_typed(const ProjGeom &pg, const void *e, int sdt, cons
                                 Coef c, void *acc, void *acc_t, int power, bool det,
                                 const float *det_scale, cudaStream_t st) {
     if (empty(pg)) return CT_OK;
+    if (pg.proj != CT_PROJ_SIDDON) {
+        if (sdt != CT_F32 || det)
+            return set_error(CT_ERR_INVALID_ARG,
+                             "footprint projectors need FP32 storage and float accumulation");
+        return sf_backward(pg, static_cast<const float *>(e), rho, c, static_cast<float *>(acc),
+                           power, st);
+    }
     switch (sdt) {
         case CT_F32:
             return back_typed<float>(pg, e, rho, c, acc, acc_t, power, det, det_scale, st);
@@ -951,6 +967,7 @@ ct_status launch_backward_typed(const ProjGeom &pg, const void *e, int sdt, cons
 ct_status launch_backward(const ProjGeom &pg, const float *e, const float *rho, Coef c,
                           float *acc, float *acc_t, int power, cudaStream_t st) {
     if (empty(pg)) return CT_OK;
+    if (pg.proj != CT_PROJ_SIDDON) return sf_backward(pg, e, rho, c, acc, power, st);
     return back_typed<float>(pg, e, rho, c, acc, acc_t, power, false, nullptr, st);
 }
 
@@ -958,12 +975,15 @@ ct_status launch_backward_det(const ProjGeom &pg, const float *e, const float *r
                               long long *acc, long long *acc_t, int power,
                               const float *det_scale, cudaStream_t st) {
     if (empty(pg)) return CT_OK;
+    if (pg.proj != CT_PROJ_SIDDON)
+        return set_error(CT_ERR_INVALID_ARG, "footprint projectors: no fixed-point mode");
     return back_typed<float>(pg, e, rho, c, acc, acc_t, power, true, det_scale, st);
 }
 
 ct_status launch_count(const ProjGeom &pg, unsigned long long *d_count, cudaStream_t st) {
     CT_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st));
     if (empty(pg)) return CT_OK;
+    if (pg.proj != CT_PROJ_SIDDON) return sf_count(pg, d_count, st);
     const ProjGeom pr = rays_order(pg);
     k_count<<<proj_grid(pr), dim3(kTU, kTV), 0, st>>>(pr, d_count);
     CT_CHECK_LAUNCH();
@@ -973,6 +993,12 @@ ct_status launch_count(const ProjGeom &pg, unsigned long long *d_count, cudaStre
 ct_status launch_forward_direct(const ProjGeom &pg, const float *vol, float *p, float alpha,
                                 float beta, double *partials, cudaStream_t st) {
     if (empty(pg)) return CT_OK;
+    if (pg.proj != CT_PROJ_SIDDON) {
+        Coef c;
+        c.alpha = alpha;
+        c.beta = beta;
+        return sf_forward(pg, vol, p, nullptr, c, partials, st);
+    }
     const ProjGeom pr = rays_order(pg);
     k_forward_direct<<<proj_grid(pr), dim3(kTU, kTV), 0, st>>>(pr, vol, p, alpha, beta,
                                                                partials);

@@ -463,6 +463,8 @@ ct_status check_opts(const ct_geometry *g, const float *b, float *x, const ct_so
         return set_error(CT_ERR_INVALID_ARG, "tikhonov_lambda must be finite and >= 0");
     if (o->recompute_every < 0) return set_error(CT_ERR_INVALID_ARG, "recompute_every < 0");
     if (dtype_size(o->storage) == 0) return set_error(CT_ERR_INVALID_ARG, "unknown storage dtype");
+    if (g->pg.proj != CT_PROJ_SIDDON && o->storage != CT_F32)
+        return set_error(CT_ERR_INVALID_ARG, "footprint projectors need FP32 storage");
     return CT_OK;
 }
 

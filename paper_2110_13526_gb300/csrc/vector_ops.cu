@@ -88,6 +88,13 @@ __global__ void __launch_bounds__(256) k_combine(int nx, int ny, float *__restri
     }
 }
 
+__global__ void k_mul(float *__restrict__ out, const float *__restrict__ v,
+                      const float *__restrict__ w, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = v[i] * w[i];
+}
+
 __global__ void k_scale(float *__restrict__ out, int64_t n, float beta) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -239,6 +246,9 @@ int vec_grid(int64_t n) {
 }
 
 int transpose_grid_count(const ProjGeom &pg) {
+    // the footprint projectors accumulate A^T in place; their combine only
+    // takes the norm partials
+    if (pg.proj != CT_PROJ_SIDDON) return vec_grid((int64_t)pg.nx * pg.ny * pg.nz);
     if (pg.cm) {
         const dim3 g = zfast_grid(pg);
         return (int)(g.x * g.y * g.z);
@@ -248,6 +258,15 @@ int transpose_grid_count(const ProjGeom &pg) {
 
 ct_status launch_transpose(const ProjGeom &pg, const float *v, const float *w, float *t,
                            float *out_plain, cudaStream_t st) {
+    if (pg.proj != CT_PROJ_SIDDON) {
+        // the footprint projectors read the caller's layout: only the scaled copy
+        if (!out_plain) return CT_OK;
+        const int64_t n = (int64_t)pg.nx * pg.ny * pg.nz;
+        if (w) return launch_mul(out_plain, v, w, n, st);
+        CT_CUDA_TRY(cudaMemcpyAsync(out_plain, v, (size_t)n * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, st));
+        return CT_OK;
+    }
     if (pg.cm) {
         k_to_zfast<float><<<zfast_grid(pg), dim3(kTile, 8), 0, st>>>(pg.nx, pg.ny, pg.nz, v, w, t,
                                                                      out_plain);
@@ -262,9 +281,20 @@ ct_status launch_transpose(const ProjGeom &pg, const float *v, const float *w, f
 
 ct_status launch_combine(const ProjGeom &pg, float *g, const float *acc_t, const float *w,
                          double *partials, cudaStream_t st) {
+    if (pg.proj != CT_PROJ_SIDDON) {
+        if (!partials) return CT_OK;
+        return launch_norm2(g, w, (int64_t)pg.nx * pg.ny * pg.nz, partials, st);
+    }
     if (pg.cm) return from_zfast<float>(pg, g, 1.f, ZAcc{acc_t, nullptr, nullptr}, w, partials, st);
     dim3 gr((pg.nx + kTile - 1) / kTile, (pg.ny + kTile - 1) / kTile, pg.nz), bl(kTile, 8);
     k_combine<<<gr, bl, 0, st>>>(pg.nx, pg.ny, g, acc_t, w, partials);
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+ct_status launch_mul(float *out, const float *v, const float *w, int64_t n, cudaStream_t st) {
+    if (n <= 0) return CT_OK;
+    k_mul<<<vec_grid(n), kVecThreads, 0, st>>>(out, v, w, n);
     CT_CHECK_LAUNCH();
     return CT_OK;
 }
@@ -456,6 +486,8 @@ ct_status launch_det_scale(const void *e, int edt, const float *rho, int64_t m, 
 ct_status launch_combine_det(const ProjGeom &pg, float *out, float beta, const long long *acc,
                              const long long *acc_t, const double *inv, const float *w,
                              double *partials, cudaStream_t st) {
+    if (pg.proj != CT_PROJ_SIDDON)
+        return set_error(CT_ERR_INVALID_ARG, "footprint projectors: no fixed-point mode");
     if (pg.cm) return from_zfast<float>(pg, out, beta, ZAcc{nullptr, acc_t, inv}, w, partials, st);
     dim3 gr((pg.nx + kTile - 1) / kTile, (pg.ny + kTile - 1) / kTile, pg.nz), bl(kTile, 8);
     k_combine_det<<<gr, bl, 0, st>>>(pg.nx, pg.ny, out, beta, acc, acc_t, inv, w, partials);
@@ -520,6 +552,7 @@ __global__ void __launch_bounds__(256) k_combine_t(int nx, int ny, int64_t nvox,
 
 ct_status launch_transpose_typed(const ProjGeom &pg, const void *v, void *t, int dt,
                                  cudaStream_t st) {
+    if (pg.proj != CT_PROJ_SIDDON) return CT_OK;   // read in place
     if (pg.cm) {
         const dim3 gz = zfast_grid(pg), bz(kTile, 8);
         switch (dt) {
@@ -565,6 +598,12 @@ ct_status launch_combine_typed(const ProjGeom &pg, void *out, int dt, float beta
                                const float *acc_t, const long long *q, const double *inv,
                                cudaStream_t st) {
     const int64_t n = (int64_t)pg.nx * pg.ny * pg.nz;
+    if (pg.proj != CT_PROJ_SIDDON) {
+        if (dt != CT_F32 || q)
+            return set_error(CT_ERR_INVALID_ARG,
+                             "footprint projectors need FP32 storage and float accumulation");
+        return sf_axpby(static_cast<float *>(out), acc, n, beta, st);
+    }
     if (pg.cm) {
         // the column-major backprojection accumulates into the second half
         const ZAcc za{acc_t, q ? q + n : nullptr, inv};

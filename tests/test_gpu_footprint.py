@@ -1,0 +1,153 @@
+"""GPU parity of the separable-footprint projectors (ct_geometry_set_projector
+SF-TR / SF-TT) with the FP64 oracle ``oracle.footprint``, through the C ABI:
+A and A^T element by element, the adjoint identity, nnz, the solvers and
+the preconditioner weights on top of them, and the combinations rejected."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle import footprint as ofp
+from oracle.solvers import cgls as ocgls, inv_sqrt_guarded, lsqr as olsqr, sirt as osirt
+
+pytestmark = pytest.mark.gpu
+
+# FP32 breakpoints: a projected edge |u| pixels from the detector centre is
+# rounded by ~2^-24 |u| (plus the depth division), which moves footprint mass
+# between neighbouring cells; the measured relative L2 errors are below 3e-6.
+TOL = 1e-5
+
+CASES = {
+    "ragged": dict(nx=37, ny=29, nz=21, vx=1.1, vy=0.9, vz=1.3, nu=71, nv=45, du=1.0, dv=1.2,
+                   sid=300.0, sdd=520.0, nviews=17),
+    "offcentre": dict(nx=32, ny=24, nz=16, vx=1.0, vy=1.0, vz=1.0, nu=64, nv=33, du=0.8,
+                      dv=0.8, sid=200.0, sdd=380.0, nviews=11, ox=14.0, oy=-9.0, oz=3.0,
+                      det_off_u=3.3, det_off_v=-2.1),
+    # coarse detector: footprints narrower than a cell; fine detector: wider
+    # than the 8 cells a pass keeps in registers
+    "coarse": dict(nx=20, ny=20, nz=12, vx=1.0, vy=1.0, vz=1.0, nu=13, nv=9, du=4.0, dv=4.0,
+                   sid=150.0, sdd=250.0, nviews=7),
+    "fine": dict(nx=10, ny=9, nz=8, vx=3.0, vy=3.0, vz=3.0, nu=150, nv=120, du=0.25, dv=0.3,
+                 sid=100.0, sdd=180.0, nviews=5),
+}
+
+
+@pytest.fixture(scope="module")
+def ct():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2110_13526_gb300 as m
+    m.lib()
+    return m
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+class SFOperator:
+    """The oracle's SF pair behind the interface of oracle.solvers."""
+
+    def __init__(self, g, kind):
+        self.g, self.kind = g, kind
+
+    def A(self, x):
+        return ofp.project(self.g, x, self.kind)
+
+    def AT(self, y):
+        return ofp.backproject(self.g, y, self.kind)
+
+
+@pytest.mark.parametrize("kind", ["sf_tr", "sf_tt"])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_forward_backward_parity(ct, name, kind):
+    cfg = CASES[name]
+    g, og = ct.Geometry(**cfg, projector=kind), oracle.OGeom(**cfg)
+    k = kind[3:]
+    x = np.abs(synth.random_field(g.vol_shape, seed=50))
+    p = ct.project(g, torch.from_numpy(x).cuda()).cpu().numpy()
+    want = ofp.project(og, x, k)
+    assert np.count_nonzero(want) > 0.3 * want.size
+    assert rel(p, want) < TOL
+    y = synth.random_field(g.sino_shape, seed=51)
+    r = ct.backproject(g, torch.from_numpy(y).cuda()).cpu().numpy()
+    assert rel(r, ofp.backproject(og, y, k)) < TOL
+    # alpha / beta epilogues
+    out = torch.from_numpy(synth.random_field(g.sino_shape, seed=52)).cuda()
+    o0 = out.cpu().numpy()
+    ct.project(g, torch.from_numpy(x).cuda(), out=out, alpha=-0.5, beta=2.0)
+    assert rel(out.cpu().numpy(), -0.5 * want + 2.0 * o0) < TOL
+    vo = torch.from_numpy(synth.random_field(g.vol_shape, seed=53)).cuda()
+    v0 = vo.cpu().numpy()
+    ct.backproject(g, torch.from_numpy(y).cuda(), out=vo, alpha=0.25, beta=-1.0)
+    assert rel(vo.cpu().numpy(), 0.25 * ofp.backproject(og, y, k) - v0) < TOL
+
+
+@pytest.mark.parametrize("kind", ["sf_tr", "sf_tt"])
+def test_adjoint_nnz_and_norm(ct, kind):
+    cfg = CASES["ragged"]
+    g = ct.Geometry(**cfg, projector=kind)
+    x = torch.from_numpy(synth.random_field(g.vol_shape, seed=54)).cuda()
+    y = torch.from_numpy(synth.random_field(g.sino_shape, seed=55)).cuda()
+    lhs = float((ct.project(g, x).double() * y.double()).sum())
+    rhs = float((x.double() * ct.backproject(g, y).double()).sum())
+    scale = float((ct.project(g, x.abs()).double() * y.double().abs()).sum())
+    assert abs(lhs - rhs) <= 2e-6 * scale
+    _, n2 = ct.project_norm2(g, x)
+    assert float(n2) == pytest.approx(float((ct.project(g, x).double() ** 2).sum()), rel=1e-6)
+    # nnz against the dense oracle matrix of a tiny case
+    tiny = dict(nx=4, ny=3, nz=3, vx=1.0, vy=1.2, vz=0.9, nu=9, nv=7, du=0.8, dv=0.7,
+                sid=30.0, sdd=50.0, nviews=3, angles=[0.2, 1.9, 4.0])
+    gt = ct.Geometry(**tiny, projector=kind)
+    M = ofp.dense_matrix(oracle.OGeom(**tiny), kind[3:])
+    assert ct.count_nnz(gt) == int(np.count_nonzero(M))
+
+
+@pytest.mark.parametrize("kind", ["sf_tr", "sf_tt"])
+def test_solvers_and_weights_on_footprints(ct, kind):
+    cfg = CASES["offcentre"]
+    og = oracle.OGeom(**cfg)
+    g = ct.Geometry(**cfg, projector=kind)
+    op = SFOperator(og, kind[3:])
+    x_true = synth.voxelize(synth.random_ellipsoids(5, 3, *synth.box_of(cfg),
+                                                    axis_range=(3.0, 9.0)), cfg)
+    b = op.A(x_true.astype(np.float64))
+    b32 = b.astype(np.float32)
+    bd = torch.from_numpy(b32).cuda()
+    ref = ocgls(op, b32.astype(np.float64), K=10)
+    x, rep = ct.cgls(g, bd, max_iter=10)
+    assert rel(x.cpu().numpy(), ref.x) < 1e-4
+    np.testing.assert_allclose(rep.history, ref.history, rtol=1e-4)
+    ref = olsqr(op, b32.astype(np.float64), K=10)
+    x, rep = ct.lsqr(g, bd, max_iter=10)
+    assert rel(x.cpu().numpy(), ref.x) < 1e-4
+    ref = osirt(op, b32.astype(np.float64), K=6, lam=1.5)
+    x, rep = ct.sirt(g, bd, max_iter=6, relax=1.5)
+    assert rel(x.cpu().numpy(), ref.x) < 1e-4
+    # preconditioner weights R^-1/2, C^-1/2 with R = A 1, C = A^T 1.  A ray that
+    # grazes a voxel corner has a tiny footprint sliver whose FP32 cell
+    # integral carries a large relative error, magnified by the inverse square
+    # root; the weights are compared where the sums are not tiny.
+    wc, wr = ct.precond_weights(g, "rowcol")
+    for w, sums in ((wr, op.A(np.ones(og.vol_shape))), (wc, op.AT(np.ones(og.sino_shape)))):
+        ok = sums > 1e-3 * sums.max()
+        assert ok.mean() > 0.5
+        assert rel(w.cpu().numpy()[ok], inv_sqrt_guarded(sums)[ok]) < 1e-5
+    x, _ = ct.cgls(g, bd, max_iter=8, precond="jacobi")
+    assert torch.isfinite(x).all()
+
+
+def test_rejected_combinations(ct):
+    cfg = CASES["coarse"]
+    g = ct.Geometry(**cfg, projector="sf_tt")
+    bd = torch.zeros(g.sino_shape, device="cuda")
+    with pytest.raises(RuntimeError, match="CT_ERR_INVALID_ARG"):
+        ct.cgls(g, bd, max_iter=3, storage="bf16")
+    with pytest.raises(RuntimeError, match="CT_ERR_INVALID_ARG"):
+        ct.project(g, torch.zeros(g.vol_shape, device="cuda", dtype=torch.float16))
+    with pytest.raises(RuntimeError, match="CT_ERR_INVALID_ARG"):
+        ct.Geometry(**cfg, projector="sf_tt", deterministic=True)
+    gd = ct.Geometry(**cfg, deterministic=True)
+    assert ct.lib().ct_geometry_set_projector(gd.handle, 2) == 1      # CT_ERR_INVALID_ARG
+    assert ct.lib().ct_geometry_set_projector(g.handle, 7) == 1       # unknown projector
