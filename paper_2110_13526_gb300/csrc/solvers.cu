@@ -110,7 +110,7 @@ __global__ void k_norm2_t(const S *__restrict__ v, int64_t n, double *__restrict
 // stored as S.
 // zpart (may be NULL): partial sums of the stored z^2, one per CTA (the
 // lam ||z||^2 term of NP2 with Tikhonov regularisation).
-template <class S>
+template <class S, bool ZNORM>
 __global__ void k_vol_update(float *__restrict__ x, S *__restrict__ z,
                              const float *__restrict__ g, const float *__restrict__ W, int64_t n,
                              const double *__restrict__ a_pend, const double *__restrict__ beta,
@@ -137,12 +137,12 @@ __global__ void k_vol_update(float *__restrict__ x, S *__restrict__ z,
             zn = from_f<S>(fmaf(b, zo, r));
         }
         z[i] = zn;
-        if (zpart) {
+        if (ZNORM) {
             const double q = to_f(zn);
             sq = fma(q, q, sq);
         }
     }
-    if (zpart) {
+    if (ZNORM) {
         const double t = block_sum(sq, sh);
         if (threadIdx.x == 0) zpart[blockIdx.x] = t;
     }
@@ -669,6 +669,17 @@ ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
     const double lam = o->tikhonov_lambda;
     double *zpart = nullptr;               // partials of ||z||^2 for NP2
     if (lam > 0.0) CT_TRY(sv.ws.alloc(&zpart, (size_t)gn));
+    // x = x + alpha d_x (delayed); d_x = r_x + beta d_x (+ ||d_x||^2 partials)
+    auto vol_update = [&](cudaStream_t s, int first) -> ct_status {
+        if (zpart)
+            k_vol_update<ST, true><<<gn, kVecThreads, 0, s>>>(x, z, gv, sv.W, n, &S->a_pend,
+                                                              &S->beta, &S->zs, first, zpart);
+        else
+            k_vol_update<ST, false><<<gn, kVecThreads, 0, s>>>(x, z, gv, sv.W, n, &S->a_pend,
+                                                               &S->beta, &S->zs, first, nullptr);
+        CT_CHECK_LAUNCH();
+        return CT_OK;
+    };
     // r_x = A^T e_b into gv, NR2 partials into sv.part (count returned)
     auto gradient = [&](int first, int64_t *np) -> ct_status {
         if (lam == 0.0) {
@@ -705,9 +716,7 @@ ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
     }
     k_cgls_nr2<<<1, 1024, 0, st>>>(sv.part, nrp, S, 1, mxp, gn);
     CT_CHECK_LAUNCH();
-    k_vol_update<<<gn, kVecThreads, 0, st>>>(x, z, gv, sv.W, n, &S->a_pend, &S->beta, &S->zs,
-                                             1, zpart);
-    CT_CHECK_LAUNCH();
+    CT_TRY(vol_update(st, 1));
     // p_b = A d_x; NP2 (+ lam ||d_x||^2); alpha
     CT_TRY(sv.forward_t(z, sd, Ts, p, sd, one, sv.part));
     k_cgls_np2<<<1, 1024, 0, st>>>(sv.part, nfp, S, zpart, gn, lam);
@@ -741,9 +750,7 @@ ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
         k_cgls_nr2<<<1, 1024, 0, s>>>(sv.part, nrp, S, 0, mxp, gn);
         CT_CHECK_LAUNCH();
         // x = x + alpha d_x (previous iteration); d_x = r_x + beta d_x
-        k_vol_update<<<gn, kVecThreads, 0, s>>>(x, z, gv, sv.W, n, &S->a_pend, &S->beta,
-                                                &S->zs, 0, zpart);
-        CT_CHECK_LAUNCH();
+        CT_TRY(vol_update(s, 0));
         // p_b = A d_x; NP2 (+ lam ||d_x||^2); alpha
         CT_TRY(sv.forward_t(z, sd, Ts, p, sd, one, sv.part));
         k_cgls_np2<<<1, 1024, 0, s>>>(sv.part, nfp, S, zpart, gn, lam);
