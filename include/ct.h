@@ -137,8 +137,10 @@ ct_status ct_project(const ct_geometry *g, const float *d_vol, float *d_sino, fl
 
 /* Backprojection, the exact transpose of ct_project (Algorithm 1 step
  * r_x = A^T e_b):   d_vol = alpha * (A^T d_sino) + beta * d_vol.
- * With beta == 0, d_vol is not read.  Sums are accumulated with float
- * atomics, so the last bits may differ between runs. */
+ * With beta == 0, d_vol is not read.  With the Siddon projector the sums are
+ * accumulated with float atomics, so the last bits may differ between runs
+ * (see ct_geometry_set_deterministic); the footprint projectors gather, and
+ * their backprojection is reproducible. */
 ct_status ct_backproject(const ct_geometry *g, const float *d_sino, float *d_vol, float alpha,
                          float beta, void *stream);
 
@@ -168,8 +170,9 @@ ct_status ct_project_norm2(const ct_geometry *g, const float *d_vol, float *d_si
  * allocator call).  Same arguments and results as ct_project_norm2; the
  * volume is read in place, and the FP64 partial sums live in a fixed 2 MiB
  * device array that every GPU loading the library holds until exit.
- * Limit: nviews * ceil(nu/32) * ceil(nv/8) <= 262144, else
- * CT_ERR_INVALID_ARG with a message saying so.
+ * Limit (Siddon): nviews * ceil(nu/32) * ceil(nv/8) <= 262144, else
+ * CT_ERR_INVALID_ARG with a message saying so; the footprint projectors need
+ * at most 1216 partials.
  * The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress) with the device current; make that first call before
  * any stream capture.  All calls share the array: calls that overlap on the
@@ -184,6 +187,8 @@ ct_status ct_project_norm2_noalloc(const ct_geometry *g, const float *d_vol, flo
  * nonzeros of A (the unit of the ray-voxel update rate).  *out is a HOST
  * int64.  Blocks until done. */
 ct_status ct_count_nnz(const ct_geometry *g, int64_t *out, void *stream);
+/* (With a footprint projector: the (ray, voxel) pairs with a positive
+ * footprint weight.) */
 
 typedef enum {
     CT_PRECOND_NONE = 0,
@@ -217,7 +222,12 @@ typedef struct {
                                 test stay on the data term ||L (b - A x)||.
                                 LSQR: must be 0. */
     int32_t recompute_every; /* k > 0: e_b = b - A x every k updates (CGLS)    */
-    int32_t timing;          /* nonzero: time every A and A^T with CUDA events */
+    int32_t timing;          /* nonzero: time every A and A^T with CUDA events
+                                and launch every kernel directly.  Otherwise
+                                (and with recompute_every == 0) one update is
+                                captured as a CUDA graph on a private stream
+                                and replayed on `stream`, one graph launch per
+                                update; results are the same. */
     int32_t storage;         /* ct_dtype of the Krylov vectors d_x, e_b, p_b
                                 (CGLS; LSQR needs CT_F32).  x and the
                                 backprojection sums stay FP32. */
