@@ -549,6 +549,19 @@ ct_status ct_geometry_set_projector(ct_geometry *g, int32_t kind) {
                              "footprint projectors cannot run in deterministic mode");
         if (g->desc.ny > 65535 * 8)
             return set_error(CT_ERR_INVALID_ARG, "footprint projectors need ny <= 524280");
+        // every voxel corner in front of the source in every view: the
+        // footprint divides by the depth along the central ray
+        const ct_geometry_desc &d = g->desc;
+        double rmax = 0.0;
+        for (int cx = 0; cx < 2; ++cx)
+            for (int cy = 0; cy < 2; ++cy) {
+                const double x = (cx ? 0.5 : -0.5) * d.nx * d.vx + d.off_x;
+                const double y = (cy ? 0.5 : -0.5) * d.ny * d.vy + d.off_y;
+                rmax = std::max(rmax, std::sqrt(x * x + y * y));
+            }
+        if (!(rmax < d.sid))
+            return set_error(CT_ERR_INVALID_ARG,
+                             "footprint projectors need the volume inside the source circle");
         if (!g->d_sf && g->desc.nviews > 0) {
             DeviceGuard dg(g->device);
             CT_TRY(dg.status());

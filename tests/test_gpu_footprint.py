@@ -151,3 +151,6 @@ def test_rejected_combinations(ct):
     gd = ct.Geometry(**cfg, deterministic=True)
     assert ct.lib().ct_geometry_set_projector(gd.handle, 2) == 1      # CT_ERR_INVALID_ARG
     assert ct.lib().ct_geometry_set_projector(g.handle, 7) == 1       # unknown projector
+    # a volume reaching the source: the footprint's depth division is undefined
+    with pytest.raises(RuntimeError, match="source circle"):
+        ct.Geometry(**dict(cfg, sid=12.0, sdd=40.0), projector="sf_tt")
