@@ -120,8 +120,9 @@ ct_status ct_geometry_set_deterministic(ct_geometry *g, int32_t on);
  * ct_backproject_ex and the solvers' storage), cannot be combined with
  * deterministic accumulation (their forward projection scatters with float
  * atomics; their backprojection gathers and is deterministic anyway), and
- * need ny <= 524280.  Change the projector only while no call on this
- * geometry is in flight. */
+ * need ny <= 524280 and the volume's xy extent inside the source circle
+ * (every voxel in front of the source).  Change the projector only while no
+ * call on this geometry is in flight. */
 typedef enum { CT_PROJ_SIDDON = 0, CT_PROJ_SF_TR = 1, CT_PROJ_SF_TT = 2 } ct_projector;
 ct_status ct_geometry_set_projector(ct_geometry *g, int32_t kind);
 
