@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 # FP32 breakpoints: a projected edge |u| pixels from the detector centre is
 # rounded by ~2^-24 |u| (plus the depth division), which moves footprint mass
-# between neighbouring cells; the measured relative L2 errors are below 3e-6.
+# between neighbouring cells; the parity bar of the Siddon pair holds.
 TOL = 1e-5
 
 CASES = {
