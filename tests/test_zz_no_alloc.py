@@ -52,9 +52,10 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def test_noalloc_matches_allocating_entry_point_twice(ct):
+@pytest.mark.parametrize("projector", ["siddon", "sf_tt"])
+def test_noalloc_matches_allocating_entry_point_twice(ct, projector):
     L = ct.lib()
-    g = ct.Geometry(**CFG)
+    g = ct.Geometry(**CFG, projector=projector)
     for call, (seed, alpha, beta) in enumerate([(21, 1.0, 0.0), (22, -0.5, 1.5)]):
         vol = torch.from_numpy(synth.random_field(g.vol_shape, seed=seed)).cuda()
         start = torch.from_numpy(synth.random_field(g.sino_shape, seed=seed + 100)).cuda()
