@@ -21,9 +21,11 @@
 // computes the transaxial footprint once and walks the column in z, adding
 // its contributions to the detector cells with float reductions (the 32
 // lanes of a warp are 32 neighbouring columns, whose footprints are
-// neighbouring cells).  A^T gathers: one thread per column segment of kSfZ
+// neighbouring cells).  A^T gathers: one thread per column segment of kSfZB
 // voxels loops over all views and sums the cells under each voxel's
-// footprint, so every voxel is written once, without reductions.
+// footprint into shared memory, so every voxel is written once, without
+// reductions, and the transaxial footprint of a column is computed once per
+// view and segment.
 // Coordinates are relative to the volume centre (per-view constants computed
 // in FP64 on the host), which keeps the FP32 breakpoints accurate.
 #include <algorithm>
@@ -39,8 +41,7 @@ namespace {
 // take several passes): A 4, A^T 8 (measured at 256^3, 1 mm voxels and
 // pixels, magnification 1.6: footprints of 2-4 cells).
 constexpr int kSfKUF = 4;
-constexpr int kSfKUB = 8;
-constexpr int kSfZ = 8;    // voxels per A^T thread (one column segment)
+constexpr int kSfZB = 16;  // voxels per A^T thread (a column segment; sums in shared memory)
 
 struct SfColumn {
     float tau[4];          // sorted transaxial breakpoints (pixel index units)
@@ -198,68 +199,71 @@ __global__ void __launch_bounds__(256) k_sf_forward(ProjGeom g, const float *__r
 }
 
 // acc[z][y][x] += alpha * sum over views and cells of A_ij^POWER rho_i e_i
-// (e == NULL: e = 1) for kSfZ voxels of one column.
+// (e == NULL: e = 1).  A CTA covers 32 x 8 voxel columns and kSfZB voxels of
+// each column, one thread per column, with its kSfZB sums in shared memory:
+// the transaxial footprint of a column and view is computed once for the
+// whole segment, in passes of kSfKUF cells kept in registers.
 template <bool HAS_RHO, int POWER, bool TT>
 __global__ void __launch_bounds__(256) k_sf_backward(ProjGeom g, const float *__restrict__ e,
                                                      const float *__restrict__ rho, Coef cf,
                                                      float *__restrict__ acc) {
+    __shared__ float sacc[kSfZB][256];
+    const int tid = threadIdx.y * 32 + threadIdx.x;
     const int i = blockIdx.x * 32 + threadIdx.x;
     const int j = blockIdx.y * 8 + threadIdx.y;
-    const int kz0 = blockIdx.z * kSfZ;
-    if (i >= g.nx || j >= g.ny) return;
-    float sum[kSfZ];
+    const int kz0 = blockIdx.z * kSfZB;
+    const int nzs = min(kSfZB, g.nz - kz0);
+    for (int dz = 0; dz < kSfZB; ++dz) sacc[dz][tid] = 0.f;
+    // no CTA-wide synchronisation: every thread touches its own column only
+    if (i < g.nx && j < g.ny) {
+        for (int view = 0; view < g.nviews; ++view) {
+            SfColumn c;
+            if (!sf_column<TT>(g, view, i, j, c)) continue;
+            const size_t vbase = (size_t)view * g.nv * g.nu;
+            for (int k0 = c.ku0; k0 <= c.ku1; k0 += kSfKUF) {
+                float fu[kSfKUF];
+                const int nk = min(kSfKUF, c.ku1 - k0 + 1);
 #pragma unroll
-    for (int q = 0; q < kSfZ; ++q) sum[q] = 0.f;
-    const int nz = min(kSfZ, g.nz - kz0);
-    for (int view = 0; view < g.nviews; ++view) {
-        SfColumn c;
-        if (!sf_column<TT>(g, view, i, j, c)) continue;
-        const size_t vbase = (size_t)view * g.nv * g.nu;
-        for (int k0 = c.ku0; k0 <= c.ku1; k0 += kSfKUB) {
-            float fu[kSfKUB];
-            const int nk = min(kSfKUB, c.ku1 - k0 + 1);
+                for (int q = 0; q < kSfKUF; ++q)
+                    fu[q] = q < nk ? trap_cell(c.tau[0], c.tau[1], c.tau[2], c.tau[3],
+                                               (float)(k0 + q) - 0.5f, (float)(k0 + q) + 0.5f)
+                                   : 0.f;
+                for (int dz = 0; dz < nzs; ++dz) {
+                    float vb[4], amp;
+                    sf_axial<TT>(g, c, kz0 + dz, vb, amp);
+                    const int kv0 = max(0, (int)floorf(vb[0] + 0.5f));
+                    const int kv1 = min(g.nv - 1, (int)floorf(vb[3] + 0.5f));
+                    float s = 0.f;
+                    for (int l = kv0; l <= kv1; ++l) {
+                        const float fv = trap_cell(vb[0], vb[1], vb[2], vb[3], (float)l - 0.5f,
+                                                   (float)l + 0.5f);
+                        if (fv == 0.f) continue;
+                        const size_t row = vbase + (size_t)l * g.nu + k0;
+                        float su = 0.f;
 #pragma unroll
-            for (int q = 0; q < kSfKUB; ++q)
-                fu[q] = q < nk ? trap_cell(c.tau[0], c.tau[1], c.tau[2], c.tau[3],
-                                           (float)(k0 + q) - 0.5f, (float)(k0 + q) + 0.5f)
-                               : 0.f;
-#pragma unroll
-            for (int dz = 0; dz < kSfZ; ++dz) {
-                if (dz >= nz) break;
-                float vb[4], amp;
-                sf_axial<TT>(g, c, kz0 + dz, vb, amp);
-                const int kv0 = max(0, (int)floorf(vb[0] + 0.5f));
-                const int kv1 = min(g.nv - 1, (int)floorf(vb[3] + 0.5f));
-                float s = 0.f;
-                for (int l = kv0; l <= kv1; ++l) {
-                    const float fv = trap_cell(vb[0], vb[1], vb[2], vb[3], (float)l - 0.5f,
-                                               (float)l + 0.5f);
-                    if (fv == 0.f) continue;
-                    const size_t row = vbase + (size_t)l * g.nu;
-                    float su = 0.f;
-#pragma unroll
-                    for (int q = 0; q < kSfKUB; ++q) {
-                        if (q < nk && fu[q] != 0.f) {
-                            float w = e ? e[row + k0 + q] : 1.f;
-                            if (HAS_RHO) w *= rho[row + k0 + q];
-                            su = POWER == 1 ? fmaf(fu[q], w, su) : fmaf(fu[q] * fu[q], w, su);
+                        for (int q = 0; q < kSfKUF; ++q) {
+                            if (q < nk && fu[q] != 0.f) {
+                                float w = e ? e[row + q] : 1.f;
+                                if (HAS_RHO) w *= rho[row + q];
+                                su = POWER == 1 ? fmaf(fu[q], w, su) : fmaf(fu[q] * fu[q], w, su);
+                            }
                         }
+                        s = POWER == 1 ? fmaf(fv, su, s) : fmaf(fv * fv, su, s);
                     }
-                    s = POWER == 1 ? fmaf(fv, su, s) : fmaf(fv * fv, su, s);
+                    if (s != 0.f)
+                        sacc[dz][tid] = POWER == 1 ? fmaf(amp, s, sacc[dz][tid])
+                                                   : fmaf(amp * amp, s, sacc[dz][tid]);
                 }
-                sum[dz] = POWER == 1 ? fmaf(amp, s, sum[dz]) : fmaf(amp * amp, s, sum[dz]);
             }
         }
-    }
-    float alpha;
-    coef_sf(cf, alpha);
-    const size_t plane = (size_t)g.nx * g.ny;
-#pragma unroll
-    for (int q = 0; q < kSfZ; ++q)
-        if (q < nz) {
-            const size_t idx = (size_t)(kz0 + q) * plane + (size_t)j * g.nx + i;
-            acc[idx] = fmaf(alpha, sum[q], acc[idx]);
+        float alpha;
+        coef_sf(cf, alpha);
+        const size_t plane = (size_t)g.nx * g.ny;
+        for (int dz = 0; dz < nzs; ++dz) {
+            const size_t idx = (size_t)(kz0 + dz) * plane + (size_t)j * g.nx + i;
+            acc[idx] = fmaf(alpha, sacc[dz][tid], acc[idx]);
         }
+    }
 }
 
 // Number of (ray, voxel) pairs with A_ij > 0.
@@ -356,7 +360,7 @@ ct_status sf_forward(const ProjGeom &pg, const float *vol, float *p, const float
 
 ct_status sf_backward(const ProjGeom &pg, const float *e, const float *rho, Coef c, float *acc,
                       int power, cudaStream_t st) {
-    const dim3 gr = sf_cols_grid(pg, (pg.nz + kSfZ - 1) / kSfZ), bl(32, 8);
+    const dim3 gr = sf_cols_grid(pg, (pg.nz + kSfZB - 1) / kSfZB), bl(32, 8);
     const bool tt = pg.proj == CT_PROJ_SF_TT, hr = rho != nullptr;
 #define CT_SFB(HR, P, TT_) k_sf_backward<HR, P, TT_><<<gr, bl, 0, st>>>(pg, e, rho, c, acc)
     if (tt) {
