@@ -588,13 +588,14 @@ struct UpdateGraph {
     cudaStream_t cs = nullptr;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaStream_t last = nullptr;  // stream of the last replay
+    cudaStream_t last = nullptr;  // stream of the last replay (may be the legacy stream)
+    bool launched = false;
     long long nk = 0;             // kernels per replay (ct_kernel_launches)
     UpdateGraph() = default;
     UpdateGraph(const UpdateGraph &) = delete;
     UpdateGraph &operator=(const UpdateGraph &) = delete;
     ~UpdateGraph() {
-        if (last) cudaStreamSynchronize(last);   // replays finish before the graph goes
+        if (launched) cudaStreamSynchronize(last);   // replays finish before the graph goes
         if (exec) cudaGraphExecDestroy(exec);
         if (g) cudaGraphDestroy(g);
         if (cs) cudaStreamDestroy(cs);
@@ -627,6 +628,7 @@ struct UpdateGraph {
     ct_status launch(cudaStream_t st) {
         CT_CUDA_TRY(cudaGraphLaunch(exec, st));
         last = st;
+        launched = true;
         note_launches(nk);
         return CT_OK;
     }
