@@ -146,9 +146,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_for(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel source changed since the counters were taken."""
+def ncu_counters(kernel: str):
+    """The committed ncu counters of a projector kernel (DRAM bytes per launch,
+    L1 and L2 hit rates), or None when the kernel source changed since they
+    were taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_2110_13526_gb300", "csrc", "projector.cu")
     try:
@@ -157,10 +158,29 @@ def traffic_for(kernel: str):
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
         ent = d.get(kernel)
         if ent and ent.get("projector_sha256") == sha:
-            return float(ent["dram_bytes_per_launch"])
+            return ent
     except Exception:
         pass
     return None
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, or None."""
+    ent = ncu_counters(kernel)
+    return float(ent["dram_bytes_per_launch"]) if ent else None
+
+
+def kernel_report(kernel: str, seconds: float, nnz: int, algo_bytes: float) -> dict:
+    """Per-kernel figures: live CUDA-event time, ray-voxel updates per second
+    and effective gather bandwidth; DRAM bandwidth (ncu bytes over the live
+    time) and L1/L2 hit rates from the committed ncu counters."""
+    ent = ncu_counters(kernel) or {}
+    dram = ent.get("dram_bytes_per_launch")
+    return {"ms_per_launch": seconds * 1e3, "gray_voxel_per_s": nnz / seconds / 1e9,
+            "effective_gbs": algo_bytes / seconds / 1e9,
+            "dram_gbs": dram / seconds / 1e9 if dram is not None else None,
+            "l1_hit_rate": ent.get("l1_hit_rate"), "l2_hit_rate": ent.get("l2_hit_rate"),
+            "counters": "ncu" if ent else None}
 
 
 PHANTOM_SEED = {"B256": 1, "P512": 2}
@@ -318,6 +338,8 @@ def run_ours(a):
                        "nnz": nnz},
             "gray_voxel_per_s": {"A": nnz / t_f / 1e9, "AT": nnz / t_b / 1e9},
             "ms_per_op": {"A": t_f * 1e3, "AT": t_b * 1e3},
+            "kernels": {"k_forward_cm": kernel_report("k_forward_cm", t_f, nnz, bytes_f),
+                        "k_backward_cm": kernel_report("k_backward_cm", t_b, nnz, bytes_b)},
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": "iters/s",
                     "h2d_bytes_per_step": 4 * n_rays, "d2h_bytes_per_step": 4 * n_vox},
