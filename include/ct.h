@@ -285,6 +285,55 @@ typedef struct {
 ct_status ct_sirt(const ct_geometry *g, const float *d_b, float *d_x, const ct_sirt_opts *opts,
                   ct_solver_report *report, void *stream);
 
+/* ---- batched CGLS (continuous batching of several solves) ----------------
+ *
+ * A ct_batch advances several independent CGLS solves (Algorithm 1, each
+ * with its own geometry, data and options) in lock step: every
+ * ct_batch_step performs one x update of every active job.  The A^T of all
+ * jobs whose geometry uses the column-major Siddon kernels runs as ONE
+ * persistent kernel launch over all their rays (jobs with fixed-point
+ * backprojection in a second one), and likewise their A; the other jobs
+ * (ray-major geometries, footprint projectors) launch their own projectors
+ * inside the same step.  The step of a fixed set of jobs is captured as a
+ * CUDA graph and replayed until a job joins or leaves.  Each job's arithmetic
+ * is exactly that of ct_cgls with the same arguments, tile for tile: with a
+ * deterministic geometry (ct_geometry_set_deterministic) x and the report are
+ * bitwise those of a ct_cgls call; with float-atomic backprojection they
+ * agree to the run-to-run rounding of the atomics.
+ *
+ * Jobs join between steps (ct_batch_add_cgls) and leave when their stopping
+ * rule fires (i = K or NB / NB0 <= ERR, tested after every step) or when
+ * removed.  A batch belongs to the device current at ct_batch_create and to
+ * one host thread at a time; all its work is enqueued on `stream`.  The
+ * caller keeps every geometry, d_b and d_x alive until the job is removed or
+ * the batch destroyed.  Device workspace per job: that of ct_cgls. */
+typedef struct ct_batch ct_batch;
+
+/* New empty batch whose work runs on `stream` (a cudaStream_t, NULL = the
+ * legacy default stream).  Free with ct_batch_destroy. */
+ct_status ct_batch_create(void *stream, ct_batch **out);
+/* Waits for the batch's stream, then frees the batch and its jobs' workspace
+ * (the x of an unfinished job keeps its last completed update).  NULL: no-op. */
+ct_status ct_batch_destroy(ct_batch *b);
+/* Adds a CGLS job: d_b (device, read only) and d_x (device, in = x0, out = x)
+ * as for ct_cgls, opts with storage CT_F32, timing 0 and recompute_every 0
+ * (else CT_ERR_INVALID_ARG).  Runs the initialisation and the first update
+ * on the batch's stream before returning (blocking), and returns the job's
+ * id in *job.  A job whose stopping rule already holds is done at once. */
+ct_status ct_batch_add_cgls(ct_batch *b, const ct_geometry *g, const float *d_b, float *d_x,
+                            const ct_solver_opts *opts, int32_t *job);
+/* One x update of every active job, then the stopping rules (one host wait
+ * for the jobs with err_tol > 0).  *n_active: jobs still active afterwards.
+ * A job that stops here gets its final x and report (blocking). */
+ct_status ct_batch_step(ct_batch *b, int32_t *n_active);
+/* *done = 1 once job has stopped; then, if report is not NULL, fills it as
+ * ct_cgls would (history_nb / history_cap are the caller's, as there).  An
+ * unknown id is CT_ERR_INVALID_ARG. */
+ct_status ct_batch_poll(ct_batch *b, int32_t job, int32_t *done, ct_solver_report *report);
+/* Removes a job (finishing its x first if it is still active) and frees its
+ * workspace; returns after the batch's stream has drained. */
+ct_status ct_batch_remove(ct_batch *b, int32_t job);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char *ct_last_error(void);
 

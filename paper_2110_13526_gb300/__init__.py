@@ -41,7 +41,9 @@ EXPORTS = ("ct_geometry_create", "ct_geometry_destroy", "ct_geometry_sizes", "ct
            "ct_backproject", "ct_project_norm2", "ct_count_nnz", "ct_precond_weights",
            "ct_cgls", "ct_lsqr", "ct_last_error", "ct_version", "ct_kernel_launches",
            "ct_project_norm2_noalloc", "ct_geometry_set_deterministic", "ct_project_ex",
-           "ct_backproject_ex", "ct_sirt", "ct_geometry_set_projector")
+           "ct_backproject_ex", "ct_sirt", "ct_geometry_set_projector", "ct_batch_create",
+           "ct_batch_destroy", "ct_batch_add_cgls", "ct_batch_step", "ct_batch_poll",
+           "ct_batch_remove")
 
 
 class CTError(RuntimeError):
@@ -131,6 +133,14 @@ def lib():
                                ctypes.c_float, vp], ctypes.c_int),
             "ct_backproject_ex": ([vp, vp, ctypes.c_int32, vp, ctypes.c_int32, ctypes.c_float,
                                    ctypes.c_float, vp], ctypes.c_int),
+            "ct_batch_create": ([vp, P(vp)], ctypes.c_int),
+            "ct_batch_destroy": ([vp], ctypes.c_int),
+            "ct_batch_add_cgls": ([vp, vp, vp, vp, P(SolverOpts), P(ctypes.c_int32)],
+                                  ctypes.c_int),
+            "ct_batch_step": ([vp, P(ctypes.c_int32)], ctypes.c_int),
+            "ct_batch_poll": ([vp, ctypes.c_int32, P(ctypes.c_int32), P(_Report)],
+                              ctypes.c_int),
+            "ct_batch_remove": ([vp, ctypes.c_int32], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -362,6 +372,98 @@ def cgls(g: Geometry, b: torch.Tensor, x0: Optional[torch.Tensor] = None, max_it
     the data discrepancy)."""
     return _solve(lib().ct_cgls, g, b, x0, max_iter, err_tol, precond, recompute_every, timing,
                   stream, storage, tikhonov)
+
+
+class Batch:
+    """Several CGLS solves advanced in lock step (ct_batch): every ``step()``
+    performs one x update of each active job, with the projectors of all
+    column-major Siddon jobs in one batched launch per operator.  Jobs join
+    with ``add`` between steps and leave when their stopping rule fires.
+
+    All work runs on ``stream`` (default: the current stream at creation).
+    One host thread at a time."""
+
+    def __init__(self, stream=None):
+        self._stream = torch.cuda.current_stream() if stream is None else stream
+        self._device = self._stream.device
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self._device):
+            _check(lib().ct_batch_create(ctypes.c_void_p(self._stream.cuda_stream),
+                                         ctypes.byref(h)))
+        self._h = h
+        self._jobs = {}   # id -> (geometry, b, x, host, max_iter)
+
+    def add(self, g: Geometry, b: torch.Tensor, x0: Optional[torch.Tensor] = None,
+            max_iter: int = 20, err_tol: float = 0.0, precond="none",
+            tikhonov: float = 0.0) -> int:
+        """Admit a CGLS job (initialisation and first update run now); returns its id."""
+        host = not b.is_cuda
+        with torch.cuda.device(self._device), torch.cuda.stream(self._stream):
+            bd = _dev(b, g.sino_shape, "b", g.device)
+            if x0 is None:
+                x = torch.zeros(g.vol_shape, dtype=torch.float32, device=g.device)
+            else:
+                x = _dev(x0, g.vol_shape, "x0", g.device).clone()
+        opts = SolverOpts(int(max_iter), float(err_tol), _PRECOND[precond], float(tikhonov),
+                          0, 0, 0)
+        jid = ctypes.c_int32(0)
+        _check(lib().ct_batch_add_cgls(self.handle, g.handle, _ptr(bd), _ptr(x),
+                                       ctypes.byref(opts), ctypes.byref(jid)))
+        self._jobs[jid.value] = (g, bd, x, host, int(max_iter))
+        return jid.value
+
+    def step(self) -> int:
+        """One update of every active job; returns the number still active."""
+        n = ctypes.c_int32(0)
+        _check(lib().ct_batch_step(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def done(self, job: int) -> bool:
+        d = ctypes.c_int32(0)
+        _check(lib().ct_batch_poll(self.handle, int(job), ctypes.byref(d), None))
+        return bool(d.value)
+
+    def result(self, job: int, remove: bool = True):
+        """(x, SolveReport) of a finished job (None while it runs); by default
+        the job then leaves the batch."""
+        _, _, x, host, k = self._jobs[job]
+        hist = (ctypes.c_double * max(k, 1))()
+        rep = _Report(0, 0.0, 0.0, ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)),
+                      max(k, 1), 0, 0, 0.0, 0.0)
+        d = ctypes.c_int32(0)
+        _check(lib().ct_batch_poll(self.handle, int(job), ctypes.byref(d), ctypes.byref(rep)))
+        if not d.value:
+            return None
+        r = SolveReport(rep.iterations, rep.nb0, rep.nb, list(hist[:rep.iterations]),
+                        rep.n_forward, rep.n_back, rep.ms_forward, rep.ms_back)
+        if remove:
+            self.remove(job)
+        return (x.cpu() if host else x), r
+
+    def remove(self, job: int):
+        _check(lib().ct_batch_remove(self.handle, int(job)))
+        self._jobs.pop(job, None)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("batch is closed")
+        return self._h
+
+    def active(self) -> int:
+        return sum(not self.done(j) for j in self._jobs)
+
+    def close(self):
+        if self._h is not None:
+            _check(lib().ct_batch_destroy(self._h))
+            self._h = None
+            self._jobs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sirt(g: Geometry, b: torch.Tensor, x0: Optional[torch.Tensor] = None, max_iter: int = 20,

@@ -157,6 +157,36 @@ ct_status launch_forward(const ProjGeom &pg, const float *vol, const float *vol_
 ct_status launch_backward(const ProjGeom &pg, const float *e, const float *rho, Coef c,
                           float *acc, float *acc_t, int power, cudaStream_t st);
 
+// One job of a batched projector launch (launch_batch): a column-major
+// Siddon geometry (batchable) with its vectors.  A: in = the [y][x][z] copy
+// of the volume, out = p (FP32), partials = FP64 sums of p^2 per tile (or
+// NULL).  A^T: in = e (FP32), out = the [y][x][z] accumulator (float, or
+// int64 fixed point with det_scale).  rho may be NULL.
+struct BatchJob {
+    ProjGeom g;              // with the launch order of the operator (batch_job_grid)
+    const void *in;
+    void *out;
+    const float *rho;
+    Coef c;
+    double *partials;
+    const float *det_scale;
+    unsigned tile0;          // first tile of the job in the batch's tile sequence
+    unsigned gx, gy;         // the job's grid (x, y); z = tiles / (gx gy)
+    unsigned tiles;
+};
+// Can A and A^T of this geometry join a batched launch?
+bool batchable(const ProjGeom &pg);
+// Fills g, gx, gy, tiles of *b for A (backward = false) or A^T.
+ct_status batch_job_grid(const ProjGeom &pg, bool backward, BatchJob *b);
+// Finds the resident CTAs of the batched kernels on the current device; call
+// once per device before launch_batch, outside stream capture.
+ct_status batch_prepare();
+// One persistent launch over the ntiles tiles of njobs jobs (device table
+// d_jobs, tile0 ascending, the same operator for all).  flag: A -> FP64 norm
+// partials, A^T -> fixed-point sums.  d_next: a device counter (reset here).
+ct_status launch_batch(const BatchJob *d_jobs, int njobs, unsigned ntiles, bool backward,
+                       bool flag, unsigned *d_next, cudaStream_t st);
+
 // Count the (ray, voxel) pairs with positive length into *d_count (int64).
 ct_status launch_count(const ProjGeom &pg, unsigned long long *d_count, cudaStream_t st);
 

@@ -39,6 +39,7 @@
 // Either way the warp's gathers (and the backprojector's reductions) fall on
 // one or two 128-byte lines.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <type_traits>
 
@@ -486,12 +487,15 @@ __global__ void __launch_bounds__(kTU *kTV) k_forward_direct(ProjGeom g,
 // not fit this scheme; geometries that have any use the ray-major kernels
 // above instead (ProjGeom::cm).
 
-__device__ __forceinline__ void tile_of_cm(const ProjGeom &g, int &u, int &v, int &view) {
-    const int grp = (int)blockIdx.z / g.nvb;
-    const int vb = (int)blockIdx.z - grp * g.nvb;
-    u = blockIdx.x * kCU + threadIdx.y;
+// Tile (bx, by, bz) of the projector grid (blockIdx in a plain launch; a
+// batched launch maps its work items onto each job's grid).
+__device__ __forceinline__ void tile_of_cm(const ProjGeom &g, uint3 bid, int &u, int &v,
+                                           int &view) {
+    const int grp = (int)bid.z / g.nvb;
+    const int vb = (int)bid.z - grp * g.nvb;
+    u = bid.x * kCU + threadIdx.y;
     v = vb * kCV + threadIdx.x;
-    view = grp * g.vgroup + (int)blockIdx.y;
+    view = grp * g.vgroup + (int)bid.y;
 }
 
 // One warp's column (the same in all lanes) and one lane's row of it.
@@ -663,17 +667,17 @@ __device__ __forceinline__ void walk_cm(const CmRay &r, bool ok, Fn &&fn) {
     for (; k <= ke; ++k) slab(clamped{});
 }
 
-// p = alpha * rho o (A vol) + beta * p from the [y][x][z] copy vol_z (NULL:
-// the all-ones volume).
-template <bool HAS_RHO, bool NORM, bool UNIT_VOL, class TV = float, class TS = float>
-__global__ void __launch_bounds__(kCU *kCV, 5) k_forward_cm(ProjGeom g,
-                                                         const TV *__restrict__ vol_z,
-                                                         TS *__restrict__ out,
-                                                         const float *__restrict__ rho, Coef c,
-                                                         double *__restrict__ partials) {
-    __shared__ double sh[32];
+// One tile of p = alpha * rho o (A vol) + beta * p from the [y][x][z] copy
+// vol_z (NULL: the all-ones volume); with NORM the tile's FP64 sum of p^2
+// goes to partials[tile index in grid gdim].  All threads of the CTA call it.
+template <bool HAS_RHO, bool NORM, bool UNIT_VOL, class TV, class TS>
+__device__ __forceinline__ void forward_cm_tile(const ProjGeom &g, uint3 bid, uint3 gdim,
+                                                const TV *__restrict__ vol_z,
+                                                TS *__restrict__ out,
+                                                const float *__restrict__ rho, const Coef &c,
+                                                double *__restrict__ partials, double *sh) {
     int u, v, view;
-    tile_of_cm(g, u, v, view);
+    tile_of_cm(g, bid, u, v, view);
     const bool col_live = (u < g.nu) && (view < g.nviews);
     CmRay r;
     const bool ok = cm_setup(g, view, u, v, col_live, r);
@@ -704,21 +708,33 @@ __global__ void __launch_bounds__(kCU *kCV, 5) k_forward_cm(ProjGeom g,
     if (NORM) {
         double t = block_sum_d(sq, sh);
         if (threadIdx.x == 0 && threadIdx.y == 0)
-            partials[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = t;
+            partials[bid.x + gdim.x * (bid.y + (size_t)gdim.y * bid.z)] = t;
     }
 }
 
-// acc_z ([y][x][z]) += the k_backward contributions of the column-major rays.
-template <bool HAS_RHO, int POWER, bool DET, class TS = float>
-__global__ void __launch_bounds__(kCU *kCV, 5) k_backward_cm(ProjGeom g,
-                                                          const TS *__restrict__ e,
-                                                          const float *__restrict__ rho, Coef c,
-                                                          void *__restrict__ acc_z,
-                                                          const float *__restrict__ det_scale) {
+template <bool HAS_RHO, bool NORM, bool UNIT_VOL, class TV = float, class TS = float>
+__global__ void __launch_bounds__(kCU *kCV, 5) k_forward_cm(ProjGeom g,
+                                                         const TV *__restrict__ vol_z,
+                                                         TS *__restrict__ out,
+                                                         const float *__restrict__ rho, Coef c,
+                                                         double *__restrict__ partials) {
+    __shared__ double sh[32];
+    forward_cm_tile<HAS_RHO, NORM, UNIT_VOL, TV, TS>(g, blockIdx, gridDim, vol_z, out, rho, c,
+                                                     partials, sh);
+}
+
+// One tile of acc_z ([y][x][z]) += the k_backward contributions of the
+// column-major rays.  No CTA-wide synchronisation.
+template <bool HAS_RHO, int POWER, bool DET, class TS>
+__device__ __forceinline__ void backward_cm_tile(const ProjGeom &g, uint3 bid,
+                                                 const TS *__restrict__ e,
+                                                 const float *__restrict__ rho, const Coef &c,
+                                                 void *__restrict__ acc_z,
+                                                 const float *__restrict__ det_scale) {
     int u, v, view;
-    tile_of_cm(g, u, v, view);
+    tile_of_cm(g, bid, u, v, view);
     const bool col_live = (u < g.nu) && (view < g.nviews);
-    if (!col_live) return;   // warp-uniform; no CTA-wide synchronisation follows
+    if (!col_live) return;   // warp-uniform
     CmRay r;
     const bool ok = cm_setup(g, view, u, v, col_live, r);
     float alpha, beta;
@@ -746,6 +762,83 @@ __global__ void __launch_bounds__(kCU *kCV, 5) k_backward_cm(ProjGeom g,
             const float lm = l * ls;
             red_add_if(base + o, POWER == 1 ? w * l : w * lm * lm, p && nz);
         });
+    }
+}
+
+template <bool HAS_RHO, int POWER, bool DET, class TS = float>
+__global__ void __launch_bounds__(kCU *kCV, 5) k_backward_cm(ProjGeom g,
+                                                          const TS *__restrict__ e,
+                                                          const float *__restrict__ rho, Coef c,
+                                                          void *__restrict__ acc_z,
+                                                          const float *__restrict__ det_scale) {
+    backward_cm_tile<HAS_RHO, POWER, DET, TS>(g, blockIdx, e, rho, c, acc_z, det_scale);
+}
+
+// ---- batched launches over several jobs -------------------------------------
+// A persistent grid (resident CTAs only) takes tiles from a work counter in
+// order: the tiles of job 0 in its own grid order, then those of job 1, and
+// so on.  A tile runs exactly the code of a plain launch on that job (the
+// same rays per CTA, the same partial sums in the same slots), so each job's
+// result is the one of its own launch: bitwise for A and for fixed-point
+// A^T.  Several small jobs thus share one launch and fill the GPU together.
+
+// Next tile of the CTA (the same in all its threads), or UINT_MAX when none.
+__device__ __forceinline__ unsigned next_tile(unsigned *next, unsigned ntiles, unsigned *slot) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) *slot = atomicAdd(next, 1u);
+    __syncthreads();
+    const unsigned t = *slot;
+    __syncthreads();   // read by all before thread 0 overwrites it
+    return t < ntiles ? t : UINT_MAX;
+}
+
+// The job owning tile t (jobs sorted by tile0) and the tile within its grid.
+__device__ __forceinline__ const BatchJob &job_of(const BatchJob *__restrict__ jobs, int njobs,
+                                                  unsigned t, uint3 &bid, uint3 &gdim) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {   // the last job with tile0 <= t
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+    }
+    const BatchJob &b = jobs[lo];
+    const unsigned lt = t - b.tile0;
+    gdim = make_uint3(b.gx, b.gy, 0u);
+    bid = make_uint3(lt % b.gx, (lt / b.gx) % b.gy, lt / (b.gx * b.gy));
+    return b;
+}
+
+template <bool NORM>
+__global__ void __launch_bounds__(kCU *kCV, 5) k_forward_cm_batch(
+    const BatchJob *__restrict__ jobs, int njobs, unsigned ntiles, unsigned *__restrict__ next) {
+    __shared__ double sh[32];
+    __shared__ unsigned slot;
+    for (unsigned t = next_tile(next, ntiles, &slot); t != UINT_MAX;
+         t = next_tile(next, ntiles, &slot)) {
+        uint3 bid, gdim;
+        const BatchJob &b = job_of(jobs, njobs, t, bid, gdim);
+        const float *vz = static_cast<const float *>(b.in);
+        float *out = static_cast<float *>(b.out);
+        if (b.rho)
+            forward_cm_tile<true, NORM, false, float, float>(b.g, bid, gdim, vz, out, b.rho, b.c,
+                                                            b.partials, sh);
+        else
+            forward_cm_tile<false, NORM, false, float, float>(b.g, bid, gdim, vz, out, nullptr,
+                                                             b.c, b.partials, sh);
+    }
+}
+
+template <bool DET>
+__global__ void __launch_bounds__(kCU *kCV, 5) k_backward_cm_batch(
+    const BatchJob *__restrict__ jobs, int njobs, unsigned ntiles, unsigned *__restrict__ next) {
+    __shared__ unsigned slot;
+    for (unsigned t = next_tile(next, ntiles, &slot); t != UINT_MAX;
+         t = next_tile(next, ntiles, &slot)) {
+        uint3 bid, gdim;
+        const BatchJob &b = job_of(jobs, njobs, t, bid, gdim);
+        const float *e = static_cast<const float *>(b.in);
+        if (b.rho)
+            backward_cm_tile<true, 1, DET, float>(b.g, bid, e, b.rho, b.c, b.out, b.det_scale);
+        else
+            backward_cm_tile<false, 1, DET, float>(b.g, bid, e, nullptr, b.c, b.out, b.det_scale);
     }
 }
 
@@ -978,6 +1071,69 @@ ct_status launch_backward_det(const ProjGeom &pg, const float *e, const float *r
     if (pg.proj != CT_PROJ_SIDDON)
         return set_error(CT_ERR_INVALID_ARG, "footprint projectors: no fixed-point mode");
     return back_typed<float>(pg, e, rho, c, acc, acc_t, power, true, det_scale, st);
+}
+
+bool batchable(const ProjGeom &pg) { return pg.proj == CT_PROJ_SIDDON && pg.cm && !empty(pg); }
+
+ct_status batch_job_grid(const ProjGeom &pg, bool backward, BatchJob *b) {
+    if (!batchable(pg)) return set_error(CT_ERR_INVALID_ARG, "geometry cannot be batched");
+    b->g = backward ? back_order(pg) : pg;
+    const dim3 gr = proj_grid(b->g);
+    b->gx = gr.x;
+    b->gy = gr.y;
+    b->tiles = gr.x * gr.y * gr.z;
+    return CT_OK;
+}
+
+namespace {
+constexpr int kMaxDevices = 64;
+// Resident CTAs of the four batched kernels per device (0: not yet known),
+// found by batch_prepare outside any stream capture.
+std::atomic<int> g_batch_grid[kMaxDevices][4];
+
+template <class K>
+ct_status resident_ctas(K kernel, int dev, int *grid) {
+    int sms = 0, per_sm = 0;
+    CT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kCU * kCV, 0));
+    *grid = std::max(1, sms * std::max(per_sm, 1));
+    return CT_OK;
+}
+}  // namespace
+
+ct_status batch_prepare() {
+    int dev = 0;
+    CT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return set_error(CT_ERR_INVALID_ARG, "device index");
+    int gr[4];
+    CT_TRY(resident_ctas(k_backward_cm_batch<false>, dev, &gr[0]));
+    CT_TRY(resident_ctas(k_backward_cm_batch<true>, dev, &gr[1]));
+    CT_TRY(resident_ctas(k_forward_cm_batch<false>, dev, &gr[2]));
+    CT_TRY(resident_ctas(k_forward_cm_batch<true>, dev, &gr[3]));
+    for (int k = 0; k < 4; ++k) g_batch_grid[dev][k].store(gr[k]);
+    return CT_OK;
+}
+
+ct_status launch_batch(const BatchJob *d_jobs, int njobs, unsigned ntiles, bool backward,
+                       bool flag, unsigned *d_next, cudaStream_t st) {
+    if (njobs <= 0 || ntiles == 0) return CT_OK;
+    int dev = 0;
+    CT_CUDA_TRY(cudaGetDevice(&dev));
+    const int which = (backward ? 0 : 2) + (flag ? 1 : 0);
+    const int resident = (dev >= 0 && dev < kMaxDevices) ? g_batch_grid[dev][which].load() : 0;
+    if (resident <= 0) return set_error(CT_ERR_INVALID_ARG, "launch_batch before batch_prepare");
+    const unsigned grid = std::min<unsigned>((unsigned)resident, ntiles);
+    CT_CUDA_TRY(cudaMemsetAsync(d_next, 0, sizeof(unsigned), st));
+    const dim3 bl(kCV, kCU);
+    if (backward) {
+        if (flag) k_backward_cm_batch<true><<<grid, bl, 0, st>>>(d_jobs, njobs, ntiles, d_next);
+        else      k_backward_cm_batch<false><<<grid, bl, 0, st>>>(d_jobs, njobs, ntiles, d_next);
+    } else {
+        if (flag) k_forward_cm_batch<true><<<grid, bl, 0, st>>>(d_jobs, njobs, ntiles, d_next);
+        else      k_forward_cm_batch<false><<<grid, bl, 0, st>>>(d_jobs, njobs, ntiles, d_next);
+    }
+    CT_CHECK_LAUNCH();
+    return CT_OK;
 }
 
 ct_status launch_count(const ProjGeom &pg, unsigned long long *d_count, cudaStream_t st) {

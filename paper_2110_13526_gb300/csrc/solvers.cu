@@ -14,6 +14,7 @@
 // backprojector's ray weight).
 #include <algorithm>
 #include <cmath>
+#include <memory>
 #include <vector>
 
 #include "ct_internal.h"
@@ -508,38 +509,82 @@ struct Solve {
         return CT_OK;
     }
     // out (sdt) = c.alpha * L o (A vol (vdt)) + c.beta * out; tbuf receives the
-    // transposed copy of vol (same dtype) first.
-    ct_status forward_t(const void *vol, int vdt, void *tbuf, void *out, int sdt, Coef c,
-                        double *partials) {
-        CT_TRY(launch_transpose_typed(pg, vol, tbuf, vdt, st));
+    // transposed copy of vol (same dtype) first.  In two parts, so that a
+    // batched step can launch the projectors of several solves together:
+    // fwd_pre writes the copy, fwd_proj projects.
+    ct_status fwd_pre(const void *vol, int vdt, void *tbuf) {
+        return launch_transpose_typed(pg, vol, tbuf, vdt, st);
+    }
+    ct_status fwd_proj(const void *vol, int vdt, const void *tbuf, void *out, int sdt, Coef c,
+                       double *partials) {
         CT_TRY(tm.mark(tm.fwd));
         CT_TRY(launch_forward_typed(pg, vol, tbuf, vdt, out, sdt, L, c, partials, st));
         CT_TRY(tm.mark(tm.fwd));
         ++n_fwd;
         return CT_OK;
     }
+    ct_status forward_t(const void *vol, int vdt, void *tbuf, void *out, int sdt, Coef c,
+                        double *partials) {
+        CT_TRY(fwd_pre(vol, vdt, tbuf));
+        return fwd_proj(vol, vdt, tbuf, out, sdt, c, partials);
+    }
+    // fwd_proj of FP32 vectors as a job of a batched launch (batchable(pg)).
+    ct_status fwd_job(const float *tbuf, float *out, Coef c, double *partials, BatchJob *b) const {
+        CT_TRY(batch_job_grid(pg, false, b));
+        b->in = tbuf;
+        b->out = out;
+        b->rho = L;
+        b->c = c;
+        b->partials = partials;
+        b->det_scale = nullptr;
+        return CT_OK;
+    }
     // gout = c * A^T (L o e) (e of dtype edt), then partials of (Wg)^2 if
     // requested; the geometry decides float-atomic or fixed-point
-    // (deterministic) sums.
-    ct_status back_t(const void *e, int edt, float *gout, Coef c, const float *wnorm,
-                     double *partials) {
+    // (deterministic) sums.  In three parts: back_pre clears the accumulators
+    // (and finds the fixed-point scale), back_proj scatters, back_post
+    // combines them into gout.
+    ct_status back_pre(const void *e, int edt, float *gout, Coef c) {
         if (!g->deterministic) {
             CT_CUDA_TRY(cudaMemsetAsync(gout, 0, (size_t)n * sizeof(float), st));
             CT_CUDA_TRY(cudaMemsetAsync(T, 0, (size_t)n * sizeof(float), st));
-            CT_TRY(tm.mark(tm.back));
-            CT_TRY(launch_backward_typed(pg, e, edt, L, c, gout, T, 1, false, nullptr, st));
-            CT_TRY(tm.mark(tm.back));
-            ++n_back;
-            return launch_combine(pg, gout, T, wnorm, partials, st);
+            return CT_OK;
         }
         CT_CUDA_TRY(cudaMemsetAsync(bs.q, 0, 2 * (size_t)n * sizeof(long long), st));
-        CT_TRY(launch_det_scale(e, edt, L, m, det_value_bound(g, 1), c, bs.part, bs.scale,
-                                bs.inv, st));
+        return launch_det_scale(e, edt, L, m, det_value_bound(g, 1), c, bs.part, bs.scale,
+                                bs.inv, st);
+    }
+    ct_status back_proj(const void *e, int edt, float *gout, Coef c) {
         CT_TRY(tm.mark(tm.back));
-        CT_TRY(launch_backward_typed(pg, e, edt, L, c, bs.q, bs.q + n, 1, true, bs.scale, st));
+        if (!g->deterministic)
+            CT_TRY(launch_backward_typed(pg, e, edt, L, c, gout, T, 1, false, nullptr, st));
+        else
+            CT_TRY(launch_backward_typed(pg, e, edt, L, c, bs.q, bs.q + n, 1, true, bs.scale, st));
         CT_TRY(tm.mark(tm.back));
         ++n_back;
+        return CT_OK;
+    }
+    ct_status back_post(float *gout, const float *wnorm, double *partials) {
+        if (!g->deterministic) return launch_combine(pg, gout, T, wnorm, partials, st);
         return launch_combine_det(pg, gout, 0.f, bs.q, bs.q + n, bs.inv, wnorm, partials, st);
+    }
+    ct_status back_t(const void *e, int edt, float *gout, Coef c, const float *wnorm,
+                     double *partials) {
+        CT_TRY(back_pre(e, edt, gout, c));
+        CT_TRY(back_proj(e, edt, gout, c));
+        return back_post(gout, wnorm, partials);
+    }
+    // back_proj of an FP32 e as a job of a batched launch (batchable(pg)); the
+    // column-major kernels accumulate into the [y][x][z] buffer only.
+    ct_status back_job(const float *e, Coef c, BatchJob *b) const {
+        CT_TRY(batch_job_grid(pg, true, b));
+        b->in = e;
+        b->out = g->deterministic ? static_cast<void *>(bs.q + n) : static_cast<void *>(T);
+        b->rho = L;
+        b->c = c;
+        b->partials = nullptr;
+        b->det_scale = g->deterministic ? bs.scale : nullptr;
+        return CT_OK;
     }
     ct_status back(const float *e, float *gout, Coef c, const float *wnorm, double *partials) {
         return back_t(e, CT_F32, gout, c, wnorm, partials);
@@ -600,18 +645,23 @@ struct UpdateGraph {
         if (g) cudaGraphDestroy(g);
         if (cs) cudaStreamDestroy(cs);
     }
-    // body() enqueues one update on *sref, which points at the capture stream
-    // meanwhile.  Nothing runs during capture, so the kernels it counted are
-    // taken back from ct_kernel_launches and added again per replay.
+    // body() enqueues one update on the stream(s) that set_stream(s) points
+    // at (the capture stream meanwhile, the original one afterwards).
+    // Nothing runs during capture, so the kernels it counted are taken back
+    // from ct_kernel_launches and added again per replay.
     template <class F>
     ct_status capture(F &&body, cudaStream_t *sref) {
+        const cudaStream_t saved = *sref;
+        return capture(body, [&](cudaStream_t s) { *sref = s ? s : saved; });
+    }
+    template <class F, class G>
+    ct_status capture(F &&body, G &&set_stream) {
         CT_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         const long long k0 = thread_launches();
         CT_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        const cudaStream_t saved = *sref;
-        *sref = cs;
+        set_stream(cs);
         const ct_status sb = body();
-        *sref = saved;
+        set_stream(nullptr);
         cudaGraph_t gr = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(cs, &gr);
         nk = thread_launches() - k0;
@@ -634,45 +684,42 @@ struct UpdateGraph {
     }
 };
 
+// The state of one CGLS solve (Algorithm 1) and its steps.  ct_cgls runs
+// one of these to the end; a ct_batch advances several together, launching
+// their projectors as one batched kernel (the phases of update() below).
 template <class ST>
-ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_solver_opts *o,
-                    ct_solver_report *rep, cudaStream_t st) {
-    const int sd = o->storage;
-    const int K = o->max_iter;
-    const double ERR = o->err_tol;
-    Solve sv(g, st, o->timing != 0);
-    CT_TRY(sv.init(o->precond));
-    const int64_t n = sv.n, m = sv.m;
-    const int gn = vec_grid(n), gm = vec_grid(m);
-    const int64_t nfp = forward_partials(sv.pg), ncp = transpose_grid_count(sv.pg);
+struct CglsJob {
+    const float *b;
+    float *x;
+    ct_solver_opts o;
+    Solve sv;
+    int sd, K;
+    double ERR, lam;
+    int64_t n, m;
+    int gn = 0, gm = 0;
+    int64_t nfp = 0, ncp = 0, nrp = 0;
     ST *z = nullptr, *e = nullptr, *p = nullptr;
     float *gv = nullptr;
-    void *Ts = nullptr;  // transposed copy of z (the float scratch T when ST is float)
+    void *Ts = nullptr;          // transposed copy of z (the float scratch T when ST is float)
+    float *mxp = nullptr;        // block maxima of |W^2 g| (direction scaling, reduced storage)
     CglsS *S = nullptr;
     double *hist = nullptr;
-    CT_TRY(sv.ws.alloc(&z, (size_t)n));
-    CT_TRY(sv.ws.alloc(&gv, (size_t)n));
-    float *mxp = nullptr;  // block maxima of |W^2 g| (direction scaling, reduced storage)
-    if (sd == CT_F32) {
-        Ts = sv.T;
-    } else {
-        CT_TRY(sv.ws.alloc(&mxp, (size_t)gn));
-        ST *t = nullptr;
-        CT_TRY(sv.ws.alloc(&t, (size_t)n));
-        Ts = t;
+    double *zpart = nullptr;     // partials of ||z||^2 for NP2 (Tikhonov)
+    Coef one, sub;               // (1, 0) and (-1, 1): e = e - L A x
+    int i = 0;                   // updates done
+    CglsS hs{};
+
+    CglsJob(const ct_geometry *g, const float *b_, float *x_, const ct_solver_opts *o_,
+            cudaStream_t st)
+        : b(b_), x(x_), o(*o_), sv(g, st, o_->timing != 0), sd(o_->storage), K(o_->max_iter),
+          ERR(o_->err_tol), lam(o_->tikhonov_lambda), n(g->nvox), m(g->nrays) {
+        sub.alpha = -1.f;
+        sub.beta = 1.f;
     }
-    CT_TRY(sv.ws.alloc(&e, (size_t)std::max<int64_t>(m, 1)));
-    CT_TRY(sv.ws.alloc(&p, (size_t)std::max<int64_t>(m, 1)));
-    CT_TRY(sv.ws.alloc(&S, 1));
-    CT_TRY(sv.ws.alloc(&hist, (size_t)K));
-    CT_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(CglsS), st));
-    // Tikhonov regularisation (Software section): minimise
-    // ||L (A x - b)||^2 + lam ||x||^2, Algorithm 1 on [L A W; sqrt(lam) W]
-    const double lam = o->tikhonov_lambda;
-    double *zpart = nullptr;               // partials of ||z||^2 for NP2
-    if (lam > 0.0) CT_TRY(sv.ws.alloc(&zpart, (size_t)gn));
+
     // x = x + alpha d_x (delayed); d_x = r_x + beta d_x (+ ||d_x||^2 partials)
-    auto vol_update = [&](cudaStream_t s, int first) -> ct_status {
+    ct_status vol_update(int first) {
+        const cudaStream_t s = sv.st;
         if (zpart)
             k_vol_update<ST, true><<<gn, kVecThreads, 0, s>>>(x, z, gv, sv.W, n, &S->a_pend,
                                                               &S->beta, &S->zs, first, zpart);
@@ -681,106 +728,179 @@ ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
                                                                &S->beta, &S->zs, first, nullptr);
         CT_CHECK_LAUNCH();
         return CT_OK;
-    };
-    // r_x = A^T e_b into gv, NR2 partials into sv.part (count returned)
-    auto gradient = [&](int first, int64_t *np) -> ct_status {
+    }
+    // r_x = A^T e_b (- lam x) into gv and the NR2 partials into sv.part, in
+    // the three parts of Solve::back_t; nrp = the partials' count.
+    ct_status grad_pre() { return sv.back_pre(e, sd, gv, Coef()); }
+    ct_status grad_proj() { return sv.back_proj(e, sd, gv, Coef()); }
+    ct_status grad_post(int first) {
         if (lam == 0.0) {
-            CT_TRY(sv.back_t(e, sd, gv, Coef(), sv.W, sv.part));
-            *np = ncp;
+            CT_TRY(sv.back_post(gv, sv.W, sv.part));
+            nrp = ncp;
             return CT_OK;
         }
-        CT_TRY(sv.back_t(e, sd, gv, Coef(), sv.W, nullptr));
-        k_tikhonov_grad<<<gn, kVecThreads, 0, sv.st>>>(gv, x, z, sv.W, n, &S->a_pend, lam,
-                                                       first, sv.part);
+        CT_TRY(sv.back_post(gv, sv.W, nullptr));
+        k_tikhonov_grad<<<gn, kVecThreads, 0, sv.st>>>(gv, x, z, sv.W, n, &S->a_pend, lam, first,
+                                                       sv.part);
         CT_CHECK_LAUNCH();
-        *np = gn;
+        nrp = gn;
         return CT_OK;
-    };
-    Coef one;                              // (1, 0)
-    Coef sub;                              // (-1, 1): e = e - L A x
-    sub.alpha = -1.f;
-    sub.beta = 1.f;
-
-    // NB0 = ||b||; e_b = b - A x0 (the A x0 call is skipped for x0 = 0)
-    bool x0nz = false;
-    CT_TRY(sv.nonzero(x, &x0nz));
-    k_sino_weighted_copy<<<gm, kVecThreads, 0, st>>>(e, b, sv.L, m, sv.part);
-    CT_CHECK_LAUNCH();
-    k_cgls_nb0<<<1, 1024, 0, st>>>(sv.part, gm, S);
-    CT_CHECK_LAUNCH();
-    if (x0nz) CT_TRY(sv.forward_t(x, CT_F32, sv.T, e, sd, sub, nullptr));
-    // r_x = A^T e_b (- lam x); d_x = r_x; NR2_old = ||r_x||^2
-    int64_t nrp = 0;
-    CT_TRY(gradient(1, &nrp));
-    if (mxp) {
-        k_absmax_w2g<<<gn, kVecThreads, 0, st>>>(gv, sv.W, n, mxp);
-        CT_CHECK_LAUNCH();
     }
-    k_cgls_nr2<<<1, 1024, 0, st>>>(sv.part, nrp, S, 1, mxp, gn);
-    CT_CHECK_LAUNCH();
-    CT_TRY(vol_update(st, 1));
-    // p_b = A d_x; NP2 (+ lam ||d_x||^2); alpha
-    CT_TRY(sv.forward_t(z, sd, Ts, p, sd, one, sv.part));
-    k_cgls_np2<<<1, 1024, 0, st>>>(sv.part, nfp, S, zpart, gn, lam);
-    CT_CHECK_LAUNCH();
-    // (x = x + alpha d_x is delayed into the next volume update)
-    // e_b = e_b - alpha p_b; NB = ||e_b||
-    k_sino_axpy<<<gm, kVecThreads, 0, st>>>(e, p, m, &S->alpha, sv.part);
-    CT_CHECK_LAUNCH();
-    k_cgls_nb<<<1, 1024, 0, st>>>(sv.part, gm, S, hist, -1);
-    CT_CHECK_LAUNCH();
-    int i = 1;
-    CglsS hs{};
-    auto keep_going = [&](bool *go) -> ct_status {
-        *go = i < K;
-        if (*go && ERR > 0.0) {
-            CT_TRY(read_scalars(S, &hs, st));
-            *go = (hs.nb0 > 0.0) && (hs.nb / hs.nb0 > ERR);
-        }
-        return CT_OK;
-    };
-    // One x update after the first, enqueued on sv.st; ends with NB in
-    // sv.part (k_cgls_nb reads it).
-    auto update = [&]() -> ct_status {
+    // NR2 and beta, then x += alpha_prev d_x; d_x = r_x + beta d_x, then the
+    // transposed copy of d_x for A.
+    ct_status middle(int first) {
         const cudaStream_t s = sv.st;
-        // r_x = A^T e_b (- lam x); NR2_now; beta; NR2_old = NR2_now
-        CT_TRY(gradient(0, &nrp));
         if (mxp) {
             k_absmax_w2g<<<gn, kVecThreads, 0, s>>>(gv, sv.W, n, mxp);
             CT_CHECK_LAUNCH();
         }
-        k_cgls_nr2<<<1, 1024, 0, s>>>(sv.part, nrp, S, 0, mxp, gn);
+        k_cgls_nr2<<<1, 1024, 0, s>>>(sv.part, nrp, S, first, mxp, gn);
         CT_CHECK_LAUNCH();
-        // x = x + alpha d_x (previous iteration); d_x = r_x + beta d_x
-        CT_TRY(vol_update(s, 0));
-        // p_b = A d_x; NP2 (+ lam ||d_x||^2); alpha
-        CT_TRY(sv.forward_t(z, sd, Ts, p, sd, one, sv.part));
+        CT_TRY(vol_update(first));
+        return sv.fwd_pre(z, sd, Ts);
+    }
+    // p_b = A d_x with the NP2 partials
+    ct_status fwd_proj() { return sv.fwd_proj(z, sd, Ts, p, sd, one, sv.part); }
+    // NP2 (+ lam ||d_x||^2), alpha; e_b = e_b - alpha p_b with the NB partials
+    ct_status tail() {
+        const cudaStream_t s = sv.st;
         k_cgls_np2<<<1, 1024, 0, s>>>(sv.part, nfp, S, zpart, gn, lam);
         CT_CHECK_LAUNCH();
-        // e_b = e_b - alpha p_b; NB
         k_sino_axpy<<<gm, kVecThreads, 0, s>>>(e, p, m, &S->alpha, sv.part);
         CT_CHECK_LAUNCH();
         return CT_OK;
-    };
-    auto finish = [&]() -> ct_status {
+    }
+    // NB = ||e_b|| into S and the history
+    ct_status finish() {
         k_cgls_nb<<<1, 1024, 0, sv.st>>>(sv.part, gm, S, hist, -1);
         CT_CHECK_LAUNCH();
         return CT_OK;
-    };
+    }
+    // One x update after the first; ends with the NB partials in sv.part.
+    ct_status update() {
+        CT_TRY(grad_pre());
+        CT_TRY(grad_proj());
+        CT_TRY(grad_post(0));
+        CT_TRY(middle(0));
+        CT_TRY(fwd_proj());
+        return tail();
+    }
+    // The batched launch descriptors of grad_proj and fwd_proj (FP32 storage).
+    ct_status back_job(BatchJob *bj) const {
+        return sv.back_job(reinterpret_cast<const float *>(e), Coef(), bj);
+    }
+    ct_status fwd_job(BatchJob *bj) const {
+        return sv.fwd_job(static_cast<const float *>(Ts), reinterpret_cast<float *>(p), one,
+                          sv.part, bj);
+    }
+
+    // Allocations, NB0, and the first update (i = 1).
+    ct_status start() {
+        CT_TRY(sv.init(o.precond));
+        const cudaStream_t st = sv.st;
+        gn = vec_grid(n);
+        gm = vec_grid(m);
+        nfp = forward_partials(sv.pg);
+        ncp = transpose_grid_count(sv.pg);
+        CT_TRY(sv.ws.alloc(&z, (size_t)n));
+        CT_TRY(sv.ws.alloc(&gv, (size_t)n));
+        if (sd == CT_F32) {
+            Ts = sv.T;
+        } else {
+            CT_TRY(sv.ws.alloc(&mxp, (size_t)gn));
+            ST *t = nullptr;
+            CT_TRY(sv.ws.alloc(&t, (size_t)n));
+            Ts = t;
+        }
+        CT_TRY(sv.ws.alloc(&e, (size_t)std::max<int64_t>(m, 1)));
+        CT_TRY(sv.ws.alloc(&p, (size_t)std::max<int64_t>(m, 1)));
+        CT_TRY(sv.ws.alloc(&S, 1));
+        CT_TRY(sv.ws.alloc(&hist, (size_t)K));
+        CT_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(CglsS), st));
+        // Tikhonov regularisation (Software section): minimise
+        // ||L (A x - b)||^2 + lam ||x||^2, Algorithm 1 on [L A W; sqrt(lam) W]
+        if (lam > 0.0) CT_TRY(sv.ws.alloc(&zpart, (size_t)gn));
+        // NB0 = ||b||; e_b = b - A x0 (the A x0 call is skipped for x0 = 0)
+        bool x0nz = false;
+        CT_TRY(sv.nonzero(x, &x0nz));
+        k_sino_weighted_copy<<<gm, kVecThreads, 0, st>>>(e, b, sv.L, m, sv.part);
+        CT_CHECK_LAUNCH();
+        k_cgls_nb0<<<1, 1024, 0, st>>>(sv.part, gm, S);
+        CT_CHECK_LAUNCH();
+        if (x0nz) CT_TRY(sv.forward_t(x, CT_F32, sv.T, e, sd, sub, nullptr));
+        // r_x = A^T e_b (- lam x); d_x = r_x; NR2_old = ||r_x||^2
+        CT_TRY(grad_pre());
+        CT_TRY(grad_proj());
+        CT_TRY(grad_post(1));
+        CT_TRY(middle(1));
+        // p_b = A d_x; NP2 (+ lam ||d_x||^2); alpha
+        // (x = x + alpha d_x is delayed into the next volume update)
+        // e_b = e_b - alpha p_b; NB = ||e_b||
+        CT_TRY(fwd_proj());
+        CT_TRY(tail());
+        CT_TRY(finish());
+        i = 1;
+        return CT_OK;
+    }
+    // The stopping rule of Algorithm 1 given the scalars h read back after
+    // update i (only read when ERR > 0).
+    bool go_on(const CglsS &h) const {
+        if (i >= K) return false;
+        return ERR <= 0.0 || ((h.nb0 > 0.0) && (h.nb / h.nb0 > ERR));
+    }
+    ct_status keep_going(bool *go) {
+        if (i < K && ERR > 0.0) CT_TRY(read_scalars(S, &hs, sv.st));
+        *go = go_on(hs);
+        return CT_OK;
+    }
+    // Periodic recomputation of the discrepancy from the solution (Discussion).
+    ct_status recompute() {
+        const cudaStream_t st = sv.st;
+        k_vol_axpy<<<gn, kVecThreads, 0, st>>>(x, z, n, &S->a_pend);
+        CT_CHECK_LAUNCH();
+        k_set_zero<<<1, 1, 0, st>>>(&S->a_pend);
+        CT_CHECK_LAUNCH();
+        k_sino_weighted_copy<<<gm, kVecThreads, 0, st>>>(e, b, sv.L, m, nullptr);
+        CT_CHECK_LAUNCH();
+        CT_TRY(sv.forward_t(x, CT_F32, sv.T, e, sd, sub, nullptr));
+        k_norm2_t<<<gm, kVecThreads, 0, st>>>(e, m, sv.part);
+        CT_CHECK_LAUNCH();
+        return CT_OK;
+    }
+    // The last pending x = x + alpha d_x, then the report (waits for the stream).
+    ct_status end(ct_solver_report *rep) {
+        const cudaStream_t st = sv.st;
+        k_vol_axpy<<<gn, kVecThreads, 0, st>>>(x, z, n, &S->a_pend);
+        CT_CHECK_LAUNCH();
+        std::vector<double> h((size_t)K, 0.0);
+        CT_CUDA_TRY(cudaMemcpyAsync(h.data(), hist, sizeof(double) * (size_t)i,
+                                    cudaMemcpyDeviceToHost, st));
+        CT_TRY(read_scalars(S, &hs, st));
+        sv.report(rep, i, hs.nb0, hs.nb, h);
+        return CT_OK;
+    }
+};
+
+template <class ST>
+ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_solver_opts *o,
+                    ct_solver_report *rep, cudaStream_t st) {
+    CglsJob<ST> job(g, b, x, o, st);
+    CT_TRY(job.start());
     // Without per-operator timing or recomputation every update enqueues the
     // same launches with the same arguments (the scalars live on the device),
     // so the first one is captured as a CUDA graph and replayed: one launch
     // per update instead of a dozen.
     UpdateGraph graph;
-    const bool use_graph = !o->timing && o->recompute_every == 0 && K > 2;
+    const bool use_graph = !o->timing && o->recompute_every == 0 && job.K > 2;
     bool go = false;
-    CT_TRY(keep_going(&go));
+    CT_TRY(job.keep_going(&go));
+    Solve &sv = job.sv;
     int dfwd = 0, dback = 0;               // operator calls per replayed update
     if (go && use_graph) {
         const int f0 = sv.n_fwd, b0 = sv.n_back;
         CT_TRY(graph.capture([&]() -> ct_status {
-            CT_TRY(update());
-            return finish();
+            CT_TRY(job.update());
+            return job.finish();
         }, &sv.st));
         dfwd = sv.n_fwd - f0;
         dback = sv.n_back - b0;
@@ -792,36 +912,16 @@ ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
             CT_TRY(graph.launch(st));
             sv.n_fwd += dfwd;
             sv.n_back += dback;
-            ++i;
-            CT_TRY(keep_going(&go));
-            continue;
+        } else {
+            CT_TRY(job.update());
+            if (o->recompute_every > 0 && (job.i + 1) % o->recompute_every == 0)
+                CT_TRY(job.recompute());
+            CT_TRY(job.finish());
         }
-        CT_TRY(update());
-        ++i;
-        if (o->recompute_every > 0 && i % o->recompute_every == 0) {
-            // discrepancy recomputed from the solution (Discussion)
-            k_vol_axpy<<<gn, kVecThreads, 0, st>>>(x, z, n, &S->a_pend);
-            CT_CHECK_LAUNCH();
-            k_set_zero<<<1, 1, 0, st>>>(&S->a_pend);
-            CT_CHECK_LAUNCH();
-            k_sino_weighted_copy<<<gm, kVecThreads, 0, st>>>(e, b, sv.L, m, nullptr);
-            CT_CHECK_LAUNCH();
-            CT_TRY(sv.forward_t(x, CT_F32, sv.T, e, sd, sub, nullptr));
-            k_norm2_t<<<gm, kVecThreads, 0, st>>>(e, m, sv.part);
-            CT_CHECK_LAUNCH();
-        }
-        CT_TRY(finish());
-        CT_TRY(keep_going(&go));
+        ++job.i;
+        CT_TRY(job.keep_going(&go));
     }
-    // the last pending x = x + alpha d_x
-    k_vol_axpy<<<gn, kVecThreads, 0, st>>>(x, z, n, &S->a_pend);
-    CT_CHECK_LAUNCH();
-    std::vector<double> h((size_t)K, 0.0);
-    CT_CUDA_TRY(cudaMemcpyAsync(h.data(), hist, sizeof(double) * (size_t)i,
-                                cudaMemcpyDeviceToHost, st));
-    CT_TRY(read_scalars(S, &hs, st));
-    sv.report(rep, i, hs.nb0, hs.nb, h);
-    return CT_OK;
+    return job.end(rep);
 }
 
 ct_status lsqr_impl(const ct_geometry *g, const float *b, float *x, const ct_solver_opts *o,
@@ -1020,7 +1120,353 @@ ct_status sirt_impl(const ct_geometry *g, const float *b, float *x, const ct_sir
 
 using namespace ct;
 
+// Several CGLS solves advanced in lock step (continuous batching): each
+// ct_batch_step runs one update of every active job, with the A^T of all
+// batchable jobs in one persistent launch and their A in another (the
+// vector kernels stay per job).  Jobs join (ct_batch_add_cgls) and leave
+// (their stopping rule, ct_batch_remove) between steps.  The step of a fixed
+// set of jobs is captured as a CUDA graph and replayed until the set changes.
+// Side streams over which a batched step spreads the jobs' vector kernels.
+constexpr int kBatchSideStreams = 8;
+
+struct ct_batch {
+    struct Entry {
+        int32_t id = 0;
+        std::unique_ptr<CglsJob<float>> job;
+        bool done = false;
+        bool batched = false;           // its projectors run in the batched launches
+        ct_solver_report rep{};
+        std::vector<double> hist;
+    };
+    int device = 0;
+    cudaStream_t st = nullptr;
+    std::vector<Entry> jobs;
+    int32_t next_id = 1;
+    bool dirty = true;                  // the set of active jobs changed since the tables
+    BatchJob *h_tab = nullptr;          // pinned host staging of the launch tables
+    BatchJob *d_tab = nullptr;          // [A^T float | A^T fixed point | A] tables
+    size_t tab_cap = 0;
+    unsigned *d_next = nullptr;         // work counter of the batched launches
+    CglsS *h_s = nullptr;               // pinned copies of the jobs' scalars
+    size_t s_cap = 0;
+    int nbf = 0, nbd = 0, nfw = 0;      // jobs in each table
+    unsigned tbf = 0, tbd = 0, tfw = 0; // tiles in each table
+    std::unique_ptr<UpdateGraph> graph;
+    std::vector<cudaStream_t> side;     // streams of the per-job phases
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
+
+    ct_status init_streams(int n) {
+        CT_CUDA_TRY(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+        for (int k = 0; k < n; ++k) {
+            cudaStream_t s = nullptr;
+            CT_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+            side.push_back(s);
+            cudaEvent_t e = nullptr;
+            CT_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            ev_join.push_back(e);
+        }
+        return CT_OK;
+    }
+
+    ~ct_batch() {
+        graph.reset();
+        jobs.clear();                   // frees their workspaces on st
+        if (st) cudaStreamSynchronize(st);
+        for (auto s : side) cudaStreamDestroy(s);
+        for (auto e : ev_join) cudaEventDestroy(e);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (d_tab) cudaFree(d_tab);
+        if (d_next) cudaFree(d_next);
+        if (h_tab) cudaFreeHost(h_tab);
+        if (h_s) cudaFreeHost(h_s);
+    }
+
+    Entry *find(int32_t id) {
+        for (auto &e : jobs)
+            if (e.id == id) return &e;
+        return nullptr;
+    }
+
+    // Rebuild and upload the launch tables of the active jobs.
+    ct_status build_tables() {
+        CT_CUDA_TRY(cudaStreamSynchronize(st));   // the old tables are no longer read
+        std::vector<BatchJob> bf, bd, fw;
+        unsigned t;
+        for (auto &en : jobs) {
+            if (en.done) continue;
+            CglsJob<float> &j = *en.job;
+            en.batched = batchable(j.sv.pg) && !j.sv.tm.on;
+            if (!en.batched) continue;
+            BatchJob bb{}, fb{};
+            CT_TRY(j.back_job(&bb));
+            CT_TRY(j.fwd_job(&fb));
+            (j.sv.g->deterministic ? bd : bf).push_back(bb);
+            fw.push_back(fb);
+        }
+        auto offsets = [&](std::vector<BatchJob> &v, unsigned *total) -> ct_status {
+            t = 0;
+            for (auto &x : v) {
+                x.tile0 = t;
+                if ((uint64_t)t + x.tiles > 0xffffff00ull)
+                    return set_error(CT_ERR_INVALID_ARG, "batch: too many tiles in one launch");
+                t += x.tiles;
+            }
+            *total = t;
+            return CT_OK;
+        };
+        CT_TRY(offsets(bf, &tbf));
+        CT_TRY(offsets(bd, &tbd));
+        CT_TRY(offsets(fw, &tfw));
+        nbf = (int)bf.size();
+        nbd = (int)bd.size();
+        nfw = (int)fw.size();
+        const size_t need = bf.size() + bd.size() + fw.size();
+        if (need > tab_cap) {
+            if (d_tab) CT_CUDA_TRY(cudaFree(d_tab));
+            if (h_tab) CT_CUDA_TRY(cudaFreeHost(h_tab));
+            d_tab = nullptr;
+            h_tab = nullptr;
+            tab_cap = 0;
+            CT_CUDA_TRY(cudaMalloc(&d_tab, need * sizeof(BatchJob)));
+            CT_CUDA_TRY(cudaMallocHost(&h_tab, need * sizeof(BatchJob)));
+            tab_cap = need;
+        }
+        std::copy(bf.begin(), bf.end(), h_tab);
+        std::copy(bd.begin(), bd.end(), h_tab + nbf);
+        std::copy(fw.begin(), fw.end(), h_tab + nbf + nbd);
+        if (need)
+            CT_CUDA_TRY(cudaMemcpyAsync(d_tab, h_tab, need * sizeof(BatchJob),
+                                        cudaMemcpyHostToDevice, st));
+        graph.reset();
+        dirty = false;
+        return CT_OK;
+    }
+
+    // Runs fn(entry) for every active job, the jobs spread over the side
+    // streams (forked from and joined back into the jobs' stream), so that
+    // the small vector kernels of different jobs overlap.
+    template <class F>
+    ct_status phase(F &&fn) {
+        const cudaStream_t m = jobs_stream();
+        int act = 0;
+        for (auto &en : jobs) act += !en.done;
+        const int used = std::min<int>(act, (int)side.size());
+        CT_CUDA_TRY(cudaEventRecord(ev_fork, m));
+        for (int k = 0; k < used; ++k) CT_CUDA_TRY(cudaStreamWaitEvent(side[k], ev_fork, 0));
+        int k = 0;
+        for (auto &en : jobs) {
+            if (en.done) continue;
+            en.job->sv.st = side[(size_t)(k++ % used)];
+            CT_TRY(fn(en));
+            en.job->sv.st = m;
+        }
+        for (int j = 0; j < used; ++j) {
+            CT_CUDA_TRY(cudaEventRecord(ev_join[j], side[j]));
+            CT_CUDA_TRY(cudaStreamWaitEvent(m, ev_join[j], 0));
+        }
+        return CT_OK;
+    }
+
+    // One update of every active job (the phases of CglsJob::update), with
+    // the batchable jobs' A^T and A as batched launches between the phases.
+    ct_status step_body() {
+        CT_TRY(phase([](Entry &en) -> ct_status {
+            CT_TRY(en.job->grad_pre());
+            return en.batched ? CT_OK : en.job->grad_proj();
+        }));
+        const cudaStream_t s = jobs_stream();
+        CT_TRY(launch_batch(d_tab, nbf, tbf, true, false, d_next, s));
+        CT_TRY(launch_batch(d_tab + nbf, nbd, tbd, true, true, d_next, s));
+        CT_TRY(phase([](Entry &en) -> ct_status {
+            CT_TRY(en.job->grad_post(0));
+            CT_TRY(en.job->middle(0));
+            return en.batched ? CT_OK : en.job->fwd_proj();
+        }));
+        CT_TRY(launch_batch(d_tab + nbf + nbd, nfw, tfw, false, true, d_next, s));
+        return phase([](Entry &en) -> ct_status {
+            CT_TRY(en.job->tail());
+            return en.job->finish();
+        });
+    }
+    // The stream the jobs currently launch on (the capture stream meanwhile).
+    cudaStream_t cur = nullptr;
+    cudaStream_t jobs_stream() const { return cur ? cur : st; }
+    void set_stream(cudaStream_t s) {
+        cur = s;
+        for (auto &en : jobs)
+            if (!en.done) en.job->sv.st = s ? s : st;
+    }
+
+    ct_status step(int32_t *n_active) {
+        int active = 0;
+        for (auto &en : jobs) active += !en.done;
+        if (active > 0) {
+            if (dirty) CT_TRY(build_tables());
+            if (!graph) {
+                // the same launches with the same arguments until the set changes
+                graph.reset(new UpdateGraph());
+                std::vector<int> f0, b0;
+                for (auto &en : jobs) {
+                    f0.push_back(en.job->sv.n_fwd);
+                    b0.push_back(en.job->sv.n_back);
+                }
+                CT_TRY(graph->capture([&]() { return step_body(); },
+                                      [&](cudaStream_t cs) { set_stream(cs); }));
+                for (size_t k = 0; k < jobs.size(); ++k) {   // counted again per replay
+                    jobs[k].job->sv.n_fwd = f0[k];
+                    jobs[k].job->sv.n_back = b0[k];
+                }
+            }
+            CT_TRY(graph->launch(st));
+            // scalars of the jobs that test a tolerance, one wait for all
+            if (jobs.size() > s_cap) {
+                if (h_s) CT_CUDA_TRY(cudaFreeHost(h_s));
+                h_s = nullptr;
+                s_cap = 0;
+                CT_CUDA_TRY(cudaMallocHost(&h_s, jobs.size() * sizeof(CglsS)));
+                s_cap = jobs.size();
+            }
+            bool any_read = false;
+            for (size_t k = 0; k < jobs.size(); ++k) {
+                Entry &en = jobs[k];
+                if (en.done) continue;
+                CglsJob<float> &j = *en.job;
+                ++j.i;
+                ++j.sv.n_back;   // one A^T and one A per update
+                ++j.sv.n_fwd;
+                if (j.i < j.K && j.ERR > 0.0) {
+                    CT_CUDA_TRY(cudaMemcpyAsync(h_s + k, j.S, sizeof(CglsS),
+                                                cudaMemcpyDeviceToHost, st));
+                    any_read = true;
+                }
+            }
+            if (any_read) CT_CUDA_TRY(cudaStreamSynchronize(st));
+            for (size_t k = 0; k < jobs.size(); ++k) {
+                Entry &en = jobs[k];
+                if (en.done) continue;
+                CglsJob<float> &j = *en.job;
+                if (j.i < j.K && j.ERR > 0.0) j.hs = h_s[k];
+                if (!j.go_on(j.hs)) CT_TRY(retire(en));
+            }
+        }
+        int left = 0;
+        for (auto &en : jobs) left += !en.done;
+        *n_active = left;
+        return CT_OK;
+    }
+
+    // The job's stopping rule fired: finish x and keep the report.
+    ct_status retire(Entry &en) {
+        en.hist.assign((size_t)en.job->K, 0.0);
+        en.rep = ct_solver_report{};
+        en.rep.history_nb = en.hist.data();
+        en.rep.history_cap = en.job->K;
+        CT_TRY(en.job->end(&en.rep));
+        en.done = true;
+        dirty = true;
+        return CT_OK;
+    }
+};
+
 extern "C" {
+
+ct_status ct_batch_create(void *stream, ct_batch **out) {
+    clear_error();
+    if (!out) return set_error(CT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    std::unique_ptr<ct_batch> b(new ct_batch());
+    b->st = (cudaStream_t)stream;
+    CT_CUDA_TRY(cudaGetDevice(&b->device));
+    CT_TRY(batch_prepare());
+    CT_TRY(b->init_streams(kBatchSideStreams));
+    CT_CUDA_TRY(cudaMalloc(&b->d_next, sizeof(unsigned)));
+    *out = b.release();
+    return CT_OK;
+}
+
+ct_status ct_batch_destroy(ct_batch *b) {
+    clear_error();
+    if (!b) return CT_OK;
+    DeviceGuard dg(b->device);
+    CT_TRY(dg.status());
+    delete b;
+    return CT_OK;
+}
+
+ct_status ct_batch_add_cgls(ct_batch *b, const ct_geometry *g, const float *d_b, float *d_x,
+                            const ct_solver_opts *opts, int32_t *job) {
+    clear_error();
+    if (!b || !job) return set_error(CT_ERR_INVALID_ARG, "NULL batch or job");
+    CT_TRY(check_opts(g, d_b, d_x, opts));
+    if (g->device != b->device)
+        return set_error(CT_ERR_INVALID_ARG, "batch: geometry on another device");
+    if (opts->storage != CT_F32 || opts->timing != 0 || opts->recompute_every != 0)
+        return set_error(CT_ERR_INVALID_ARG,
+                         "batch: FP32 storage, no timing and no recomputation only");
+    DeviceGuard dg(b->device);
+    CT_TRY(dg.status());
+    ct_batch::Entry en;
+    en.id = b->next_id++;
+    en.job.reset(new CglsJob<float>(g, d_b, d_x, opts, b->st));
+    ct_status s = en.job->start();
+    bool go = false;
+    if (s == CT_OK) s = en.job->keep_going(&go);
+    if (s != CT_OK) {
+        cudaStreamSynchronize(b->st);
+        return s;
+    }
+    b->jobs.push_back(std::move(en));
+    ct_batch::Entry &added = b->jobs.back();
+    if (!go) CT_TRY(b->retire(added));
+    b->dirty = true;
+    *job = added.id;
+    return CT_OK;
+}
+
+ct_status ct_batch_step(ct_batch *b, int32_t *n_active) {
+    clear_error();
+    if (!b || !n_active) return set_error(CT_ERR_INVALID_ARG, "NULL batch or n_active");
+    DeviceGuard dg(b->device);
+    CT_TRY(dg.status());
+    return b->step(n_active);
+}
+
+ct_status ct_batch_poll(ct_batch *b, int32_t job, int32_t *done, ct_solver_report *report) {
+    clear_error();
+    if (!b || !done) return set_error(CT_ERR_INVALID_ARG, "NULL batch or done");
+    ct_batch::Entry *en = b->find(job);
+    if (!en) return set_error(CT_ERR_INVALID_ARG, "batch: unknown job");
+    *done = en->done ? 1 : 0;
+    if (en->done && report) {
+        double *hn = report->history_nb;
+        const int32_t cap = report->history_cap;
+        *report = en->rep;
+        report->history_nb = hn;
+        report->history_cap = cap;
+        if (hn && cap > 0) {
+            const int k = std::min<int>(cap, std::min<int>(en->rep.iterations, (int)en->hist.size()));
+            for (int j = 0; j < k; ++j) hn[j] = en->hist[(size_t)j];
+        }
+    }
+    return CT_OK;
+}
+
+ct_status ct_batch_remove(ct_batch *b, int32_t job) {
+    clear_error();
+    if (!b) return set_error(CT_ERR_INVALID_ARG, "NULL batch");
+    DeviceGuard dg(b->device);
+    CT_TRY(dg.status());
+    for (size_t k = 0; k < b->jobs.size(); ++k) {
+        if (b->jobs[k].id != job) continue;
+        if (!b->jobs[k].done) CT_TRY(b->retire(b->jobs[k]));   // x gets its pending update
+        b->jobs.erase(b->jobs.begin() + (long)k);
+        b->dirty = true;
+        CT_CUDA_TRY(cudaStreamSynchronize(b->st));
+        return CT_OK;
+    }
+    return set_error(CT_ERR_INVALID_ARG, "batch: unknown job");
+}
 
 ct_status ct_cgls(const ct_geometry *g, const float *d_b, float *d_x, const ct_solver_opts *opts,
                   ct_solver_report *report, void *stream) {

@@ -11,6 +11,15 @@ arrival order).  Every solve is the unchanged library call (ct_cgls /
 ct_lsqr): a result does not depend on which other jobs share the GPU, up to
 the float-atomic summation order of the backprojection.
 
+With ``batched=True`` the FP32 CGLS requests instead join one ct_batch
+(iteration-level continuous batching): a batch thread advances all admitted
+CGLS jobs one update per step, with the backprojections of all of them in one
+persistent kernel launch and their projections in another, inside a CUDA
+graph; jobs join between steps as they are admitted and leave when their
+stopping rule fires.  LSQR and reduced-storage requests keep the per-slot
+streams.  A batched job's result is that of ct_cgls alone (bitwise with a
+deterministic geometry).
+
 Latency of a request = completion time - arrival time.
 """
 from __future__ import annotations
@@ -23,7 +32,7 @@ from typing import Dict, List, Optional, Tuple
 import numpy as np
 import torch
 
-from . import Geometry, cgls, lsqr
+from . import Batch, Geometry, cgls, lsqr
 
 
 @dataclass
@@ -81,10 +90,14 @@ class ServeStats:
 
 class Server:
     def __init__(self, slots: int = 8, hbm_budget_bytes: float = 150e9, device=None,
-                 deterministic: bool = False):
+                 deterministic: bool = False, batched: bool = False, batch_jobs: int = 32):
         if slots < 1:
             raise ValueError("slots must be >= 1")
+        if batch_jobs < 1:
+            raise ValueError("batch_jobs must be >= 1")
         self.slots = slots
+        self.batched = batched
+        self.batch_jobs = batch_jobs
         self.deterministic = deterministic
         self.budget = int(hbm_budget_bytes)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
@@ -112,7 +125,9 @@ class Server:
         torch.cuda.synchronize(self.device)
         cv = threading.Condition()
         state = {"free_slots": self.slots, "bytes": 0, "running": 0, "max_running": 0,
-                 "max_bytes": 0, "errors": []}
+                 "max_bytes": 0, "errors": [], "batch_active": 0, "batch_stop": False,
+                 "batch_steps": 0}
+        inbox: List[Tuple[Request, int, float]] = []    # admitted, not yet in the batch
         results: List[Result] = []
         streams = [torch.cuda.Stream(device=self.device) for _ in range(self.slots)]
         free_streams = list(range(self.slots))
@@ -147,7 +162,58 @@ class Server:
                 free_streams.append(si)
                 cv.notify_all()
 
+        def batch_worker():
+            live = {}                                     # job id -> (request, bytes, start)
+            new: List[Tuple[Request, int, float]] = []    # taken from the inbox, not yet added
+            try:
+                torch.cuda.set_device(self.device)
+                s = torch.cuda.Stream(device=self.device)
+                with torch.cuda.stream(s):
+                    bt = Batch(stream=s)
+                    while True:
+                        with cv:
+                            while not inbox and not live and not state["batch_stop"]:
+                                cv.wait()
+                            if state["batch_stop"] and not inbox and not live:
+                                break
+                            new.extend(inbox)
+                            inbox.clear()
+                        while new:
+                            req = new[0][0]
+                            jid = bt.add(self.geometry(req.geometry), req.b,
+                                         max_iter=req.max_iter, err_tol=req.err_tol)
+                            live[jid] = new.pop(0)
+                        if any(not bt.done(j) for j in live):
+                            bt.step()
+                            state["batch_steps"] += 1
+                        for j in [j for j in live if bt.done(j)]:
+                            x, rep = bt.result(j)
+                            req, fp, t_start = live.pop(j)
+                            res = Result(req.rid, x, rep.iterations,
+                                         rep.nb / rep.nb0 if rep.nb0 else 0.0, req.arrival,
+                                         t_start, time.perf_counter() - t0)
+                            with cv:
+                                results.append(res)
+                                state["bytes"] -= fp
+                                state["batch_active"] -= 1
+                                state["running"] -= 1
+                                cv.notify_all()
+                    bt.close()
+            except Exception as e:  # reported after the run
+                with cv:
+                    state["errors"].append(("batch", repr(e)))
+                    for req, fp, _ in list(live.values()) + new + inbox:
+                        state["bytes"] -= fp
+                        state["batch_active"] -= 1
+                        state["running"] -= 1
+                    inbox.clear()
+                    state["batch_dead"] = True
+                    cv.notify_all()
+
         threads = []
+        if self.batched:
+            bthread = threading.Thread(target=batch_worker, daemon=True)
+            bthread.start()
         pending: List[Request] = []
         i = 0
         with cv:
@@ -156,10 +222,25 @@ class Server:
                 while i < len(reqs) and reqs[i].arrival <= now:
                     pending.append(reqs[i])
                     i += 1
-                # admit in arrival order while a slot and the budget allow
-                while pending and state["free_slots"] > 0:
+                # admit in arrival order while a slot (or the batch) and the budget allow
+                while pending:
                     fp = footprint_bytes(pending[0].geometry, pending[0].solver)
                     if state["bytes"] + fp > self.budget:
+                        break
+                    if (self.batched and pending[0].solver == "cgls"
+                            and pending[0].storage == "f32"):
+                        if state["batch_active"] >= self.batch_jobs or state.get("batch_dead"):
+                            break
+                        req = pending.pop(0)
+                        state["batch_active"] += 1
+                        state["bytes"] += fp
+                        state["running"] += 1
+                        state["max_running"] = max(state["max_running"], state["running"])
+                        state["max_bytes"] = max(state["max_bytes"], state["bytes"])
+                        inbox.append((req, fp, now))
+                        cv.notify_all()
+                        continue
+                    if state["free_slots"] <= 0:
                         break
                     req = pending.pop(0)
                     si = free_streams.pop(0)
@@ -173,12 +254,19 @@ class Server:
                     t.start()
                 if i >= len(reqs) and not pending and state["running"] == 0:
                     break
+                if state.get("batch_dead") and pending:
+                    break
                 wait = None
                 if i < len(reqs):
                     wait = max(0.0, reqs[i].arrival - (time.perf_counter() - t0))
                 cv.wait(timeout=wait if wait is not None else 0.5)
         for t in threads:
             t.join()
+        if self.batched:
+            with cv:
+                state["batch_stop"] = True
+                cv.notify_all()
+            bthread.join()
         wall = time.perf_counter() - t0
         if state["errors"]:
             raise RuntimeError("requests failed: %s" % state["errors"])
@@ -187,7 +275,8 @@ class Server:
         return ServeStats(results, wall, state["max_running"], state["max_bytes"],
                           iterations=sum(r.iterations for r in results),
                           p50=float(np.percentile(lat, 50)) if len(lat) else 0.0,
-                          p99=float(np.percentile(lat, 99)) if len(lat) else 0.0)
+                          p99=float(np.percentile(lat, 99)) if len(lat) else 0.0,
+                          extra={"batch_steps": state["batch_steps"]})
 
 
 def serving_geometry(n: int, views: int) -> dict:

@@ -74,13 +74,17 @@ def test_hbm_budget_limits_admission(ct):
         Server(slots=2, hbm_budget_bytes=0.5 * biggest).run(reqs)
 
 
-def test_deterministic_results_bitwise_equal_alone_and_in_the_mix(ct):
+@pytest.mark.parametrize("batched", [False, True])
+def test_deterministic_results_bitwise_equal_alone_and_in_the_mix(ct, batched):
     """With fixed-point backprojection every solve is bitwise reproducible, so
-    a result computed among concurrent jobs equals the one computed alone."""
+    a result computed among concurrent jobs equals the one computed alone --
+    also when the CGLS requests share batched projector launches."""
     from paper_2110_13526_gb300.serving import Server
     reqs = make_requests(ct, n_req=8, rate=200.0, seed=13)
-    stats = Server(slots=4, deterministic=True).run(reqs)
+    stats = Server(slots=4, deterministic=True, batched=batched).run(reqs)
     assert stats.max_concurrent >= 2
+    if batched:
+        assert stats.extra["batch_steps"] > 0
     for req, res in zip(reqs, stats.results):
         g = ct.Geometry(**req.geometry, deterministic=True)
         fn = ct.cgls if req.solver == "cgls" else ct.lsqr
