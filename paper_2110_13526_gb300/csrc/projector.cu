@@ -662,7 +662,7 @@ __device__ __forceinline__ void walk_cm(const CmRay &r, bool ok, Fn &&fn) {
     using interior = std::integral_constant<bool, false>;
     int k = kb;
     for (; k < k_mid0; ++k) slab(clamped{});
-#pragma unroll 4
+#pragma unroll 8
     for (; k <= k_mid1; ++k) slab(interior{});
     for (; k <= ke; ++k) slab(clamped{});
 }
