@@ -380,6 +380,7 @@ ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out) {
         }
     }
     set_launch_order(g->pg);
+    set_row_pairing(g->pg, d.dv * d.sid / (d.sdd * d.vz));
     *out = g;
     return CT_OK;
 }

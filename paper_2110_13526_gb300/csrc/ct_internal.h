@@ -56,11 +56,15 @@ struct ProjGeom {
     int vgroup;              // launch order of A: views per group (set_launch_order)
     int vgroup_bt;           // launch order of A^T
     int nvb;                 // row blocks of the projector grid
+    int bt_pairs;            // column-major A^T: pairs of row blocks, a warp every other row
 };
 
 // Choose the order in which the projector kernels visit (view, row block)
 // tiles; call once the sizes of pg are set.
 void set_launch_order(ProjGeom &pg);
+// Then choose the lane-to-row mapping of the column-major A^T from the
+// height of a detector row at the isocentre in voxels (dv SID / (SDD vz)).
+void set_row_pairing(ProjGeom &pg, double row_vox);
 
 }  // namespace ct
 

@@ -45,6 +45,11 @@ CASES = {
     # depends on the last bit of sin/cos) and is not a parity case.
     "axes": dict(nx=21, ny=21, nz=11, vx=1.0, vy=1.0, vz=1.0, nu=33, nv=9, du=1.0, dv=1.0,
                  sid=150.0, sdd=250.0, nviews=8),
+    # detector rows under a voxel high (A^T pairs row blocks, a warp taking
+    # every other row) with three row blocks: one pair, one unpaired, and a
+    # ragged last column block
+    "pairs": dict(nx=40, ny=36, nz=30, vx=1.0, vy=1.0, vz=1.0, nu=50, nv=90, du=0.9, dv=0.9,
+                  sid=260.0, sdd=450.0, nviews=9),
     # single voxel and a one-pixel detector
     "tiny": dict(nx=1, ny=1, nz=1, vx=3.0, vy=3.0, vz=3.0, nu=5, nv=3, du=1.0, dv=1.0,
                  sid=50.0, sdd=90.0, nviews=4, angles=[0.1, 1.3, 2.9, 4.4]),
@@ -225,7 +230,7 @@ def test_host_tensors_round_trip(ct):
     assert torch.equal(p_host, p_dev)
 
 
-@pytest.mark.parametrize("name", ["ragged", "offcentre", "bigcone"])
+@pytest.mark.parametrize("name", ["ragged", "offcentre", "bigcone", "pairs"])
 def test_deterministic_backprojection(ct, name):
     """Fixed-point accumulation: bitwise repeatable, same parity bar."""
     cfg = CASES[name]
