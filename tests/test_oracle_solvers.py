@@ -7,6 +7,9 @@ identical results), the operator-call count that the restructuring saves
 discrepancy drift (Discussion: below 0.0001 % after 10 iterations), and the
 qualitative CGLS-vs-PSIRT ordering of the Results section.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -15,6 +18,10 @@ from oracle import OGeom, Operator, project
 from oracle.dense import dense_matrix
 from oracle.solvers import (DenseOperator, cgls, inv_sqrt_guarded, jacobi_weights, lsqr,
                             psirt, rowcol_weights, sirt)
+
+# values the paper prints, with their citations
+PAPER = {k: v["value"] for k, v in json.load(open(os.path.join(
+    os.path.dirname(os.path.abspath(__file__)), "golden", "paper_results.json")))["values"].items()}
 
 SMALL = dict(nx=32, ny=32, nz=32, vx=2.0, vy=2.0, vz=2.0, nu=64, nv=48, du=2.0, dv=2.0,
              sid=750.0, sdd=1200.0, nviews=45)
@@ -102,10 +109,10 @@ def test_discrepancy_monotone_and_drift():
     c = cgls(Operator(g), b, K=10, keep_iterates=True)
     rec = [np.linalg.norm(b - project(g, xk)) for xk in c.iterates]
     assert all(rec[k + 1] <= rec[k] * (1 + 1e-12) for k in range(len(rec) - 1))
-    assert abs(c.nb - rec[-1]) / rec[-1] < 1e-6
+    assert abs(c.nb - rec[-1]) / rec[-1] < PAPER["drift_10"]
     # ||A^T r_k|| is not monotone in theory; log it only (see readings)
     r2 = cgls(Operator(g), b, K=10, recompute_every=5)
-    assert abs(r2.nb - rec[-1]) / rec[-1] < 1e-6
+    assert abs(r2.nb - rec[-1]) / rec[-1] < PAPER["drift_10"]
 
 
 def test_stopping_rule():
@@ -129,8 +136,12 @@ def test_cgls_beats_psirt_at_equal_iterations():
     c = cgls(Operator(g), b, K=K)
     p = psirt(Operator(g), b, K=K)
     s = sirt(Operator(g), b, K=K)
-    # the paper: 0.18 % vs 3.64 % after 40 iterations, a factor of 20
-    assert c.history[-1] < 0.2 * p.history[-1]
+    # the paper: 0.18 % vs 3.64 % after 40 iterations, a factor of 20; this
+    # smaller problem must show at least a quarter of that factor
+    assert c.history[-1] < 4 * PAPER["e_cgls_40"] / PAPER["e_psirt_40"] * p.history[-1]
+    # the paper: PSIRT needs 112 iterations for what CGLS reaches in 20 (5.6x);
+    # here CGLS must reach PSIRT's 40-iteration level at least 2x sooner
+    assert PAPER["n_to_1pct_psirt"] / PAPER["n_to_1pct_cgls"] > 5
     level = p.history[-1]
     k_cgls = next(k for k, h in enumerate(c.history) if h <= level) + 1
     assert k_cgls * 2 <= K
