@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="serve mode: FP32 CGLS requests join one ct_batch (batched projector "
                          "launches, iteration-level scheduling)")
+    ap.add_argument("--batch-executors", type=int, default=1,
+                    help="serve mode with --batched: batches on their own streams")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
                     help="serve mode: CGLS Krylov-vector storage")
     ap.add_argument("--serve-requests", type=int, default=32,
@@ -401,7 +403,7 @@ def run_ops(a):
 
 
 def serve_stream(n_requests: int, rate: float, slots: int, budget_gb: float = 150.0,
-                 storage: str = "f32", batched: bool = False):
+                 storage: str = "f32", batched: bool = False, batch_executors: int = 1):
     """Serving workload: Poisson arrivals (seed 3), volumes 64..256^3, 60..360
     views, detector scaled to magnification 1.6, CGLS or LSQR to relative
     discrepancy 1e-3 or 50 updates; continuous batching over ``slots``
@@ -424,7 +426,8 @@ def serve_stream(n_requests: int, rate: float, slots: int, budget_gb: float = 15
         reqs.append(Request(s["rid"], cfg, b, s["solver"], s["arrival"], max_iter=50,
                             err_tol=1e-3, storage=storage))
     torch.cuda.synchronize()
-    stats = Server(slots=slots, hbm_budget_bytes=budget_gb * 1e9, batched=batched).run(reqs)
+    stats = Server(slots=slots, hbm_budget_bytes=budget_gb * 1e9, batched=batched,
+                   batch_executors=batch_executors).run(reqs)
     iters = stats.iterations
     return {"requests": len(reqs), "rate_per_s": rate, "slots": slots,
             "p50_s": stats.p50, "p99_s": stats.p99, "wall_s": stats.wall_s,
@@ -433,7 +436,8 @@ def serve_stream(n_requests: int, rate: float, slots: int, budget_gb: float = 15
             "max_gb_in_use": stats.max_bytes_in_use / 1e9,
             "mean_iterations": iters / max(len(reqs), 1),
             "storage": storage,
-            "batched": batched, "batch_steps": stats.extra.get("batch_steps", 0),
+            "batched": batched, "batch_executors": batch_executors if batched else 0,
+            "batch_steps": stats.extra.get("batch_steps", 0),
             "mean_rel_discrepancy": float(sum(r.rel_discrepancy for r in stats.results)
                                           / max(len(stats.results), 1)),
             "workload": "Poisson arrivals (seed 3); n in {64,128,192,256}, views in "
@@ -501,7 +505,8 @@ def run_serve(a):
     import torch
     torch.cuda.set_device(0)
     out = {"mode": "serve"}
-    out.update(serve_stream(a.requests, a.rate, a.slots, storage=a.storage, batched=a.batched))
+    out.update(serve_stream(a.requests, a.rate, a.slots, storage=a.storage, batched=a.batched,
+                            batch_executors=a.batch_executors))
     print(json.dumps(out))
     return 0
 

@@ -11,9 +11,10 @@ arrival order).  Every solve is the unchanged library call (ct_cgls /
 ct_lsqr): a result does not depend on which other jobs share the GPU, up to
 the float-atomic summation order of the backprojection.
 
-With ``batched=True`` the FP32 CGLS requests instead join one ct_batch
-(iteration-level continuous batching): a batch thread advances all admitted
-CGLS jobs one update per step, with the backprojections of all of them in one
+With ``batched=True`` the FP32 CGLS requests instead join a ct_batch
+(iteration-level continuous batching; ``batch_executors`` batches on their
+own streams, each request to the least loaded): a batch thread advances its
+admitted CGLS jobs one update per step, with the backprojections of all of them in one
 persistent kernel launch and their projections in another, inside a CUDA
 graph; jobs join between steps as they are admitted and leave when their
 stopping rule fires.  LSQR and reduced-storage requests keep the per-slot
@@ -90,14 +91,16 @@ class ServeStats:
 
 class Server:
     def __init__(self, slots: int = 8, hbm_budget_bytes: float = 150e9, device=None,
-                 deterministic: bool = False, batched: bool = False, batch_jobs: int = 32):
+                 deterministic: bool = False, batched: bool = False, batch_jobs: int = 32,
+                 batch_executors: int = 1):
         if slots < 1:
             raise ValueError("slots must be >= 1")
-        if batch_jobs < 1:
-            raise ValueError("batch_jobs must be >= 1")
+        if batch_jobs < 1 or batch_executors < 1:
+            raise ValueError("batch_jobs and batch_executors must be >= 1")
         self.slots = slots
         self.batched = batched
         self.batch_jobs = batch_jobs
+        self.batch_executors = batch_executors
         self.deterministic = deterministic
         self.budget = int(hbm_budget_bytes)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
@@ -127,7 +130,10 @@ class Server:
         state = {"free_slots": self.slots, "bytes": 0, "running": 0, "max_running": 0,
                  "max_bytes": 0, "errors": [], "batch_active": 0, "batch_stop": False,
                  "batch_steps": 0}
-        inbox: List[Tuple[Request, int, float]] = []    # admitted, not yet in the batch
+        # per batch executor: admitted jobs not yet in its batch, and its load
+        n_ex = self.batch_executors if self.batched else 0
+        inboxes: List[List[Tuple[Request, int, float]]] = [[] for _ in range(n_ex)]
+        load = [0] * n_ex
         results: List[Result] = []
         streams = [torch.cuda.Stream(device=self.device) for _ in range(self.slots)]
         free_streams = list(range(self.slots))
@@ -162,7 +168,11 @@ class Server:
                 free_streams.append(si)
                 cv.notify_all()
 
-        def batch_worker():
+        def batch_worker(k: int):
+            """Executor k: one ct_batch on its own stream, so that the vector
+            kernels of one batch's step overlap the projector launches of
+            another's."""
+            inbox = inboxes[k]
             live = {}                                     # job id -> (request, bytes, start)
             new: List[Tuple[Request, int, float]] = []    # taken from the inbox, not yet added
             try:
@@ -185,7 +195,8 @@ class Server:
                             live[jid] = new.pop(0)
                         if any(not bt.done(j) for j in live):
                             bt.step()
-                            state["batch_steps"] += 1
+                            with cv:
+                                state["batch_steps"] += 1
                         for j in [j for j in live if bt.done(j)]:
                             x, rep = bt.result(j)
                             req, fp, t_start = live.pop(j)
@@ -196,6 +207,7 @@ class Server:
                                 results.append(res)
                                 state["bytes"] -= fp
                                 state["batch_active"] -= 1
+                                load[k] -= 1
                                 state["running"] -= 1
                                 cv.notify_all()
                     bt.close()
@@ -205,15 +217,17 @@ class Server:
                     for req, fp, _ in list(live.values()) + new + inbox:
                         state["bytes"] -= fp
                         state["batch_active"] -= 1
+                        load[k] -= 1
                         state["running"] -= 1
                     inbox.clear()
                     state["batch_dead"] = True
                     cv.notify_all()
 
         threads = []
-        if self.batched:
-            bthread = threading.Thread(target=batch_worker, daemon=True)
-            bthread.start()
+        bthreads = [threading.Thread(target=batch_worker, args=(k,), daemon=True)
+                    for k in range(n_ex)]
+        for t in bthreads:
+            t.start()
         pending: List[Request] = []
         i = 0
         with cv:
@@ -232,12 +246,14 @@ class Server:
                         if state["batch_active"] >= self.batch_jobs or state.get("batch_dead"):
                             break
                         req = pending.pop(0)
+                        k = min(range(n_ex), key=lambda j: load[j])   # least loaded executor
+                        load[k] += 1
                         state["batch_active"] += 1
                         state["bytes"] += fp
                         state["running"] += 1
                         state["max_running"] = max(state["max_running"], state["running"])
                         state["max_bytes"] = max(state["max_bytes"], state["bytes"])
-                        inbox.append((req, fp, now))
+                        inboxes[k].append((req, fp, now))
                         cv.notify_all()
                         continue
                     if state["free_slots"] <= 0:
@@ -262,11 +278,11 @@ class Server:
                 cv.wait(timeout=wait if wait is not None else 0.5)
         for t in threads:
             t.join()
-        if self.batched:
-            with cv:
-                state["batch_stop"] = True
-                cv.notify_all()
-            bthread.join()
+        with cv:
+            state["batch_stop"] = True
+            cv.notify_all()
+        for t in bthreads:
+            t.join()
         wall = time.perf_counter() - t0
         if state["errors"]:
             raise RuntimeError("requests failed: %s" % state["errors"])
