@@ -105,10 +105,13 @@ ct_status backproject_impl(const ct_geometry *g, const BackScratch &s, const flo
     const ProjGeom &pg = g->pg;
     const int64_t n = g->nvox;
     if (!g->deterministic) {
-        CT_TRY(launch_scale(out, n, beta, st));
+        // column-major Siddon kernels accumulate in acc_t only, and the
+        // combine applies beta; the others accumulate into out itself
+        const bool zfast_only = pg.proj == CT_PROJ_SIDDON && pg.cm;
+        if (!zfast_only) CT_TRY(launch_scale(out, n, beta, st));
         CT_CUDA_TRY(cudaMemsetAsync(s.acc_t, 0, (size_t)n * sizeof(float), st));
         CT_TRY(launch_backward(pg, e, rho, c, out, s.acc_t, power, st));
-        return launch_combine(pg, out, s.acc_t, w, partials, st);
+        return launch_combine(pg, out, s.acc_t, w, partials, st, zfast_only ? beta : 1.f);
     }
     CT_CUDA_TRY(cudaMemsetAsync(s.q, 0, 2 * (size_t)n * sizeof(long long), st));
     CT_TRY(launch_det_scale(e, CT_F32, rho, g->nrays, det_value_bound(g, power), c, s.part,

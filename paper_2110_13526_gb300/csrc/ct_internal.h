@@ -250,10 +250,12 @@ constexpr int kVecThreads = 256;
 ct_status launch_transpose(const ProjGeom &pg, const float *v, const float *w, float *t,
                            float *out_plain, cudaStream_t st);
 // g = acc + transpose(acc_t)  ([nz][nx][ny] -> [nz][ny][nx]); with partials,
-// one FP64 partial per CTA of sum (w o g)^2 (w may be NULL).
+// one FP64 partial per CTA of sum (w o g)^2 (w may be NULL).  Column-major
+// geometries keep all of A^T in acc_t ([y][x][z]): there g = beta g +
+// acc_t transposed (beta 0: g is not read); the others add (beta ignored).
 int transpose_grid_count(const ProjGeom &pg);
 ct_status launch_combine(const ProjGeom &pg, float *g, const float *acc_t, const float *w,
-                         double *partials, cudaStream_t st);
+                         double *partials, cudaStream_t st, float beta = 1.f);
 // Typed transpose: t (dt) = transpose of v (dt), [nz][ny][nx] -> [nz][nx][ny].
 ct_status launch_transpose_typed(const ProjGeom &pg, const void *v, void *t, int dt,
                                  cudaStream_t st);

@@ -37,14 +37,41 @@ __device__ __forceinline__ double block_sum(double x, double *sh) {
 }
 
 // Fixed-order sum of partials by one CTA (1024 threads); result in thread 0.
+// Four running sums per thread keep four loads in flight (A's 155520 CTA
+// partials at 256^3 took 50 us one load at a time).
 __device__ __forceinline__ double sum_partials(const double *__restrict__ p, int64_t n,
                                                double *sh) {
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += p[i];
-    return block_sum(s, sh);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    const int64_t st = blockDim.x;
+    int64_t i = threadIdx.x;
+    for (; i + 3 * st < n; i += 4 * st) {
+        s0 += p[i];
+        s1 += p[i + st];
+        s2 += p[i + 2 * st];
+        s3 += p[i + 3 * st];
+    }
+    for (; i < n; i += st) s0 += p[i];
+    return block_sum((s0 + s1) + (s2 + s3), sh);
 }
 
 __device__ __forceinline__ double safe_div(double a, double b) { return b != 0.0 ? a / b : 0.0; }
+
+// First stage of a long partial sum: CTA b adds p[b chunk, (b + 1) chunk) in
+// a fixed order into out[b].  One SM adds FP64 at about 4e9 per second on
+// GB300, so A's 155520 CTA partials at 256^3 took 50 us in one CTA.
+__global__ void __launch_bounds__(256) k_partials_stage(const double *__restrict__ p, int64_t n,
+                                                        int64_t chunk, double *__restrict__ out) {
+    __shared__ double sh[32];
+    const int64_t lo = blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+    double s = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += p[i];
+    const double t = block_sum(s, sh);
+    if (threadIdx.x == 0) out[blockIdx.x] = t;
+}
+
+// Partial counts above this are first summed in chunks by k_partials_stage.
+constexpr int64_t kStageMin = 8192;
+constexpr int kStageMax = 256;   // CTAs (and second-stage partials) at most
 
 // ---- CGLS ------------------------------------------------------------------
 // zs: the direction is stored as z~ = zs z (zs a power of two, 1 in FP32
@@ -61,15 +88,14 @@ __global__ void k_sino_weighted_copy(S *__restrict__ e, const float *__restrict_
                                      const float *__restrict__ L, int64_t n,
                                      double *__restrict__ part) {
     __shared__ double sh[32];
-    double sq = 0.0;
+    SqSum sq;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const S v = from_f<S>(L ? L[i] * b[i] : b[i]);
         e[i] = v;
-        const double q = to_f(v);
-        sq = fma(q, q, sq);
+        sq.add(to_f(v));
     }
-    const double t = block_sum(sq, sh);
+    const double t = block_sum(sq.value(), sh);
     if (threadIdx.x == 0 && part) part[blockIdx.x] = t;
 }
 
@@ -79,15 +105,30 @@ __global__ void k_sino_axpy(S *__restrict__ e, const S *__restrict__ p, int64_t 
                             const double *__restrict__ alpha, double *__restrict__ part) {
     __shared__ double sh[32];
     const float a = (float)alpha[0];
-    double sq = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    SqSum sq;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    // four elements per pass: their loads are in flight together
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        float ev[4], pv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            ev[k] = to_f(e[i + k * stride]);
+            pv[k] = to_f(p[i + k * stride]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const S v = from_f<S>(fmaf(-a, pv[k], ev[k]));
+            e[i + k * stride] = v;
+            sq.add(to_f(v));
+        }
+    }
+    for (; i < n; i += stride) {
         const S v = from_f<S>(fmaf(-a, to_f(p[i]), to_f(e[i])));
         e[i] = v;
-        const double q = to_f(v);
-        sq = fma(q, q, sq);
+        sq.add(to_f(v));
     }
-    const double t = block_sum(sq, sh);
+    const double t = block_sum(sq.value(), sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -95,13 +136,11 @@ __global__ void k_sino_axpy(S *__restrict__ e, const S *__restrict__ p, int64_t 
 template <class S>
 __global__ void k_norm2_t(const S *__restrict__ v, int64_t n, double *__restrict__ part) {
     __shared__ double sh[32];
-    double sq = 0.0;
+    SqSum sq;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const double q = to_f(v[i]);
-        sq = fma(q, q, sq);
-    }
-    const double t = block_sum(sq, sh);
+         i += (int64_t)gridDim.x * blockDim.x)
+        sq.add(to_f(v[i]));
+    const double t = block_sum(sq.value(), sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -121,7 +160,7 @@ __global__ void k_vol_update(float *__restrict__ x, S *__restrict__ z,
     const float a = first ? 0.f : (float)a_pend[0];
     const float b = first ? 0.f : (float)beta[0];
     const float gs = (float)zs[0];
-    double sq = 0.0;
+    SqSum sq;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         float r = g[i] * gs;
@@ -138,13 +177,10 @@ __global__ void k_vol_update(float *__restrict__ x, S *__restrict__ z,
             zn = from_f<S>(fmaf(b, zo, r));
         }
         z[i] = zn;
-        if (ZNORM) {
-            const double q = to_f(zn);
-            sq = fma(q, q, sq);
-        }
+        if (ZNORM) sq.add(to_f(zn));
     }
     if (ZNORM) {
-        const double t = block_sum(sq, sh);
+        const double t = block_sum(sq.value(), sh);
         if (threadIdx.x == 0) zpart[blockIdx.x] = t;
     }
 }
@@ -161,17 +197,16 @@ __global__ void k_tikhonov_grad(float *__restrict__ g, const float *__restrict__
     __shared__ double sh[32];
     const float a = first ? 0.f : (float)a_pend[0];
     const float l = (float)lam;
-    double sq = 0.0;
+    SqSum sq;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         float xc = x[i];
         if (!first && a != 0.f) xc = fmaf(a, to_f(z[i]), xc);
         const float gi = fmaf(-l, xc, g[i]);
         g[i] = gi;
-        const double q = W ? (double)(W[i] * gi) : (double)gi;
-        sq = fma(q, q, sq);
+        sq.add(W ? W[i] * gi : gi);
     }
-    const double t = block_sum(sq, sh);
+    const double t = block_sum(sq.value(), sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -368,16 +403,16 @@ __global__ void k_lsqr_v(float *__restrict__ v, const float *__restrict__ g,
                          double *__restrict__ part) {
     __shared__ double sh[32];
     const float b = (float)S->beta;
-    double sq = 0.0;
+    SqSum sq;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         float t = g[i];
         if (W) t *= W[i];
         t = fmaf(-b, v[i], t);
         v[i] = t;
-        sq = fma((double)t, (double)t, sq);
+        sq.add(t);
     }
-    const double t = block_sum(sq, sh);
+    const double t = block_sum(sq.value(), sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -480,6 +515,7 @@ struct Solve {
     float *T = nullptr;           // transposed scratch volume (input copy / accumulator)
     BackScratch bs;               // backprojection scratch (T, or int64 accumulators)
     double *part = nullptr;       // FP64 partial sums
+    double *part2 = nullptr;      // their first-stage sums (reduce)
     float *W = nullptr, *L = nullptr;
     int64_t n, m;
     Solve(const ct_geometry *g_, cudaStream_t s, bool timing)
@@ -491,6 +527,7 @@ struct Solve {
         int64_t np = std::max<int64_t>(forward_partials(pg), transpose_grid_count(pg));
         np = std::max<int64_t>(np, std::max(vec_grid(n), vec_grid(m)));
         CT_TRY(ws.alloc(&part, (size_t)np));
+        CT_TRY(ws.alloc(&part2, (size_t)kStageMax));
         if (precond != CT_PRECOND_NONE) {
             CT_TRY(ws.alloc(&W, (size_t)n));
             if (precond == CT_PRECOND_ROWCOL) CT_TRY(ws.alloc(&L, (size_t)std::max<int64_t>(m, 1)));
@@ -544,9 +581,13 @@ struct Solve {
     // (deterministic) sums.  In three parts: back_pre clears the accumulators
     // (and finds the fixed-point scale), back_proj scatters, back_post
     // combines them into gout.
+    // Column-major Siddon kernels accumulate A^T in T only; their combine
+    // then overwrites gout (beta 0) instead of adding to a cleared one.
+    bool zfast_only() const { return pg.proj == CT_PROJ_SIDDON && pg.cm; }
     ct_status back_pre(const void *e, int edt, float *gout, Coef c) {
         if (!g->deterministic) {
-            CT_CUDA_TRY(cudaMemsetAsync(gout, 0, (size_t)n * sizeof(float), st));
+            if (!zfast_only())
+                CT_CUDA_TRY(cudaMemsetAsync(gout, 0, (size_t)n * sizeof(float), st));
             CT_CUDA_TRY(cudaMemsetAsync(T, 0, (size_t)n * sizeof(float), st));
             return CT_OK;
         }
@@ -565,7 +606,8 @@ struct Solve {
         return CT_OK;
     }
     ct_status back_post(float *gout, const float *wnorm, double *partials) {
-        if (!g->deterministic) return launch_combine(pg, gout, T, wnorm, partials, st);
+        if (!g->deterministic)
+            return launch_combine(pg, gout, T, wnorm, partials, st, zfast_only() ? 0.f : 1.f);
         return launch_combine_det(pg, gout, 0.f, bs.q, bs.q + n, bs.inv, wnorm, partials, st);
     }
     ct_status back_t(const void *e, int edt, float *gout, Coef c, const float *wnorm,
@@ -588,6 +630,21 @@ struct Solve {
     }
     ct_status back(const float *e, float *gout, Coef c, const float *wnorm, double *partials) {
         return back_t(e, CT_F32, gout, c, wnorm, partials);
+    }
+    // The partials p[0, n) a one-CTA scalar kernel will sum: long lists are
+    // first summed in fixed chunks (k_partials_stage); *pp, *np: what to sum.
+    ct_status reduce(const double *p, int64_t n, const double **pp, int64_t *np) {
+        *pp = p;
+        *np = n;
+        if (n <= kStageMin) return CT_OK;
+        const int64_t blocks = std::min<int64_t>(kStageMax, (n + 1023) / 1024);
+        const int64_t chunk = (n + blocks - 1) / blocks;
+        const int64_t used = (n + chunk - 1) / chunk;
+        k_partials_stage<<<(unsigned)used, 256, 0, st>>>(p, n, chunk, part2);
+        CT_CHECK_LAUNCH();
+        *pp = part2;
+        *np = used;
+        return CT_OK;
     }
     // Is x0 nonzero?  (One reduction and one host read.)
     ct_status nonzero(const float *x, bool *out) {
@@ -764,7 +821,10 @@ struct CglsJob {
     // NP2 (+ lam ||d_x||^2), alpha; e_b = e_b - alpha p_b with the NB partials
     ct_status tail() {
         const cudaStream_t s = sv.st;
-        k_cgls_np2<<<1, 1024, 0, s>>>(sv.part, nfp, S, zpart, gn, lam);
+        const double *pp = nullptr;
+        int64_t np = 0;
+        CT_TRY(sv.reduce(sv.part, nfp, &pp, &np));
+        k_cgls_np2<<<1, 1024, 0, s>>>(pp, np, S, zpart, gn, lam);
         CT_CHECK_LAUNCH();
         k_sino_axpy<<<gm, kVecThreads, 0, s>>>(e, p, m, &S->alpha, sv.part);
         CT_CHECK_LAUNCH();
@@ -990,7 +1050,10 @@ ct_status lsqr_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
         k_lsqr_coef_fwd<<<1, 1, 0, s>>>(S);
         CT_CHECK_LAUNCH();
         CT_TRY(sv.forward(tin, sv.W != nullptr, u, cf, sv.part));
-        k_lsqr_beta<<<1, 1024, 0, s>>>(sv.part, nfp, S);
+        const double *pp = nullptr;
+        int64_t np = 0;
+        CT_TRY(sv.reduce(sv.part, nfp, &pp, &np));
+        k_lsqr_beta<<<1, 1024, 0, s>>>(pp, np, S);
         CT_CHECK_LAUNCH();
         // alpha v = W A^T L u - beta v
         CT_TRY(sv.back(u, gv, cb, nullptr, nullptr));

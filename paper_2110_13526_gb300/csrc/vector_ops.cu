@@ -70,19 +70,18 @@ __global__ void __launch_bounds__(256) k_combine(int nx, int ny, float *__restri
         if (x < nx && y < ny) tile[j][threadIdx.x] = acc_t[zoff + (size_t)x * ny + y];
     }
     __syncthreads();
-    double sq = 0.0;
+    SqSum sq;
     for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
         const int y = y0 + j, x = x0 + threadIdx.x;
         if (x < nx && y < ny) {
             const size_t i = zoff + (size_t)y * nx + x;
             const float val = g[i] + tile[threadIdx.x][j];
             g[i] = val;
-            const double q = w ? (double)(w[i] * val) : (double)val;
-            sq = fma(q, q, sq);
+            sq.add(w ? w[i] * val : val);
         }
     }
     if (partials) {
-        const double t = block_sum_1d(sq, sh);
+        const double t = block_sum_1d(sq.value(), sh);
         if (threadIdx.x == 0 && threadIdx.y == 0)
             partials[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = t;
     }
@@ -111,13 +110,11 @@ __global__ void k_scale_dev(float *__restrict__ out, int64_t n, const double *__
 __global__ void k_norm2(const float *__restrict__ v, const float *__restrict__ w, int64_t n,
                         double *__restrict__ partials) {
     __shared__ double sh[32];
-    double sq = 0.0;
+    SqSum sq;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const double q = w ? (double)(w[i] * v[i]) : (double)v[i];
-        sq = fma(q, q, sq);
-    }
-    const double t = block_sum_1d(sq, sh);
+         i += (int64_t)gridDim.x * blockDim.x)
+        sq.add(w ? w[i] * v[i] : v[i]);
+    const double t = block_sum_1d(sq.value(), sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
@@ -140,9 +137,15 @@ __global__ void __launch_bounds__(1024) k_sum(const double *__restrict__ partial
 // and writing along the fastest axis of each layout.
 namespace {
 
+// Tiles of (x, z) for every CTA, about two waves of 8 CTAs on each of 152
+// SMs, each CTA walking y planes (at least two, handled in pairs by
+// k_from_zfast so that twice the loads are in flight per sync).
 dim3 zfast_grid(const ProjGeom &pg) {
-    return dim3((unsigned)((pg.nx + kTile - 1) / kTile), (unsigned)((pg.nz + kTile - 1) / kTile),
-                (unsigned)std::min(pg.ny, 65535));
+    const int64_t gx = (pg.nx + kTile - 1) / kTile, gy = (pg.nz + kTile - 1) / kTile;
+    int64_t gz = (int64_t(152) * 8 * 2 + gx * gy - 1) / (gx * gy);
+    gz = std::min<int64_t>(gz, (pg.ny + 1) / 2);
+    gz = std::max<int64_t>(1, std::min<int64_t>(gz, 65535));
+    return dim3((unsigned)gx, (unsigned)gy, (unsigned)gz);
 }
 
 // in [nz][ny][nx] -> t [ny][nx][nz]; optionally scaled by w (FP32 only) and
@@ -189,39 +192,48 @@ __global__ void __launch_bounds__(256) k_from_zfast(int nx, int ny, int nz, T *_
                                                     float beta, ZAcc acc,
                                                     const float *__restrict__ w,
                                                     double *__restrict__ partials) {
-    __shared__ double tile[kTile][kTile + 1];
+    __shared__ float tile[2][kTile][kTile + 1];
     __shared__ double sh[32];
     const int x0 = blockIdx.x * kTile, z0 = blockIdx.y * kTile;
     const double s = acc.q ? acc.inv[0] : 1.0;
-    double sq = 0.0;
-    for (int y = blockIdx.z; y < ny; y += gridDim.z) {
-        for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
-            const int x = x0 + j, z = z0 + threadIdx.x;
-            if (x < nx && z < nz) {
-                const size_t it = ((size_t)y * nx + x) * nz + z;
-                tile[j][threadIdx.x] = acc.q ? (double)acc.q[it] * s : (double)acc.f[it];
+    SqSum sq;
+    // planes y and y + gridDim.z together (the second may not exist)
+    for (int y = blockIdx.z; y < ny; y += 2 * (int)gridDim.z) {
+        const int yy[2] = {y, y + (int)gridDim.z};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (yy[h] >= ny) continue;   // uniform in the CTA
+            for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
+                const int x = x0 + j, z = z0 + threadIdx.x;
+                if (x < nx && z < nz) {
+                    const size_t it = ((size_t)yy[h] * nx + x) * nz + z;
+                    tile[h][j][threadIdx.x] = acc.q ? (float)((double)acc.q[it] * s) : acc.f[it];
+                }
             }
         }
         __syncthreads();
-        for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
-            const int z = z0 + j, x = x0 + threadIdx.x;
-            if (x < nx && z < nz) {
-                const size_t i = ((size_t)z * ny + y) * nx + x;
-                float val = (float)tile[threadIdx.x][j];
-                if (beta != 0.f) val = fmaf(beta, to_f(out[i]), val);  // beta 1: a plain add
-                const T st = from_f<T>(val);
-                out[i] = st;
-                if (partials) {
-                    const float vs = to_f(st);
-                    const double qq = w ? (double)(w[i] * vs) : (double)vs;
-                    sq = fma(qq, qq, sq);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (yy[h] >= ny) continue;
+            for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
+                const int z = z0 + j, x = x0 + threadIdx.x;
+                if (x < nx && z < nz) {
+                    const size_t i = ((size_t)z * ny + yy[h]) * nx + x;
+                    float val = tile[h][threadIdx.x][j];
+                    if (beta != 0.f) val = fmaf(beta, to_f(out[i]), val);  // beta 1: a plain add
+                    const T st = from_f<T>(val);
+                    out[i] = st;
+                    if (partials) {
+                        const float vs = to_f(st);
+                        sq.add(w ? w[i] * vs : vs);
+                    }
                 }
             }
         }
         __syncthreads();
     }
     if (partials) {
-        const double t = block_sum_1d(sq, sh);
+        const double t = block_sum_1d(sq.value(), sh);
         if (threadIdx.x == 0 && threadIdx.y == 0)
             partials[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = t;
     }
@@ -280,12 +292,13 @@ ct_status launch_transpose(const ProjGeom &pg, const float *v, const float *w, f
 }
 
 ct_status launch_combine(const ProjGeom &pg, float *g, const float *acc_t, const float *w,
-                         double *partials, cudaStream_t st) {
+                         double *partials, cudaStream_t st, float beta) {
     if (pg.proj != CT_PROJ_SIDDON) {
         if (!partials) return CT_OK;
         return launch_norm2(g, w, (int64_t)pg.nx * pg.ny * pg.nz, partials, st);
     }
-    if (pg.cm) return from_zfast<float>(pg, g, 1.f, ZAcc{acc_t, nullptr, nullptr}, w, partials, st);
+    if (pg.cm)
+        return from_zfast<float>(pg, g, beta, ZAcc{acc_t, nullptr, nullptr}, w, partials, st);
     dim3 gr((pg.nx + kTile - 1) / kTile, (pg.ny + kTile - 1) / kTile, pg.nz), bl(kTile, 8);
     k_combine<<<gr, bl, 0, st>>>(pg.nx, pg.ny, g, acc_t, w, partials);
     CT_CHECK_LAUNCH();
@@ -442,7 +455,7 @@ __global__ void __launch_bounds__(256) k_combine_det(int nx, int ny, float *__re
     }
     __syncthreads();
     const double s = inv[0];
-    double sq = 0.0;
+    SqSum sq;
     for (int j = threadIdx.y; j < kTile; j += blockDim.y) {
         const int y = y0 + j, x = x0 + threadIdx.x;
         if (x < nx && y < ny) {
@@ -451,12 +464,11 @@ __global__ void __launch_bounds__(256) k_combine_det(int nx, int ny, float *__re
             float val = (float)((double)q * s);
             if (beta != 0.f) val = fmaf(beta, out[i], val);
             out[i] = val;
-            const double qq = w ? (double)(w[i] * val) : (double)val;
-            sq = fma(qq, qq, sq);
+            sq.add(w ? w[i] * val : val);
         }
     }
     if (partials) {
-        const double t = block_sum_1d(sq, sh);
+        const double t = block_sum_1d(sq.value(), sh);
         if (threadIdx.x == 0 && threadIdx.y == 0)
             partials[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = t;
     }

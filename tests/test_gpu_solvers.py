@@ -293,3 +293,21 @@ def test_graph_replay_equals_direct_launches(ct, small):
         x2, r2 = ct.lsqr(g, bd, max_iter=9, timing=True, **kw)
         assert torch.equal(x1, x2), kw
         assert r1.history == r2.history and (r1.n_forward, r1.n_back) == (r2.n_forward, r2.n_back)
+
+
+@pytest.mark.parametrize("spread", [0.0, 40.0])
+def test_streaming_norms_are_fp64_accurate(ct, small, spread):
+    """NB0 = ||b|| comes from the streaming kernels' per-thread FP32-pair sums
+    of squares and FP64 block sums: within 1e-12 of the FP64 norm, also for
+    zeros and for terms far outside the FP32-pair range (|b| from 1e-20 to
+    1e20, which the FP64 side path takes)."""
+    cfg = small[0]
+    g = ct.Geometry(**cfg)
+    rng = np.random.default_rng(5)
+    b = rng.uniform(0.0, 1000.0, g.sino_shape) * 10.0 ** rng.uniform(-spread / 2, spread / 2,
+                                                                      g.sino_shape)
+    b[rng.random(g.sino_shape) < 0.1] = 0.0
+    b32 = b.astype(np.float32)
+    _, rep = ct.cgls(g, torch.from_numpy(b32).cuda(), max_iter=1)
+    want = float(np.sqrt(np.sum(b32.astype(np.float64) ** 2)))
+    assert rep.nb0 == pytest.approx(want, rel=1e-12)
