@@ -75,6 +75,21 @@ def test_solver_options_rejected_before_cuda(built_lib):
     assert b"geometry" in L.ct_last_error()
 
 
+def test_batch_arguments_rejected_before_cuda(built_lib):
+    """ct_batch_*: NULL handles and outputs are argument errors (status 1)
+    with a message; destroying NULL is a no-op."""
+    import paper_2110_13526_gb300 as ct
+    L = ct.lib()
+    n = ctypes.c_int32()
+    assert L.ct_batch_create(None, None) == 1
+    assert L.ct_batch_step(None, ctypes.byref(n)) == 1
+    assert b"batch" in L.ct_last_error()
+    assert L.ct_batch_poll(None, 1, ctypes.byref(n), None) == 1
+    assert L.ct_batch_remove(None, 1) == 1
+    assert L.ct_batch_add_cgls(None, None, None, None, None, ctypes.byref(n)) == 1
+    assert L.ct_batch_destroy(None) == 0
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     import paper_2110_13526_gb300 as ct
     monkeypatch.setattr(ct, "_lib", None)
