@@ -1374,11 +1374,15 @@ struct ct_batch {
                     f0.push_back(en.job->sv.n_fwd);
                     b0.push_back(en.job->sv.n_back);
                 }
-                CT_TRY(graph->capture([&]() { return step_body(); },
-                                      [&](cudaStream_t cs) { set_stream(cs); }));
+                const ct_status cs = graph->capture([&]() { return step_body(); },
+                                                    [&](cudaStream_t c) { set_stream(c); });
                 for (size_t k = 0; k < jobs.size(); ++k) {   // counted again per replay
                     jobs[k].job->sv.n_fwd = f0[k];
                     jobs[k].job->sv.n_back = b0[k];
+                }
+                if (cs != CT_OK) {   // nothing ran; the next step captures again
+                    graph.reset();
+                    return cs;
                 }
             }
             CT_TRY(graph->launch(st));
