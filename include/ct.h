@@ -171,12 +171,17 @@ ct_status ct_project_norm2(const ct_geometry *g, const float *d_vol, float *d_si
  * allocator call).  Same arguments and results as ct_project_norm2; the
  * volume is read in place, and the FP64 partial sums live in a fixed 2 MiB
  * device array that every GPU loading the library holds until exit.
- * Limit (Siddon): nviews * ceil(nu/32) * ceil(nv/8) <= 262144, else
- * CT_ERR_INVALID_ARG with a message saying so; the footprint projectors need
- * at most 1216 partials.
+ * Limit (Siddon): the launch's CTA count, ceil(nu/32) * ceil(nv/8) * V,
+ * must not exceed 262144, where V = nviews rounded up to a multiple of the
+ * view group G = ceil(nviews / floor(65535 / ceil(nv/8))) (G = 1, V = nviews,
+ * unless nviews * ceil(nv/8) > 65535); else CT_ERR_INVALID_ARG with a message
+ * giving the count.  The footprint projectors need at most 1216 partials.
  * The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress) with the device current; make that first call before
- * any stream capture.  All calls share the array: calls that overlap on the
+ * any stream capture.  The address stays cached for the life of the process:
+ * do not call this entry point on a device after a device reset
+ * (cudaDeviceReset), which moves the array and also invalidates every
+ * geometry created on that device before it.  All calls share the array: calls that overlap on the
  * GPU (other streams, other threads) race on it and must be serialised by the
  * caller.  Each call overwrites what it reads, so the contents a previous
  * call left behind never matter.  No cudaMalloc, cudaFree or allocating

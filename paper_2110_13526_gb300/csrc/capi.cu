@@ -187,10 +187,14 @@ void view_constants(const ct_geometry_desc &d, const std::vector<double> &ang,
     }
 }
 
-// Per-column ray parameters (see ColParams), in FP64, stored FP32.
+// x * 2^44 rounded to the nearest integer (ColFixed).
+long long q44(double x) { return std::llround(std::ldexp(x, 44)); }
+
+// Per-column ray parameters (see ColParams), in FP64, stored FP32, and the
+// same lines in fixed point for the column-major kernels (ColFixed).
 void column_params(const ct_geometry_desc &d, const std::vector<double> &ang,
                    std::vector<float4> &ca_out, std::vector<float4> &cb_out,
-                   std::vector<int> &fl_out) {
+                   std::vector<int> &fl_out, std::vector<ColFixed> &cq_out) {
     const double h[3] = {d.vx, d.vy, d.vz};
     const int N[3] = {d.nx, d.ny, d.nz};
     const double lo[3] = {-0.5 * d.nx * d.vx + d.off_x, -0.5 * d.ny * d.vy + d.off_y,
@@ -199,6 +203,7 @@ void column_params(const ct_geometry_desc &d, const std::vector<double> &ang,
     ca_out.resize(ncol);
     cb_out.resize(ncol);
     fl_out.resize(ncol);
+    cq_out.resize(ncol);
     for (size_t k = 0; k < ang.size(); ++k) {
         const double c = std::cos(ang[k]), s = std::sin(ang[k]);
         const double src[3] = {d.sid * c, d.sid * s, 0.0};
@@ -233,6 +238,7 @@ void column_params(const ct_geometry_desc &d, const std::vector<double> &ang,
                 ca_out[i] = make_float4(0.f, 1e30f, 0.f, 0.f);
                 cb_out[i] = make_float4(1e30f, 0.f, 0.f, -1.f);
                 fl_out[i] = 0;
+                cq_out[i] = ColFixed{0, q44(65536.0), 0, 0, q44(65536.0), 0, 0.f, -1.f, 0, 0};
                 continue;
             }
             const double A = D[la] / adx;
@@ -246,11 +252,34 @@ void column_params(const ct_geometry_desc &d, const std::vector<double> &ang,
             ca_out[i] = make_float4((float)A, (float)XI0, (float)C0, (float)C1);
             cb_out[i] = make_float4((float)Z0, (float)Z1, (float)wsrc, (float)wpix);
             fl_out[i] = (ax == 0 ? 1 : 0) | (rev ? 2 : 0);
+            const double lim = 65536.0;   // a ray this far out misses the volume
+            cq_out[i] = ColFixed{q44(A), q44(std::fmin(std::fmax(XI0, -lim), lim)), q44(C0),
+                                 q44(0.5 * C1), q44(std::fmin(std::fmax(Z0, -lim), lim)),
+                                 q44(0.5 * Z1), (float)wsrc, (float)wpix, fl_out[i], 0};
         }
     }
 }
 
 }  // namespace
+
+// Column-major kernels unless some ray advances mostly along z or the
+// fixed-point lines could leave their int64 range.  A row's z slope is
+// c0 + vc2 c1h (Q.44) with vc2 = 2 v - (nv - 1), linear in v, so the first
+// and last rows bound |C|; the test uses the kernels' integer arithmetic.
+// Limits: every dimension at most 2^15 voxels (slab products below 2^59) and
+// the detector's z extent at the centre plane within 2^16 voxels.
+static bool cm_eligible(const ct_geometry_desc &d, const std::vector<ColFixed> &colq) {
+    if (d.nx > 32768 || d.ny > 32768 || d.nz > 32768) return false;
+    const long long one = 1LL << 44, m = (long long)std::max(d.nv - 1, 0);
+    for (const ColFixed &q : colq) {
+        const double cf = std::fabs((double)q.c0) + (double)m * std::fabs((double)q.c1h);
+        const double zf = (double)m * std::fabs((double)q.z1h);
+        if (cf > 2.0 * (double)one || zf > std::ldexp(1.0, 60)) return false;
+        const long long c_lo = q.c0 - m * q.c1h, c_hi = q.c0 + m * q.c1h;
+        if (std::llabs(c_lo) > one || std::llabs(c_hi) > one) return false;
+    }
+    return true;
+}
 
 extern "C" {
 
@@ -326,24 +355,31 @@ ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out) {
     view_constants(d, g->angles, vcs);
     std::vector<float4> cola, colb;
     std::vector<int> colf;
-    column_params(d, g->angles, cola, colb, colf);
+    std::vector<ColFixed> colq;
+    column_params(d, g->angles, cola, colb, colf, colq);
     g->d_cols = nullptr;
     const size_t ncol = cola.size();
+    // device layout: col_a, col_b (float4 each), col_q (ColFixed), col_flags
+    const size_t off_b = ncol * sizeof(float4), off_q = 2 * ncol * sizeof(float4);
+    const size_t off_f = off_q + ncol * sizeof(ColFixed);
     if (d.nviews > 0) {
         e = cudaMalloc(&g->d_views, sizeof(ViewConst) * vcs.size());
         if (e == cudaSuccess)
             e = cudaMemcpy(g->d_views, vcs.data(), sizeof(ViewConst) * vcs.size(),
                            cudaMemcpyHostToDevice);
         if (e == cudaSuccess && ncol > 0) {
-            e = cudaMalloc(&g->d_cols, ncol * (2 * sizeof(float4) + sizeof(int)));
+            e = cudaMalloc(&g->d_cols, off_f + ncol * sizeof(int));
             char *base = (char *)g->d_cols;
             if (e == cudaSuccess)
                 e = cudaMemcpy(base, cola.data(), ncol * sizeof(float4), cudaMemcpyHostToDevice);
             if (e == cudaSuccess)
-                e = cudaMemcpy(base + ncol * sizeof(float4), colb.data(), ncol * sizeof(float4),
+                e = cudaMemcpy(base + off_b, colb.data(), ncol * sizeof(float4),
                                cudaMemcpyHostToDevice);
             if (e == cudaSuccess)
-                e = cudaMemcpy(base + 2 * ncol * sizeof(float4), colf.data(), ncol * sizeof(int),
+                e = cudaMemcpy(base + off_q, colq.data(), ncol * sizeof(ColFixed),
+                               cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(base + off_f, colf.data(), ncol * sizeof(int),
                                cudaMemcpyHostToDevice);
         }
         if (e != cudaSuccess) {
@@ -354,10 +390,11 @@ ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out) {
         }
     }
     g->pg.views = g->d_views;
-    g->pg.col_a = g->d_cols ? (const float4 *)g->d_cols : nullptr;
-    g->pg.col_b = g->d_cols ? (const float4 *)((char *)g->d_cols + ncol * sizeof(float4)) : nullptr;
-    g->pg.col_flags =
-        g->d_cols ? (const int *)((char *)g->d_cols + 2 * ncol * sizeof(float4)) : nullptr;
+    char *cb = (char *)g->d_cols;
+    g->pg.col_a = cb ? (const float4 *)cb : nullptr;
+    g->pg.col_b = cb ? (const float4 *)(cb + off_b) : nullptr;
+    g->pg.col_q = cb ? (const ColFixed *)(cb + off_q) : nullptr;
+    g->pg.col_flags = cb ? (const int *)(cb + off_f) : nullptr;
     g->pg.nx = d.nx; g->pg.ny = d.ny; g->pg.nz = d.nz;
     g->pg.nu = d.nu; g->pg.nv = d.nv; g->pg.nviews = d.nviews;
     g->pg.hx = (float)d.vx; g->pg.hy = (float)d.vy; g->pg.hz = (float)d.vz;
@@ -365,23 +402,7 @@ ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out) {
     g->pg.sf_view = nullptr;
     g->pg.sf_ku = g->pg.sf_kv = g->pg.sf_cu = g->pg.sf_cv = g->pg.sf_oz = 0.f;
     g->d_sf = nullptr;
-    // Column-major kernels unless some ray advances mostly along z.  The
-    // kernels compute C = fmaf(vc, C1, C0) in FP32 with vc = v - (nv - 1) / 2
-    // exact; fmaf is correctly rounded, hence monotone in vc, so the largest
-    // |C| of a column is at its first or last row and the test below is the
-    // kernels' own, bit for bit.
-    g->pg.cm = 1;
-    if (d.nv > 0) {
-        const float vlo = -0.5f * (float)(d.nv - 1), vhi = 0.5f * (float)(d.nv - 1);
-        for (size_t i = 0; i < ncol; ++i) {
-            const float c0 = std::fmaf(vlo, cola[i].w, cola[i].z);
-            const float c1 = std::fmaf(vhi, cola[i].w, cola[i].z);
-            if (!(std::fabs(c0) <= 1.f && std::fabs(c1) <= 1.f)) {
-                g->pg.cm = 0;
-                break;
-            }
-        }
-    }
+    g->pg.cm = cm_eligible(d, colq) ? 1 : 0;
     set_launch_order(g->pg);
     set_row_pairing(g->pg, d.dv * d.sid / (d.sdd * d.vz));
     *out = g;

@@ -39,12 +39,29 @@ struct ColParams {
     float4 b;  // Z0, Z1, wsrc, wpix
 };
 
+// The same column lines for the column-major kernels in Q.44 fixed point
+// (value * 2^44, rounded to the nearest int64), which the walk turns into
+// exact integer lines (projector.cu).  A row v has vc2 = 2 v - (nv - 1) and
+//   C = (c0 + vc2 c1h) 2^-44,   Z0 + vc Z1 = (z0 + vc2 z1h) 2^-44,
+// so the per-row slope and offset are exact integer sums.  XI0 and Z0 are
+// clamped to +-2^16 voxels (such a ray misses every volume the column-major
+// kernels accept).
+struct __align__(16) ColFixed {
+    long long a, xi;     // A, XI0
+    long long c0, c1h;   // C0, C1 / 2
+    long long z0, z1h;   // Z0, Z1 / 2
+    float wsrc, wpix;    // as in ColParams (FP32)
+    int flags;           // bit 0: slab axis is x (else y); bit 1: walk reversed
+    int pad;
+};
+
 // Everything a projector kernel needs, passed by value.
 struct ProjGeom {
     const ViewConst *views;  // device array [nviews] (rays advancing along z)
     const float4 *col_a;     // device arrays [nviews * nu]: ColParams::a
     const float4 *col_b;     //                               ColParams::b
     const int *col_flags;    // bit 0: slab axis is x (else y); bit 1: walk reversed
+    const ColFixed *col_q;   // device array [nviews * nu]: column-major kernels
     int nx, ny, nz;
     int nu, nv, nviews;
     float hx, hy, hz;        // voxel pitch, mm

@@ -23,7 +23,11 @@ static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxPartials];
 
 // Device address of g_noalloc_partials per device ordinal.  In host code the
 // array's name is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, called once per device with that device current.
+// cudaGetSymbolAddress, called once per device with that device current.  The
+// cache lives as long as the process: a device reset (cudaDeviceReset, or
+// anything else that destroys the primary context) reloads the module, may
+// move the array and invalidates the cached address, together with every
+// geometry created on that device before the reset.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double *g_addr[kMaxDevices] = {};
@@ -67,7 +71,9 @@ extern "C" ct_status ct_project_norm2_noalloc(const ct_geometry *g, const float 
                          "ct_project_norm2_noalloc: geometry needs " + std::to_string(np) +
                              " CTAs of 32x8 rays, the static scratch holds " +
                              std::to_string(kNoAllocMaxPartials) +
-                             " (nviews * ceil(nu/32) * ceil(nv/8) must not exceed it)");
+                             " (CTAs = ceil(nu/32) * ceil(nv/8) * nviews rounded up to a "
+                             "multiple of the view group G = ceil(nviews / floor(65535 / "
+                             "ceil(nv/8))), G = 1 unless nviews * ceil(nv/8) > 65535)");
     double *part = nullptr;
     CT_TRY(scratch_address(g->device, &part));
     // every CTA overwrites its own partial, and the sum reads exactly those,

@@ -53,6 +53,12 @@ constexpr int kTU = 32;  // ray-major tile: detector columns per CTA (one warp r
 constexpr int kTV = 8;   // detector rows per CTA
 constexpr int kCU = 8;   // column-major tile: detector columns per CTA (one per warp)
 constexpr int kCV = 32;  // detector rows per CTA (one per lane)
+// Resident CTAs per SM the column-major forward kernels are compiled for
+// (32 registers a thread).  The gather waits on L1/L2 hits, so warps in
+// flight pay more than the registers they give up: measured on the 256^3
+// workload, 5 CTAs/SM (48 registers) 11.1 ms, 6 (40) 10.2 ms, 7 (32) 10.0 ms.
+// The backprojection is bound by instruction issue and keeps 5 (48).
+constexpr int kFwdCtas = 7;
 // Launch order (set_launch_order): views visited together by A and by A^T
 // (ray-major A^T: kWideGroupBack) when the volume and its transposed copy take
 // more than kL2GroupBytes.
@@ -488,6 +494,27 @@ __global__ void __launch_bounds__(kTU *kTV) k_forward_direct(ProjGeom g,
 // and no per-lane lateral state.  Rays advancing mostly along z (|C| > 1) do
 // not fit this scheme; geometries that have any use the ray-major kernels
 // above instead (ProjGeom::cm).
+//
+// Fixed-point walk.  A column's lateral line and a row's z line (ColFixed,
+// Q.44 values of the host's FP64 parameters) become integer lines in Q.32,
+// anchored at the start of the volume's first slab along the walk:
+//   X(k) = X(0) +- k dX,   dX = round(|A| 2^32)   (k: slab index of the walk)
+// and likewise Z(k) with dZ = round(|C| 2^32).  The integer part of X is the
+// lateral voxel index (centred), the fraction the position inside it.  The
+// walk keeps phi = the distance from X(k) to the next plane in the direction
+// of travel, mod 2^32, and subtracts dX once per slab: the slab crosses that
+// plane iff phi < dX (the borrow is the crossing), at the fraction phi / dX
+// of the slab, and the wrap-around leaves phi at the distance to the plane
+// after.  Integer steps are exact, so no rounding accumulates along the ray:
+// a crossing is off by at most 2^-33 voxel per slab walked (the rounding of
+// dX) plus the 2^-23 of the fraction's conversion to float, both in units of
+// a voxel relative to the slab.  (Crossings computed in FP32 relative to the
+// volume centre carry 2^-24 |w| instead: 1.5e-5 voxel at 256 voxels from the
+// centre, which a backprojected voxel, a sum of segments of unrelated rays,
+// does not average away.)  Segment lengths are therefore fractions of one
+// slab in [0, 1], multiplied by the mm-per-slab factor lsig of the ray.
+// A line exactly in a grid plane with zero slope (dX = 0) is credited to the
+// voxel above it, as the midpoint rule does.
 
 // Tile (bx, by, bz) of the projector grid (blockIdx in a plain launch; a
 // batched launch maps its work items onto each job's grid).
@@ -502,28 +529,57 @@ __device__ __forceinline__ void tile_of_cm(const ProjGeom &g, uint3 bid, int &u,
 
 // One warp's column (the same in all lanes) and one lane's row of it.
 struct CmRay {
-    float lo = 0.f, hi = 0.f;        // w range of the column inside the volume's xy extent
-    float A = 0.f, xi0 = 0.f, invA = 0.f;
-    int Ns = 0, Na = 0, Nb = 0, cs = 0, ca = 0, cb = 0;
+    long long X0 = 0, Z0 = 0;        // lateral and z lines at slab 0, Q.32, centred
+    unsigned dX = 0, dZ = 0;         // |slope| per slab, Q0.32
+    bool x_up = false, z_up = false; // the line runs towards higher indices
+    float kx = 0.f, kz = 0.f;        // 1 / |A|, 1 / |C| (slabs per unit of the axis)
+    int Ns = 0, Na = 0, Nb = 0, ca = 0, cb = 0;
     int sstride = 0, astride = 0;    // [y][x][z] strides of the slab and lateral axes
     bool rev = false;                // walk runs towards decreasing slab index
-    float C = 0.f, ze0 = 0.f, invC = 0.f;
-    float w_in = 0.f, w_out = 0.f;   // w range of this lane's ray inside the volume
-    int k_first = INT_MAX, k_last = -1;
-    float lsig = 0.f;                // mm of ray per unit w
+    float ksrc = 0.f, kpix = 0.f;    // slab coordinate of the source and of the pixel
+    int k_lo = INT_MAX, k_hi = -1;   // slabs that may hold a part of the ray
+    int k_in0 = INT_MIN, k_in1 = INT_MAX;  // slabs wholly inside the volume
+    float lsig = 0.f;                // mm of ray per slab
 };
 
+// Slab coordinate at which the Q.32 line X(k) = X0 + k s reaches the integer
+// plane P (s: signed slope per slab, in units of 2^-32).
+__device__ __forceinline__ float plane_k(int P, long long X0, float s) {
+    return __ll2float_rn(((long long)P << 32) - X0) / s;
+}
+
+// 1 + q 2^-32 truncated to a float in [1, 2): the exponent bits of 1.0f
+// (0x7f << 23) funnel-shifted in above the top 23 bits of q.
+__device__ __forceinline__ float one_plus_frac(unsigned q) {
+    return __uint_as_float(__funnelshift_r(q, 0x7fu, 9));
+}
+
+// A load the compiler may not merge with an earlier load of the same address
+// (so that values re-derived from it need no register in between).
+__device__ __forceinline__ float4 ld_volatile_f4(const float4 *p) {
+    float4 v;
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+
 // Set up ray (u, v) of a column-major warp; returns whether it crosses the
-// volume.  col_live (u and view in range) must be warp-uniform.  The clip is
-// the one of ray_clip, so a ray's w range is the same as in the ray-major
-// kernels.
+// volume.  col_live (u and view in range) must be warp-uniform.
+//
+// The slab range comes from the same integer lines the walk steps along: the
+// face crossings are computed in FP32 from exact integer distances (relative
+// error below 2^-22), and widened by a margin of 2^-16 (|k| + 1) slab, so
+// that [k_lo, k_hi] holds every slab with a part of the ray inside and
+// [k_in0, k_in1] only slabs whose every segment lies inside (their voxel
+// indices need no check).
 __device__ __forceinline__ bool cm_setup(const ProjGeom &g, int view, int u, int v, bool col_live,
                                          CmRay &r) {
     if (!col_live) return false;
-    const size_t ci = (size_t)view * g.nu + u;
-    const float4 pa = __ldg(g.col_a + ci);
-    const float4 pb = __ldg(g.col_b + ci);
-    const int fl = __ldg(g.col_flags + ci);
+    const longlong2 *q = reinterpret_cast<const longlong2 *>(g.col_q + ((size_t)view * g.nu + u));
+    const longlong2 qa = __ldg(q), qc = __ldg(q + 1), qz = __ldg(q + 2);
+    const float4 qw = __ldg(reinterpret_cast<const float4 *>(q + 3));
+    const int fl = __float_as_int(qw.z);
     float hs, ha;
     if (fl & 1) {      // slabs along x, lateral y
         r.Ns = g.nx; r.Na = g.ny; r.sstride = g.nz; r.astride = g.nx * g.nz; hs = g.hx; ha = g.hy;
@@ -532,141 +588,199 @@ __device__ __forceinline__ bool cm_setup(const ProjGeom &g, int view, int u, int
     }
     r.Nb = g.nz;
     r.rev = (fl & 2) != 0;
-    r.cs = r.Ns / 2;
+    const int cs = r.Ns / 2;
     r.ca = r.Na / 2;
     r.cb = r.Nb / 2;
-    r.A = pa.x;
-    r.xi0 = pa.y;
-    r.invA = 1.f / r.A;
-    bool ok = true;
-    float lo = fmaxf((float)(-r.cs), pb.z), hi = fminf((float)(r.Ns - r.cs), pb.w);
-    if (r.A != 0.f) {
-        const float t0 = ((float)(-r.ca) - r.xi0) * r.invA;
-        const float t1 = ((float)(r.Na - r.ca) - r.xi0) * r.invA;
-        lo = fmaxf(lo, fminf(t0, t1));
-        hi = fminf(hi, fmaxf(t0, t1));
-    } else if (!(r.xi0 >= (float)(-r.ca) && r.xi0 < (float)(r.Na - r.ca))) {
-        ok = false;
+    const long long vc2 = 2LL * v - (g.nv - 1);
+    const long long a = qa.x, xi = qa.y;
+    const long long c = qc.x + vc2 * qc.y, z = qz.x + vc2 * qz.y;
+    r.dX = (unsigned)min(((unsigned long long)llabs(a) + 2048ull) >> 12, 0xffffffffull);
+    r.dZ = (unsigned)min(((unsigned long long)llabs(c) + 2048ull) >> 12, 0xffffffffull);
+    r.x_up = a > 0 && r.dX != 0u;
+    r.z_up = c > 0 && r.dZ != 0u;
+    r.X0 = (xi - a * cs) >> 12;   // Q.44 -> Q.32 (floor)
+    r.Z0 = (z - c * cs) >> 12;
+    const float af = (float)r.dX * 0x1p-32f, cf = (float)r.dZ * 0x1p-32f;
+    r.kx = 1.f / af;
+    r.kz = 1.f / cf;
+    r.ksrc = qw.x + (float)cs;
+    r.kpix = qw.y + (float)cs;
+    float e = fmaxf(0.f, r.ksrc), x = fminf((float)r.Ns, r.kpix);
+    bool ok = v < g.nv;
+    if (r.dX != 0u) {
+        const float s = r.x_up ? (float)r.dX : -(float)r.dX;
+        const float t0 = plane_k(-r.ca, r.X0, s), t1 = plane_k(r.Na - r.ca, r.X0, s);
+        e = fmaxf(e, fminf(t0, t1));
+        x = fminf(x, fmaxf(t0, t1));
+    } else {
+        ok = ok && r.X0 >= ((long long)(-r.ca) << 32) && r.X0 < ((long long)(r.Na - r.ca) << 32);
     }
-    r.lo = lo;
-    r.hi = hi;
-    const float vc = (float)v - 0.5f * (float)(g.nv - 1);
-    r.C = fmaf(vc, pa.w, pa.z);
-    r.ze0 = fmaf(vc, pb.y, pb.x);
-    r.invC = 1.f / r.C;
-    ok = ok && (v < g.nv) && fabsf(r.C) <= 1.f;
-    float w_in = lo, w_out = hi;
-    if (r.C != 0.f) {
-        const float t0 = ((float)(-r.cb) - r.ze0) * r.invC;
-        const float t1 = ((float)(r.Nb - r.cb) - r.ze0) * r.invC;
-        w_in = fmaxf(w_in, fminf(t0, t1));
-        w_out = fminf(w_out, fmaxf(t0, t1));
-    } else if (!(r.ze0 >= (float)(-r.cb) && r.ze0 < (float)(r.Nb - r.cb))) {
-        ok = false;
+    if (r.dZ != 0u) {
+        const float s = r.z_up ? (float)r.dZ : -(float)r.dZ;
+        const float t0 = plane_k(-r.cb, r.Z0, s), t1 = plane_k(r.Nb - r.cb, r.Z0, s);
+        e = fmaxf(e, fminf(t0, t1));
+        x = fminf(x, fmaxf(t0, t1));
+    } else {
+        ok = ok && r.Z0 >= ((long long)(-r.cb) << 32) && r.Z0 < ((long long)(r.Nb - r.cb) << 32);
     }
-    ok = ok && (w_in < w_out);
-    r.k_first = max(0, (int)floorf(w_in) + r.cs);
-    r.k_last = min(r.Ns - 1, (int)ceilf(w_out) - 1 + r.cs);
-    ok = ok && (r.k_first <= r.k_last);
-    r.w_in = ok ? w_in : 0.f;   // an empty range clips every length to zero
-    r.w_out = ok ? w_out : 0.f;
-    const float la = r.A * (ha / hs), lb = r.C * (g.hz / hs);
+    ok = ok && e < x;
+    e = fminf(fmaxf(e, -2.f), (float)r.Ns + 2.f);
+    x = fminf(fmaxf(x, -2.f), (float)r.Ns + 2.f);
+    const float de = fmaf(fabsf(e), 0x1p-16f, 0x1p-16f), dx = fmaf(fabsf(x), 0x1p-16f, 0x1p-16f);
+    r.k_lo = max(0, (int)floorf(e - de));
+    r.k_hi = min(r.Ns - 1, (int)floorf(x + dx));
+    r.k_in0 = (int)ceilf(e + de);
+    r.k_in1 = (int)floorf(x - dx) - 1;
+    ok = ok && r.k_lo <= r.k_hi;
+    const float la = af * (ha / hs), lb = cf * (g.hz / hs);
     r.lsig = hs * sqrtf(fmaf(la, la, fmaf(lb, lb, 1.f)));
     return ok;
 }
 
-// Column-major slab walk; fn(offset, w_length, p) with the contract of
-// walk().  Must be called by all 32 lanes of the warp, which hold rows of one
-// column.
+// Column-major slab walk; fn(offset, length in slabs, p) is called for the
+// segments of each slab, and may touch memory only where p is set (the
+// offset is then inside the volume).  Must be called by all 32 lanes of the
+// warp, which hold rows of one column; ci = view * nu + u is the column.
 //
-// The slab bounds and the lateral crossing come from warp-uniform values, so
-// they are equal in all lanes.  Per lane a slab holds the current voxel, the
-// voxel after the lane's z crossing (if it crosses) and, when the column
-// crosses a lateral plane, one more.  In the entry and exit slabs (and in
-// every slab of a warp where some lane has no ray) each length is clipped to
-// the lane's own range and a voxel is touched only if its clipped length is
-// positive: outside its range a lane's z index may leave the volume.  The
-// interior slabs, inside every lane's range, skip the clip.
-template <class Fn>
-__device__ __forceinline__ void walk_cm(const CmRay &r, bool ok, Fn &&fn) {
-    const unsigned full = 0xffffffffu;
-    const int kb = __reduce_min_sync(full, ok ? r.k_first : INT_MAX);
-    const int ke = __reduce_max_sync(full, ok ? r.k_last : -1);
-    if (kb > ke) return;
-    int k_mid0 = __reduce_max_sync(full, ok ? r.k_first : INT_MAX) + 1;
-    int k_mid1 = __reduce_min_sync(full, ok ? r.k_last : -1) - 1;
-    if (!__all_sync(full, ok) || k_mid0 > k_mid1) {
-        k_mid0 = ke + 1;
-        k_mid1 = ke;
-    }
-    const float lo = r.lo, hi = r.hi, w_in = r.w_in, w_out = r.w_out;
-    // lateral state at the start of the warp's first slab (uniform)
-    const float w_s = fminf(fmaxf((float)(kb - r.cs), lo), hi);
-    const float fi = fminf(fmaxf(floorf(fmaf(w_s, r.A, r.xi0)), (float)(-r.ca)),
-                           (float)(r.Na - 1 - r.ca));
-    const bool neg_a = r.A < 0.f;
-    const float sa = neg_a ? -1.f : 1.f;
-    const int astep = neg_a ? -r.astride : r.astride;
-    const float xi0 = r.xi0, invA = r.invA;
-    float px = neg_a ? fi : fi + 1.f;
-    float w_nx = (r.A != 0.f) ? (px - xi0) * invA : INFINITY;
-    const int sstep = r.rev ? -r.sstride : r.sstride;
-    int off = (r.rev ? (r.Ns - 1) * r.sstride : 0) + kb * sstep + ((int)fi + r.ca) * r.astride;
-    // this lane's z state; before its entry the index is clamped into the
-    // volume, and the next plane in the direction of travel then lies after
-    // the entry point
-    const float fk = fminf(fmaxf(floorf(fmaf(w_s, r.C, r.ze0)), (float)(-r.cb)),
-                           (float)(r.Nb - 1 - r.cb));
-    const bool neg_b = r.C < 0.f;
-    const float sb = neg_b ? -1.f : 1.f;
-    const int dz = neg_b ? -1 : 1;
-    const float ze0 = r.ze0, invC = r.invC;
-    float pz = neg_b ? fk : fk + 1.f;
-    float w_nz = (ok && r.C != 0.f) ? (pz - ze0) * invC : INFINITY;
-    int zo = ok ? (int)fk + r.cb : 0;
-    float wk = (float)(kb - r.cs);
-    float w_lo = w_s;
-    auto slab = [&](auto clamp) {
-        constexpr bool CL = decltype(clamp)::value;
-        wk += 1.f;
-        const float w_hi = CL ? fminf(fmaxf(wk, lo), hi) : wk;
-        const bool cz = w_nz < w_hi;
-        const float sz = fminf(w_nz, w_hi);
-        // clipped length of [a, b]
-        auto len = [&](float a, float b) {
-            return CL ? fminf(fmaxf(b, w_in), w_out) - fminf(fmaxf(a, w_in), w_out) : b - a;
-        };
-        const int o = off + zo;
-        if (!(w_nx < w_hi)) {   // no lateral crossing (warp-uniform)
-            const float l1 = len(w_lo, sz), l2 = len(sz, w_hi);
-            fn(o, l1, CL ? l1 > 0.f : true);
-            fn(o + dz, l2, CL ? l2 > 0.f : cz);
-        } else {
-            const float sx = w_nx;
-            const float s1 = fminf(sx, sz), s2 = fmaxf(sx, sz);
-            const float l1 = len(w_lo, s1), l2 = len(s1, s2), l3 = len(s2, w_hi);
-            fn(o, l1, CL ? l1 > 0.f : true);
-            fn(o + (sx <= sz ? astep : dz), l2, CL ? l2 > 0.f : true);
-            fn(o + astep + (cz ? dz : 0), l3, CL ? l3 > 0.f : cz);
-            off += astep;
-            px += sa;
-            w_nx = (px - xi0) * invA;
+// The warp walks the slabs any of its rays may touch.  Slabs that lie wholly
+// inside the volume for every ray of the warp (the interior, nearly all of a
+// ray) need no index checks: a slab holds the lane's current voxel, the next
+// one along z where the lane crosses a z plane, and, where the column crosses
+// a lateral plane, one more.  In the other slabs each segment is checked
+// against the volume's index ranges and clipped to the source..pixel part of
+// the ray.  A lane without a ray (ok false) keeps offset 0 with zero steps,
+// so it may touch voxel 0 but nothing else; its segments must be discarded
+// by fn (a zero weight, or a sum that is dropped).  Offsets are unsigned:
+// outside the volume they may wrap, and they are exact again whenever the
+// indices are in range.
+//
+// Everything the exit slabs need beyond the loop state is re-derived after
+// the interior from the column's parameters, so that it holds no registers
+// during the loop (the forward kernel runs at 32 registers a thread).
+template <int DZ, class Fn>
+__device__ __forceinline__ void walk_cm_dir(const ProjGeom &g, int ci, const CmRay &r, bool ok,
+                                            int kb, int ke, int k_mid0, int k_mid1, Fn &&fn) {
+    // state of both lines at the start of slab kb
+    const long long X = r.X0 + (r.x_up ? (long long)kb * r.dX : -(long long)kb * r.dX);
+    const long long Z = r.Z0 + (r.z_up ? (long long)kb * r.dZ : -(long long)kb * r.dZ);
+    int ai = (int)((r.x_up ? X - 1 : X) >> 32) + r.ca;   // voxel indices (may lie outside)
+    int zi = (int)((r.z_up ? Z - 1 : Z) >> 32) + r.cb;
+    unsigned phi = r.x_up ? (unsigned)(-X) : (unsigned)X;
+    unsigned psi = r.z_up ? (unsigned)(-Z) : (unsigned)Z;
+    // a lane without a ray never crosses a z plane (dZ = 0), so with a
+    // compile-time direction DZ its z neighbour is never touched either
+    const unsigned dX = r.dX, dZ = ok ? r.dZ : 0u;
+    const float kx = r.kx, kz = r.kz;
+    const unsigned sstep = !ok ? 0u : r.rev ? 0u - (unsigned)r.sstride : (unsigned)r.sstride;
+    const unsigned astep = !ok ? 0u : r.x_up ? (unsigned)r.astride : 0u - (unsigned)r.astride;
+    const unsigned dzu = DZ != 0 ? (unsigned)DZ : !ok ? 0u : r.z_up ? 1u : 0xffffffffu;
+    unsigned o = !ok ? 0u
+                     : (r.rev ? (unsigned)(r.Ns - 1) * (unsigned)r.sstride : 0u) +
+                           (unsigned)kb * sstep + (unsigned)ai * (unsigned)r.astride +
+                           (unsigned)zi;
+    // column constants of the entry and exit slabs (re-derived for the exit)
+    int Na = r.Na, astride = r.astride;
+    unsigned obase = r.rev ? (unsigned)(r.Ns - 1) * (unsigned)r.sstride : 0u;
+    float ksrc = r.ksrc, kpix = r.kpix;
+    auto clamped = [&](int k) {
+        const int da = (int)astep > 0 ? 1 : -1, dz = (int)dzu;
+        const bool cx = phi < dX, cz = psi < dZ;
+        const float sx = cx ? fmaf(one_plus_frac(phi), kx, -kx) : 1.f;
+        const float sz = cz ? fmaf(one_plus_frac(psi), kz, -kz) : 1.f;
+        const float s1 = fminf(sx, sz), s2 = fmaxf(sx, sz);
+        const float kf = (float)k;
+        const float c_lo = fminf(fmaxf(ksrc - kf, 0.f), 1.f);
+        const float c_hi = fminf(fmaxf(kpix - kf, 0.f), 1.f);
+        const float b1 = fminf(fmaxf(s1, c_lo), c_hi), b2 = fminf(fmaxf(s2, c_lo), c_hi);
+        const float l1 = b1 - c_lo, l2 = b2 - b1, l3 = c_hi - b2;
+        const bool a0 = (unsigned)ai < (unsigned)Na, a1 = (unsigned)(ai + da) < (unsigned)Na;
+        const bool z0 = (unsigned)zi < (unsigned)g.nz, z1 = (unsigned)(zi + dz) < (unsigned)g.nz;
+        const bool mx = sx <= sz;   // the middle segment is past the lateral crossing
+        fn((int)o, l1, a0 && z0 && l1 > 0.f);
+        fn((int)(o + (mx ? astep : dzu)), l2, (mx ? (a1 && z0) : (a0 && z1)) && l2 > 0.f);
+        fn((int)(o + (cx ? astep : 0u) + (cz ? dzu : 0u)), l3,
+           (cx ? a1 : a0) && (cz ? z1 : z0) && l3 > 0.f);
+        phi -= dX;
+        psi -= dZ;
+        if (cx) {
+            ai += da;
+            o += astep;
         }
         if (cz) {
-            zo += dz;
-            pz += sb;
-            w_nz = (pz - ze0) * invC;
+            zi += dz;
+            o += dzu;
         }
-        off += sstep;
-        w_lo = w_hi;
+        o += sstep;
     };
-    using clamped = std::integral_constant<bool, true>;
-    using interior = std::integral_constant<bool, false>;
+    // In the interior every offset handed to fn is in range or unused, so
+    // they are formed as int sums: the z neighbour (o + dz) is then a
+    // constant displacement of o's address when DZ is fixed.
+    const int dzi = DZ != 0 ? DZ : (int)dzu, ast = (int)astep;
+    auto interior = [&]() {
+        const bool cz = psi < dZ;
+        const float sz = cz ? fmaf(one_plus_frac(psi), kz, -kz) : 1.f;
+        psi -= dZ;
+        const int oi = (int)o;
+        if (phi >= dX) {   // no lateral crossing (warp-uniform)
+            fn(oi, sz, true);
+            fn(oi + dzi, 1.f - sz, cz);
+        } else {
+            const float sx = fmaf(one_plus_frac(phi), kx, -kx);
+            const float s1 = fminf(sx, sz), s2 = fmaxf(sx, sz);
+            fn(oi, s1, true);
+            fn(sx <= sz ? oi + ast : oi + dzi, s2 - s1, true);
+            fn(oi + ast + (cz ? dzi : 0), 1.f - s2, cz);
+            o += astep;
+        }
+        phi -= dX;
+        o += sstep + (cz ? dzu : 0u);
+    };
     int k = kb;
-    for (; k < k_mid0; ++k) slab(clamped{});
-#pragma unroll 8
-    for (; k <= k_mid1; ++k) slab(interior{});
-    for (; k <= ke; ++k) slab(clamped{});
+    const int k_entry_end = min(k_mid0, ke + 1);
+    for (; k < k_entry_end; ++k) clamped(k);
+    if (k <= k_mid1) {
+#pragma unroll 4
+        for (; k <= k_mid1; ++k) interior();
+        if (k > ke) return;
+        // Re-derive the column constants from its parameters (a fresh load,
+        // so they need not stay in registers through the loop), then the
+        // indices from the offset: the interior tracks them only there, and
+        // ends with them in range (meaningless in a lane without a ray).
+        const float4 qw = ld_volatile_f4(reinterpret_cast<const float4 *>(g.col_q + ci) + 3);
+        const int fl = __float_as_int(qw.z);
+        const int Ns = (fl & 1) ? g.nx : g.ny, cs = Ns / 2;
+        const int sstride = (fl & 1) ? g.nz : g.nx * g.nz;
+        Na = (fl & 1) ? g.ny : g.nx;
+        astride = (fl & 1) ? g.nx * g.nz : g.nz;
+        obase = (fl & 2) ? (unsigned)(Ns - 1) * (unsigned)sstride : 0u;
+        ksrc = qw.x + (float)cs;
+        kpix = qw.y + (float)cs;
+        const unsigned rem = o - obase - (unsigned)k * sstep;
+        ai = (int)(rem / (unsigned)astride);
+        zi = (int)(rem - (unsigned)ai * (unsigned)astride);
+    }
+    for (; k <= ke; ++k) clamped(k);
+}
+
+// The walk with the z direction fixed at compile time where all lanes of
+// the warp that hold a ray move the same way along z (every warp but the one
+// holding the column's horizontal row): the z neighbour of a voxel is then a
+// constant offset from its address.
+template <class Fn>
+__device__ __forceinline__ void walk_cm(const ProjGeom &g, int ci, const CmRay &r, bool ok,
+                                        Fn &&fn) {
+    const unsigned full = 0xffffffffu;
+    const int kb = __reduce_min_sync(full, ok ? r.k_lo : INT_MAX);
+    const int ke = __reduce_max_sync(full, ok ? r.k_hi : -1);
+    if (kb > ke) return;
+    const int k_mid0 = max(kb, __reduce_max_sync(full, ok ? r.k_in0 : INT_MIN));
+    const int k_mid1 = min(ke, __reduce_min_sync(full, ok ? r.k_in1 : INT_MAX));
+    if (__all_sync(full, !ok || r.z_up))
+        walk_cm_dir<1>(g, ci, r, ok, kb, ke, k_mid0, k_mid1, fn);
+    else if (__all_sync(full, !ok || !r.z_up))
+        walk_cm_dir<-1>(g, ci, r, ok, kb, ke, k_mid0, k_mid1, fn);
+    else
+        walk_cm_dir<0>(g, ci, r, ok, kb, ke, k_mid0, k_mid1, fn);
 }
 
 // One tile of p = alpha * rho o (A vol) + beta * p from the [y][x][z] copy
@@ -685,7 +799,7 @@ __device__ __forceinline__ void forward_cm_tile(const ProjGeom &g, uint3 bid, ui
     const bool ok = cm_setup(g, view, u, v, col_live, r);
     float acc = 0.f;
     if (col_live) {
-        walk_cm(r, ok, [&](int o, float l, bool p) {
+        walk_cm(g, view * g.nu + u, r, ok, [&](int o, float l, bool p) {
             float val = 0.f;
             if (p) val = UNIT_VOL ? 1.f : ld_f(vol_z + o);
             acc = fmaf(l, val, acc);
@@ -715,7 +829,7 @@ __device__ __forceinline__ void forward_cm_tile(const ProjGeom &g, uint3 bid, ui
 }
 
 template <bool HAS_RHO, bool NORM, bool UNIT_VOL, class TV = float, class TS = float>
-__global__ void __launch_bounds__(kCU *kCV, 5) k_forward_cm(ProjGeom g,
+__global__ void __launch_bounds__(kCU *kCV, kFwdCtas) k_forward_cm(ProjGeom g,
                                                          const TV *__restrict__ vol_z,
                                                          TS *__restrict__ out,
                                                          const float *__restrict__ rho, Coef c,
@@ -766,14 +880,14 @@ __device__ __forceinline__ void backward_cm_tile(const ProjGeom &g, uint3 bid,
     if constexpr (DET) {
         const float scale = __ldg(det_scale);
         unsigned long long *base = static_cast<unsigned long long *>(acc_z);
-        walk_cm(r, ok, [&](int o, float l, bool p) {
+        walk_cm(g, view * g.nu + u, r, ok, [&](int o, float l, bool p) {
             const float lm = l * ls;
             const float val = POWER == 1 ? w * l : w * lm * lm;
             red_add_u64_if(base + o, __float2ll_rn(val * scale), p && nz);
         });
     } else {
         float *base = static_cast<float *>(acc_z);
-        walk_cm(r, ok, [&](int o, float l, bool p) {
+        walk_cm(g, view * g.nu + u, r, ok, [&](int o, float l, bool p) {
             const float lm = l * ls;
             red_add_if(base + o, POWER == 1 ? w * l : w * lm * lm, p && nz);
         });
@@ -822,7 +936,7 @@ __device__ __forceinline__ const BatchJob &job_of(const BatchJob *__restrict__ j
 }
 
 template <bool NORM>
-__global__ void __launch_bounds__(kCU *kCV, 5) k_forward_cm_batch(
+__global__ void __launch_bounds__(kCU *kCV, kFwdCtas) k_forward_cm_batch(
     const BatchJob *__restrict__ jobs, int njobs, unsigned ntiles, unsigned *__restrict__ next) {
     __shared__ double sh[32];
     __shared__ unsigned slot;

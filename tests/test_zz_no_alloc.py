@@ -70,6 +70,28 @@ def test_noalloc_matches_allocating_entry_point_twice(ct, projector):
         assert float(n_new) == pytest.approx(float((s_new.double() ** 2).sum()), rel=1e-12)
 
 
+def test_noalloc_grouped_views(ct):
+    """nviews * ceil(nv/8) > 65535: the direct launch groups 2 views per grid
+    slot (40001 views, 16 rows: G = ceil(40001 / 32767) = 2), and the last
+    group is half empty.  Its idle CTAs must still write zero partials."""
+    L = ct.lib()
+    cfg = dict(nx=6, ny=5, nz=4, vx=1.0, vy=1.0, vz=1.0, nu=20, nv=16, du=0.7, dv=0.7,
+               sid=40.0, sdd=70.0, nviews=40001)
+    g = ct.Geometry(**cfg)
+    for seed, alpha, beta in [(31, 1.0, 0.0), (32, 2.0, -1.0)]:
+        vol = torch.from_numpy(synth.random_field(g.vol_shape, seed=seed)).cuda()
+        start = torch.from_numpy(synth.random_field(g.sino_shape, seed=seed + 100)).cuda()
+        s_ref, s_new = start.clone(), start.clone()
+        n_ref = torch.zeros((), dtype=torch.float64, device="cuda")
+        n_new = torch.full((), float("nan"), dtype=torch.float64, device="cuda")
+        _call(L, "ct_project_norm2", g, vol, s_ref, alpha, beta, n_ref)
+        _call(L, "ct_project_norm2_noalloc", g, vol, s_new, alpha, beta, n_new)
+        torch.cuda.synchronize()
+        assert rel(s_new, s_ref) < TOL
+        assert abs(float(n_new) - float(n_ref)) <= TOL * float(n_ref)
+        assert float(n_new) == pytest.approx(float((s_new.double() ** 2).sum()), rel=1e-12)
+
+
 def test_noalloc_rejects_geometry_beyond_static_scratch(ct):
     L = ct.lib()
     # 8 * 8 * 4097 = 262 208 CTAs of 32 x 8 rays > 262 144 partial sums
@@ -82,4 +104,5 @@ def test_noalloc_rejects_geometry_beyond_static_scratch(ct):
     st = L.ct_project_norm2_noalloc(g.handle, _p(vol), _p(sino), ctypes.c_float(1.0),
                                     ctypes.c_float(0.0), _p(nrm), stream)
     assert st == 1
-    assert b"static scratch" in L.ct_last_error()
+    msg = L.ct_last_error()
+    assert b"static scratch" in msg and b"262208" in msg
