@@ -63,6 +63,9 @@ def parse():
                     help="ops mode only: 256^3 (default) or the 512^3, 720-view workload")
     ap.add_argument("--projector", default="siddon", choices=["siddon", "sf_tr", "sf_tt"],
                     help="ops mode only: Siddon rays or separable footprints (TR, TT)")
+    ap.add_argument("--views", type=int, default=0,
+                    help="ops mode only: use this many of the workload's views, evenly spread "
+                         "(a smaller case of the same kernels for profiling)")
     ap.add_argument("--cpu-sample-views", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -397,41 +400,54 @@ def run_ours(a):
 
 
 def run_ops(a):
-    """A and A^T alone on the 256^3 workload: W warm-up pairs, then K timed
-    pairs, each launch bracketed by CUDA events on the current stream."""
+    """A and A^T alone on the 256^3 (or 512^3) workload: W warm-up pairs, then
+    K timed pairs, each launch bracketed by CUDA events on the current stream.
+    A projects the phantom; A^T backprojects a dense seeded residual (like
+    CGLS's, every ray nonzero).  --views V keeps V evenly spread views."""
     import torch
 
     import paper_2110_13526_gb300 as ct
     import synth
 
     torch.cuda.set_device(0)
-    cfg, g, x_true, b = make_problem(ct, torch, synth, torch.device("cuda", 0), a.workload,
-                                     a.projector)
+    dev = torch.device("cuda", 0)
+    cfg = dict(synth.CONFIGS[a.workload])
+    if a.views:
+        import math
+        cfg["angles"] = [2.0 * math.pi * k / a.views for k in range(a.views)]
+        cfg["nviews"] = a.views
+    g = ct.Geometry(**cfg, projector=a.projector)
+    lo, hi = synth.box_of(cfg)
+    x_true = torch.from_numpy(synth.voxelize(synth.random_ellipsoids(
+        40, PHANTOM_SEED[a.workload], lo, hi), cfg)).to(dev)
+    e = torch.from_numpy(synth.random_field(g.sino_shape, seed=7)).to(dev)
     nnz = ct.count_nnz(g)
     r = torch.empty(g.vol_shape, device="cuda")
     p = torch.empty(g.sino_shape, device="cuda")
     for _ in range(a.warmup):
         ct.project(g, x_true, out=p)
-        ct.backproject(g, b, out=r)
+        ct.backproject(g, e, out=r)
     stream = torch.cuda.current_stream()
     tf, tb = [], []
     for _ in range(a.steps):
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        e[0].record(stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
         ct.project(g, x_true, out=p)
-        e[1].record(stream)
-        ct.backproject(g, b, out=r)
-        e[2].record(stream)
+        ev[1].record(stream)
+        ct.backproject(g, e, out=r)
+        ev[2].record(stream)
         torch.cuda.synchronize()
-        tf.append(e[0].elapsed_time(e[1]))
-        tb.append(e[1].elapsed_time(e[2]))
+        tf.append(ev[0].elapsed_time(ev[1]))
+        tb.append(ev[1].elapsed_time(ev[2]))
     mf, mb = statistics.median(tf), statistics.median(tb)
     print(json.dumps({"mode": "ops", "config": {"workload": a.workload, "nnz": nnz,
+                                                "views": cfg["nviews"],
                                                 "projector": a.projector},
                       "ms_project": mf, "ms_backproject": mb,
                       "gray_voxel_per_s": {"A": nnz / mf / 1e6, "AT": nnz / mb / 1e6},
                       "note": "ct_project / ct_backproject calls, including the transpose "
-                              "and combine kernels around the projector kernel"}))
+                              "and combine kernels around the projector kernel; A^T of a "
+                              "dense residual"}))
     return 0
 
 
