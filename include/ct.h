@@ -145,6 +145,27 @@ ct_status ct_project(const ct_geometry *g, const float *d_vol, float *d_sino, fl
 ct_status ct_backproject(const ct_geometry *g, const float *d_sino, float *d_vol, float alpha,
                          float beta, void *stream);
 
+/* ct_project applied to each item of a batch of volumes of one geometry
+ * (Eq. 1, item by item): for i < nbatch,
+ *   d_sinos[i m ..] = alpha * (A d_vols[i n ..]) + beta * d_sinos[i m ..],
+ * with n = nx ny nz and m = nviews nv nu; both arrays hold nbatch contiguous
+ * items (device pointers, caller-owned).  For a column-major Siddon
+ * geometry the projector is one launch over all items, each item's result
+ * bitwise that of ct_project; otherwise the items run one after another.
+ * Uses a stream-ordered workspace of nbatch * n floats.  nbatch == 0 does
+ * nothing; nbatch < 0 or a NULL vector gives CT_ERR_INVALID_ARG. */
+ct_status ct_project_batch(const ct_geometry *g, const float *d_vols, float *d_sinos,
+                           int32_t nbatch, float alpha, float beta, void *stream);
+
+/* ct_backproject applied to each item of a batch of sinograms (Algorithm 1
+ * step r_x = A^T e_b, item by item), in the same layout:
+ *   d_vols[i n ..] = alpha * (A^T d_sinos[i m ..]) + beta * d_vols[i n ..].
+ * One projector launch over all items for a column-major Siddon geometry
+ * with float accumulation (results as ct_backproject's, up to the order of
+ * the float atomics); item by item otherwise.  Workspace nbatch * n floats. */
+ct_status ct_backproject_batch(const ct_geometry *g, const float *d_sinos, float *d_vols,
+                               int32_t nbatch, float alpha, float beta, void *stream);
+
 /* ct_project / ct_backproject with typed storage: d_vol holds vol_dtype and
  * d_sino sino_dtype elements (ct_dtype).  Values are read and converted to
  * FP32, every ray or voxel sum is accumulated in FP32, and the result is
@@ -188,6 +209,17 @@ ct_status ct_project_norm2(const ct_geometry *g, const float *d_vol, float *d_si
  * library routine is called. */
 ct_status ct_project_norm2_noalloc(const ct_geometry *g, const float *d_vol, float *d_sino,
                                    float alpha, float beta, double *d_norm2, void *stream);
+
+/* Bounds checking (no counterpart in the paper).  The library built with
+ * -DCT_DEBUG_BOUNDS (libct_gb300_debug.so) checks every voxel and
+ * detector-pixel index its projector kernels are about to touch; an index
+ * out of range is not accessed, and the first one records its source line.
+ * ct_debug_status waits for the current device, then returns
+ * CT_ERR_INTERNAL (message: file and line) if a violation was recorded
+ * since the last call, and clears it; CT_OK otherwise (always, in the normal
+ * build).  ct_debug_bounds_build returns 1 in the checking build, else 0. */
+ct_status ct_debug_status(void);
+int32_t ct_debug_bounds_build(void);
 
 /* Number of (ray, voxel) pairs with positive intersection length, i.e. the
  * nonzeros of A (the unit of the ray-voxel update rate).  *out is a HOST
@@ -262,6 +294,32 @@ typedef struct {
  * 3 volumes + 2 sinograms (+ weights).  Blocks until done. */
 ct_status ct_cgls(const ct_geometry *g, const float *d_b, float *d_x, const ct_solver_opts *opts,
                   ct_solver_report *report, void *stream);
+/* (The solvers return CT_ERR_INVALID_ARG when ||b|| or the final discrepancy
+ * is not finite: NaN or Inf in b or x0 propagates into every later value.
+ * With err_tol > 0 the iterations stop at the first such value.) */
+
+/* Checkpoint / resume of CGLS (no counterpart in the paper; Algorithm 1 needs
+ * only x, d_x, e_b and the scalars NB0, NR2 between two updates).  A state is
+ * library-owned device memory for those vectors (2 volumes + 1 sinogram,
+ * FP32) plus the scalars and the history, for one geometry size and device.
+ * ct_cgls_resume runs CGLS like ct_cgls, FP32 storage only, continuing from
+ * the state when it holds updates (d_x's input is then ignored; else d_x is
+ * x0), until the TOTAL update count reaches max_iter or the stopping rule
+ * fires, saves the state and returns x in d_x; the report covers all updates
+ * so far.  With a deterministic geometry a run resumed from a state is
+ * bitwise equal to the uninterrupted run.  export writes the state to host
+ * bytes (host NULL: only *bytes), import reads such bytes back (same
+ * sizes, same library version, else CT_ERR_INVALID_ARG). */
+typedef struct ct_cgls_state ct_cgls_state;
+ct_status ct_cgls_state_create(const ct_geometry *g, ct_cgls_state **out);
+void ct_cgls_state_destroy(ct_cgls_state *state);
+ct_status ct_cgls_state_iterations(const ct_cgls_state *state, int32_t *iterations);
+ct_status ct_cgls_state_export(const ct_cgls_state *state, void *host, int64_t capacity,
+                               int64_t *bytes);
+ct_status ct_cgls_state_import(ct_cgls_state *state, const void *host, int64_t bytes);
+ct_status ct_cgls_resume(const ct_geometry *g, const float *d_b, float *d_x,
+                         const ct_solver_opts *opts, ct_solver_report *report,
+                         ct_cgls_state *state, void *stream);
 
 /* LSQR (Paige & Saunders 1982) on the same operator; K iterations cost
  * 2K + 1 operator calls (+1 with a nonzero x0).  Same arguments as ct_cgls;

@@ -26,7 +26,9 @@ from typing import Optional, Sequence
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_build", "libct_gb300.so")
+# CT_GB300_DEBUG_BOUNDS=1 loads the bounds-checking build (see ct_debug_status).
+LIB_PATH = os.path.join(_PKG, "_build", "libct_gb300_debug.so"
+                        if os.environ.get("CT_GB300_DEBUG_BOUNDS") == "1" else "libct_gb300.so")
 
 CT_OK = 0
 CT_PRECOND_NONE, CT_PRECOND_JACOBI, CT_PRECOND_ROWCOL = 0, 1, 2
@@ -43,7 +45,10 @@ EXPORTS = ("ct_geometry_create", "ct_geometry_destroy", "ct_geometry_sizes", "ct
            "ct_project_norm2_noalloc", "ct_geometry_set_deterministic", "ct_project_ex",
            "ct_backproject_ex", "ct_sirt", "ct_geometry_set_projector", "ct_batch_create",
            "ct_batch_destroy", "ct_batch_add_cgls", "ct_batch_step", "ct_batch_poll",
-           "ct_batch_remove")
+           "ct_batch_remove", "ct_project_batch", "ct_backproject_batch",
+           "ct_cgls_state_create", "ct_cgls_state_destroy", "ct_cgls_state_iterations",
+           "ct_cgls_state_export", "ct_cgls_state_import", "ct_cgls_resume",
+           "ct_debug_status", "ct_debug_bounds_build")
 
 
 class CTError(RuntimeError):
@@ -115,6 +120,18 @@ def lib():
             "ct_geometry_sizes": ([vp, P(ctypes.c_int64), P(ctypes.c_int64)], ctypes.c_int),
             "ct_project": ([vp, vp, vp, ctypes.c_float, ctypes.c_float, vp], ctypes.c_int),
             "ct_backproject": ([vp, vp, vp, ctypes.c_float, ctypes.c_float, vp], ctypes.c_int),
+            "ct_project_batch": ([vp, vp, vp, ctypes.c_int32, ctypes.c_float, ctypes.c_float, vp],
+                                 ctypes.c_int),
+            "ct_cgls_state_create": ([vp, P(vp)], ctypes.c_int),
+            "ct_debug_status": ([], ctypes.c_int),
+            "ct_debug_bounds_build": ([], ctypes.c_int32),
+            "ct_cgls_state_destroy": ([vp], None),
+            "ct_cgls_state_iterations": ([vp, P(ctypes.c_int32)], ctypes.c_int),
+            "ct_cgls_state_export": ([vp, vp, ctypes.c_int64, P(ctypes.c_int64)], ctypes.c_int),
+            "ct_cgls_state_import": ([vp, vp, ctypes.c_int64], ctypes.c_int),
+            "ct_cgls_resume": ([vp, vp, vp, P(SolverOpts), P(_Report), vp, vp], ctypes.c_int),
+            "ct_backproject_batch": ([vp, vp, vp, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                                      vp], ctypes.c_int),
             "ct_project_norm2": ([vp, vp, vp, ctypes.c_float, ctypes.c_float, vp, vp],
                                  ctypes.c_int),
             "ct_project_norm2_noalloc": ([vp, vp, vp, ctypes.c_float, ctypes.c_float, vp, vp],
@@ -157,6 +174,16 @@ def _check(status: int):
 
 def version() -> str:
     return lib().ct_version().decode()
+
+
+def debug_status() -> None:
+    """Raise CTError (CT_ERR_INTERNAL) if the bounds-checking build recorded an
+    index out of range since the last call (waits for the current device)."""
+    _check(lib().ct_debug_status())
+
+
+def debug_bounds_build() -> bool:
+    return bool(lib().ct_debug_bounds_build())
 
 
 def kernel_launches() -> int:
@@ -324,6 +351,49 @@ def backproject(g: Geometry, sino: torch.Tensor, out: Optional[torch.Tensor] = N
     return o.cpu() if host else o
 
 
+def _batched(fn, g: Geometry, t: torch.Tensor, in_shape, out_shape, name, alpha, beta, out,
+             stream):
+    if tuple(t.shape[-3:]) != tuple(in_shape):
+        raise ValueError("%s: expected trailing shape %s, got %s"
+                         % (name, tuple(in_shape), tuple(t.shape)))
+    lead = tuple(t.shape[:-3])
+    host = not t.is_cuda
+    x = t.reshape((-1,) + tuple(in_shape))
+    if x.dtype != torch.float32:
+        raise ValueError("%s: FP32 only" % name)
+    x = x.to(g.device).contiguous()
+    nb = x.shape[0]
+    if out is None:
+        o = torch.empty((nb,) + tuple(out_shape), dtype=torch.float32, device=g.device)
+    else:
+        if out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous() \
+                or out.numel() != nb * out_shape[0] * out_shape[1] * out_shape[2]:
+            raise ValueError("%s: out must be a contiguous FP32 cuda tensor of %d items"
+                             % (name, nb))
+        o = out
+    _check(fn(g.handle, _ptr(x), _ptr(o), int(nb), float(alpha), float(beta), _stream(stream)))
+    if out is not None:
+        return out
+    o = o.reshape(lead + tuple(out_shape))
+    return o.cpu() if host else o
+
+
+def project_batch(g: Geometry, vols: torch.Tensor, out: Optional[torch.Tensor] = None,
+                  alpha: float = 1.0, beta: float = 0.0, stream=None) -> torch.Tensor:
+    """A applied to every item of vols [..., nz, ny, nx] (ct_project_batch:
+    one projector launch over all items for column-major Siddon geometries)."""
+    return _batched(lib().ct_project_batch, g, vols, g.vol_shape, g.sino_shape,
+                    "project_batch", alpha, beta, out, stream)
+
+
+def backproject_batch(g: Geometry, sinos: torch.Tensor, out: Optional[torch.Tensor] = None,
+                      alpha: float = 1.0, beta: float = 0.0, stream=None) -> torch.Tensor:
+    """A^T applied to every item of sinos [..., nviews, nv, nu]
+    (ct_backproject_batch)."""
+    return _batched(lib().ct_backproject_batch, g, sinos, g.sino_shape, g.vol_shape,
+                    "backproject_batch", alpha, beta, out, stream)
+
+
 def count_nnz(g: Geometry, stream=None) -> int:
     """Nonzeros of A: (ray, voxel) pairs with positive length (ct_count_nnz)."""
     n = ctypes.c_int64()
@@ -485,6 +555,67 @@ def sirt(g: Geometry, b: torch.Tensor, x0: Optional[torch.Tensor] = None, max_it
     r = SolveReport(rep.iterations, rep.nb0, rep.nb, list(hist[:rep.iterations]),
                     rep.n_forward, rep.n_back, rep.ms_forward, rep.ms_back)
     return (x.cpu() if host else x), r
+
+
+class CglsState:
+    """A resumable CGLS solve (ct_cgls_state): run(), then run() again with a
+    larger max_iter continues it; to_bytes() / from_bytes() checkpoint it to
+    host memory (or a file) and back."""
+
+    def __init__(self, g: Geometry):
+        self.g = g
+        h = ctypes.c_void_p()
+        with torch.cuda.device(g.device):
+            _check(lib().ct_cgls_state_create(g.handle, ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def iterations(self) -> int:
+        n = ctypes.c_int32()
+        _check(lib().ct_cgls_state_iterations(self._h, ctypes.byref(n)))
+        return n.value
+
+    def run(self, b: torch.Tensor, max_iter: int, x0: Optional[torch.Tensor] = None,
+            err_tol: float = 0.0, precond="none", tikhonov: float = 0.0, stream=None):
+        """CGLS until max_iter updates in total (or the stopping rule);
+        returns (x, SolveReport over all updates)."""
+        g = self.g
+        host = not b.is_cuda
+        bd = _dev(b, g.sino_shape, "b", g.device)
+        x = (torch.zeros(g.vol_shape, dtype=torch.float32, device=g.device) if x0 is None
+             else _dev(x0, g.vol_shape, "x0", g.device).clone())
+        opts = SolverOpts(int(max_iter), float(err_tol), _PRECOND[precond], float(tikhonov), 0, 0,
+                          DTYPES[torch.float32])
+        cap = max(int(max_iter), 1)
+        hist = (ctypes.c_double * cap)()
+        rep = _Report(0, 0.0, 0.0, ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)), cap, 0, 0,
+                      0.0, 0.0)
+        _check(lib().ct_cgls_resume(g.handle, _ptr(bd), _ptr(x), ctypes.byref(opts),
+                                    ctypes.byref(rep), self._h, _stream(stream)))
+        r = SolveReport(rep.iterations, rep.nb0, rep.nb, list(hist[:rep.iterations]),
+                        rep.n_forward, rep.n_back, rep.ms_forward, rep.ms_back)
+        return (x.cpu() if host else x), r
+
+    def to_bytes(self) -> bytes:
+        n = ctypes.c_int64()
+        _check(lib().ct_cgls_state_export(self._h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().ct_cgls_state_export(self._h, buf, n.value, ctypes.byref(n)))
+        return buf.raw
+
+    def from_bytes(self, data: bytes) -> None:
+        _check(lib().ct_cgls_state_import(self._h, data, len(data)))
+
+    def close(self):
+        if self._h:
+            lib().ct_cgls_state_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def lsqr(g: Geometry, b: torch.Tensor, x0: Optional[torch.Tensor] = None, max_iter: int = 20,

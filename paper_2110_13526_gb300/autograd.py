@@ -4,8 +4,9 @@
 The operator is linear, so the vector-Jacobian product of ``y = A x`` is
 ``A^T g`` and that of ``x = A^T y`` is ``A g``: each Function's backward is
 the other hand-written CUDA kernel (exact FP32 transposes of each other, see
-``ct_backproject``).  Inputs may carry a leading batch dimension; each item is
-projected with the same geometry.
+``ct_backproject``).  Inputs may carry leading batch dimensions; all items
+share the geometry and go through ``ct_project_batch`` / ``ct_backproject_batch``:
+one projector launch for the whole batch (column-major Siddon geometries).
 
 ``unrolled_cgls`` composes them into K iterations of Algorithm 1 that autograd
 can differentiate with respect to the data ``b`` (and ``x0``).  The operator
@@ -18,18 +19,7 @@ from __future__ import annotations
 import torch
 from torch.utils.checkpoint import checkpoint
 
-from . import Geometry, backproject, project
-
-
-def _apply(fn, g: Geometry, t: torch.Tensor, in_shape, out_shape) -> torch.Tensor:
-    if tuple(t.shape[-3:]) != tuple(in_shape):
-        raise ValueError("expected trailing shape %s, got %s" % (tuple(in_shape), tuple(t.shape)))
-    lead = t.shape[:-3]
-    flat = t.reshape((-1,) + tuple(in_shape)).contiguous()
-    out = torch.empty((flat.shape[0],) + tuple(out_shape), dtype=torch.float32, device=t.device)
-    for i in range(flat.shape[0]):
-        fn(g, flat[i], out=out[i])
-    return out.reshape(tuple(lead) + tuple(out_shape))
+from . import Geometry, backproject_batch, project_batch
 
 
 class ProjectFn(torch.autograd.Function):
@@ -38,12 +28,12 @@ class ProjectFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, x, g):
         ctx.g = g
-        return _apply(project, g, x.detach(), g.vol_shape, g.sino_shape)
+        return project_batch(g, x.detach())
 
     @staticmethod
     def backward(ctx, gy):
         g = ctx.g
-        return _apply(backproject, g, gy.contiguous(), g.sino_shape, g.vol_shape), None
+        return backproject_batch(g, gy.contiguous()), None
 
 
 class BackprojectFn(torch.autograd.Function):
@@ -52,12 +42,12 @@ class BackprojectFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, y, g):
         ctx.g = g
-        return _apply(backproject, g, y.detach(), g.sino_shape, g.vol_shape)
+        return backproject_batch(g, y.detach())
 
     @staticmethod
     def backward(ctx, gx):
         g = ctx.g
-        return _apply(project, g, gx.contiguous(), g.vol_shape, g.sino_shape), None
+        return project_batch(g, gx.contiguous()), None
 
 
 def A(g: Geometry, x: torch.Tensor) -> torch.Tensor:

@@ -614,6 +614,29 @@ ct_status ct_geometry_set_projector(ct_geometry *g, int32_t kind) {
     return CT_OK;
 }
 
+ct_status ct_debug_status(void) {
+    clear_error();
+    CT_CUDA_TRY(cudaDeviceSynchronize());
+    unsigned long long wp = 0, wf = 0;
+    CT_TRY(debug_take_projector(&wp));
+    CT_TRY(debug_take_footprint(&wf));
+    if (wp)
+        return set_error(CT_ERR_INTERNAL, "index out of range in projector.cu line " +
+                                              std::to_string(wp >> 1));
+    if (wf)
+        return set_error(CT_ERR_INTERNAL, "index out of range in footprint.cu line " +
+                                              std::to_string(wf >> 1));
+    return CT_OK;
+}
+
+int32_t ct_debug_bounds_build(void) {
+#ifdef CT_DEBUG_BOUNDS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 ct_status ct_count_nnz(const ct_geometry *g, int64_t *out, void *stream) {
     clear_error();
     CT_TRY(check_geom(g));

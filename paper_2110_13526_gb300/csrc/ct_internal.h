@@ -241,6 +241,12 @@ ct_status launch_combine_det(const ProjGeom &pg, float *out, float beta, const l
 ct_status launch_forward_direct(const ProjGeom &pg, const float *vol, float *p, float alpha,
                                 float beta, double *partials, cudaStream_t st);
 
+// CT_DEBUG_BOUNDS build (ct_debug.cuh): read and clear the bounds-violation
+// word of projector.cu / footprint.cu on the current device (0: none;
+// (line << 1) | 1 otherwise).  The normal build reports 0.
+ct_status debug_take_projector(unsigned long long *word);
+ct_status debug_take_footprint(unsigned long long *word);
+
 // ---- separable-footprint projectors (footprint.cu) -----------------------------
 // Per-view constants (2 float4 per view) and the global scalars
 // scal[5] = {SDD/du, SDD/dv, cu, cv, off_z}, FP64 on the host.

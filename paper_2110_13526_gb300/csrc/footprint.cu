@@ -28,6 +28,7 @@
 // view and segment.
 // Coordinates are relative to the volume centre (per-view constants computed
 // in FP64 on the host), which keeps the FP32 breakpoints accurate.
+#include "ct_debug.cuh"
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -173,7 +174,8 @@ __global__ void __launch_bounds__(256) k_sf_forward(ProjGeom g, const float *__r
                                        (float)(k0 + q) - 0.5f, (float)(k0 + q) + 0.5f)
                            : 0.f;
         for (int k = 0; k < g.nz; ++k) {
-            const float xv = UNIT_VOL ? 1.f : vol[(size_t)k * plane + (size_t)j * g.nx + i];
+            const size_t vi = (size_t)k * plane + (size_t)j * g.nx + i;
+            const float xv = UNIT_VOL || !CT_IN_BOUNDS(vi, plane * g.nz) ? 1.f : vol[vi];
             if (xv == 0.f) continue;
             float vb[4], amp;
             sf_axial<TT>(g, c, k, vb, amp);
@@ -187,7 +189,8 @@ __global__ void __launch_bounds__(256) k_sf_forward(ProjGeom g, const float *__r
                 const size_t row = vbase + (size_t)l * g.nu;
 #pragma unroll
                 for (int q = 0; q < kSfKUF; ++q) {
-                    if (q < nk && fu[q] != 0.f) {
+                    if (q < nk && fu[q] != 0.f &&
+                        CT_IN_BOUNDS(k0 + q, g.nu) && CT_IN_BOUNDS(l, g.nv)) {
                         float val = base * fu[q];
                         if (HAS_RHO) val *= rho[row + k0 + q];
                         atomicAdd(out + row + k0 + q, val);
@@ -242,7 +245,8 @@ __global__ void __launch_bounds__(256) k_sf_backward(ProjGeom g, const float *__
                         float su = 0.f;
 #pragma unroll
                         for (int q = 0; q < kSfKUF; ++q) {
-                            if (q < nk && fu[q] != 0.f) {
+                            if (q < nk && fu[q] != 0.f &&
+                                CT_IN_BOUNDS(k0 + q, g.nu) && CT_IN_BOUNDS(l, g.nv)) {
                                 float w = e ? e[row + q] : 1.f;
                                 if (HAS_RHO) w *= rho[row + q];
                                 su = POWER == 1 ? fmaf(fu[q], w, su) : fmaf(fu[q] * fu[q], w, su);
@@ -261,7 +265,7 @@ __global__ void __launch_bounds__(256) k_sf_backward(ProjGeom g, const float *__
         const size_t plane = (size_t)g.nx * g.ny;
         for (int dz = 0; dz < nzs; ++dz) {
             const size_t idx = (size_t)(kz0 + dz) * plane + (size_t)j * g.nx + i;
-            acc[idx] = fmaf(alpha, sacc[dz][tid], acc[idx]);
+            if (CT_IN_BOUNDS(idx, plane * g.nz)) acc[idx] = fmaf(alpha, sacc[dz][tid], acc[idx]);
         }
     }
 }
@@ -391,3 +395,5 @@ ct_status sf_axpby(float *out, const float *acc, int64_t n, float beta, cudaStre
 }
 
 }  // namespace ct
+
+CT_DEBUG_ACCESSOR(debug_take_footprint)

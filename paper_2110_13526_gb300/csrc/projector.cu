@@ -43,6 +43,7 @@
 #include <climits>
 #include <type_traits>
 
+#include "ct_debug.cuh"
 #include "ct_internal.h"
 #include "ct_types.cuh"
 
@@ -348,17 +349,18 @@ __global__ void __launch_bounds__(kTU *kTV, 6) k_forward(ProjGeom g, const TV *_
     Ray r;
     const bool valid = inb && ray_setup(g, view, u, v, r);
     const TV *base = r.transposed ? vol_t : vol;
+    const int64_t nvox = (int64_t)g.nx * g.ny * g.nz;
     float acc = 0.f;
     walk(r, valid, [&](int o, float l, bool p) {
         float val = 0.f;
-        if (p) val = UNIT_VOL ? 1.f : ld_f(base + o);
+        if (p && CT_IN_BOUNDS(o, nvox)) val = UNIT_VOL ? 1.f : ld_f(base + o);
         acc = fmaf(l, val, acc);
     });
     float alpha, beta;
     coef_of(c, alpha, beta);
     double sq = 0.0;
-    if (inb) {
-        const size_t idx = ((size_t)view * g.nv + v) * g.nu + u;
+    const size_t idx = ((size_t)view * g.nv + v) * g.nu + u;
+    if (inb && CT_IN_BOUNDS(idx, (int64_t)g.nviews * g.nv * g.nu)) {
         float val = valid ? acc * r.lsig : 0.f;
         if (HAS_RHO) val *= rho[idx];
         float o = alpha * val;
@@ -396,14 +398,15 @@ __global__ void __launch_bounds__(kTU *kTV, 6) k_backward(ProjGeom g, const TS *
     float alpha, beta;
     coef_of(c, alpha, beta);
     float w = 0.f;
-    if (valid) {
-        const size_t idx = ((size_t)view * g.nv + v) * g.nu + u;
+    const size_t idx = ((size_t)view * g.nv + v) * g.nu + u;
+    if (valid && CT_IN_BOUNDS(idx, (int64_t)g.nviews * g.nv * g.nu)) {
         w = alpha * (e ? to_f(e[idx]) : 1.f);
         if (HAS_RHO) w *= rho[idx];
         if (POWER == 1) w *= r.lsig;
     }
     valid = valid && (w != 0.f);
     const float ls = r.lsig;
+    const int64_t nvox = (int64_t)g.nx * g.ny * g.nz;
     if constexpr (DET) {
         const float scale = __ldg(det_scale);
         unsigned long long *base =
@@ -411,13 +414,13 @@ __global__ void __launch_bounds__(kTU *kTV, 6) k_backward(ProjGeom g, const TS *
         walk(r, valid, [&](int o, float l, bool p) {
             const float lm = l * ls;
             const float val = POWER == 1 ? w * l : w * lm * lm;
-            red_add_u64_if(base + o, __float2ll_rn(val * scale), p);
+            red_add_u64_if(base + o, __float2ll_rn(val * scale), p && CT_IN_BOUNDS(o, nvox));
         });
     } else {
         float *base = static_cast<float *>(r.transposed ? acc_t : acc);
         walk(r, valid, [&](int o, float l, bool p) {
             const float lm = l * ls;
-            red_add_if(base + o, POWER == 1 ? w * l : w * lm * lm, p);
+            red_add_if(base + o, POWER == 1 ? w * l : w * lm * lm, p && CT_IN_BOUNDS(o, nvox));
         });
     }
 }
@@ -462,12 +465,12 @@ __global__ void __launch_bounds__(kTU *kTV) k_forward_direct(ProjGeom g,
                 const int x = rem / g.ny, y = rem - x * g.ny;
                 oo = z * nxy + y * g.nx + x;
             }
-            acc = fmaf(l, __ldg(vol + oo), acc);
+            if (CT_IN_BOUNDS(oo, nxy * (int64_t)g.nz)) acc = fmaf(l, __ldg(vol + oo), acc);
         }
     });
     double sq = 0.0;
-    if (inb) {
-        const size_t idx = ((size_t)view * g.nv + v) * g.nu + u;
+    const size_t idx = ((size_t)view * g.nv + v) * g.nu + u;
+    if (inb && CT_IN_BOUNDS(idx, (int64_t)g.nviews * g.nv * g.nu)) {
         const float val = valid ? acc * r.lsig : 0.f;
         float o = alpha * val;
         if (beta != 0.f) o = fmaf(beta, out[idx], o);
@@ -799,17 +802,18 @@ __device__ __forceinline__ void forward_cm_tile(const ProjGeom &g, uint3 bid, ui
     const bool ok = cm_setup(g, view, u, v, col_live, r);
     float acc = 0.f;
     if (col_live) {
+        const int64_t nvox = (int64_t)g.nx * g.ny * g.nz;
         walk_cm(g, view * g.nu + u, r, ok, [&](int o, float l, bool p) {
             float val = 0.f;
-            if (p) val = UNIT_VOL ? 1.f : ld_f(vol_z + o);
+            if (p && CT_IN_BOUNDS(o, nvox)) val = UNIT_VOL ? 1.f : ld_f(vol_z + o);
             acc = fmaf(l, val, acc);
         });
     }
     float alpha, beta;
     coef_of(c, alpha, beta);
     double sq = 0.0;
-    if (col_live && v < g.nv) {
-        const size_t idx = ((size_t)view * g.nv + v) * g.nu + u;
+    const size_t idx = ((size_t)view * g.nv + v) * g.nu + u;
+    if (col_live && v < g.nv && CT_IN_BOUNDS(idx, (int64_t)g.nviews * g.nv * g.nu)) {
         float val = ok ? acc * r.lsig : 0.f;
         if (HAS_RHO) val *= rho[idx];
         float o = alpha * val;
@@ -869,27 +873,30 @@ __device__ __forceinline__ void backward_cm_tile(const ProjGeom &g, uint3 bid,
     float alpha, beta;
     coef_of(c, alpha, beta);
     float w = 0.f;
-    if (ok) {
-        const size_t idx = ((size_t)view * g.nv + v) * g.nu + u;
+    const size_t idx = ((size_t)view * g.nv + v) * g.nu + u;
+    if (ok && CT_IN_BOUNDS(idx, (int64_t)g.nviews * g.nv * g.nu)) {
         w = alpha * (e ? to_f(e[idx]) : 1.f);
         if (HAS_RHO) w *= rho[idx];
         if (POWER == 1) w *= r.lsig;
     }
     const bool nz = (w != 0.f);
     const float ls = r.lsig;
+    const int64_t nvox = (int64_t)g.nx * g.ny * g.nz;
     if constexpr (DET) {
         const float scale = __ldg(det_scale);
         unsigned long long *base = static_cast<unsigned long long *>(acc_z);
         walk_cm(g, view * g.nu + u, r, ok, [&](int o, float l, bool p) {
             const float lm = l * ls;
             const float val = POWER == 1 ? w * l : w * lm * lm;
-            red_add_u64_if(base + o, __float2ll_rn(val * scale), p && nz);
+            red_add_u64_if(base + o, __float2ll_rn(val * scale),
+                           p && nz && CT_IN_BOUNDS(o, nvox));
         });
     } else {
         float *base = static_cast<float *>(acc_z);
         walk_cm(g, view * g.nu + u, r, ok, [&](int o, float l, bool p) {
             const float lm = l * ls;
-            red_add_if(base + o, POWER == 1 ? w * l : w * lm * lm, p && nz);
+            red_add_if(base + o, POWER == 1 ? w * l : w * lm * lm,
+                       p && nz && CT_IN_BOUNDS(o, nvox));
         });
     }
 }
@@ -1305,3 +1312,5 @@ ct_status launch_forward_direct(const ProjGeom &pg, const float *vol, float *p, 
 }
 
 }  // namespace ct
+
+CT_DEBUG_ACCESSOR(debug_take_projector)

@@ -14,6 +14,8 @@
 // backprojector's ray weight).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <new>
 #include <memory>
 #include <vector>
 
@@ -81,6 +83,32 @@ struct CglsS {
     double nb0, nr2_old, nr2_now, np2, alpha, beta, nb, a_pend, tmp, zs;
     int it;   // next history slot (k_cgls_nb with i < 0)
 };
+
+// A CGLS state between two updates (checkpoint / resume, FP32 storage): x
+// before its pending step alpha d_x, d_x, e_b and the FP64 scalars on the
+// device, the history on the host.  Device buffers are owned here.
+struct CglsCkpt {
+    int device = 0;
+    int64_t n = 0, m = 0;
+    float *x = nullptr, *z = nullptr, *e = nullptr;
+    CglsS *s = nullptr;
+    std::vector<double> hist;
+    int i = 0;   // updates done
+};
+
+// NB0 and NB of a finished solve must be finite: NaN or Inf in b (or x0)
+// propagates into every later value, and is reported instead of returned as
+// a result.
+ct_status finite_or_error(double nb0, double nb) {
+    if (!std::isfinite(nb0))
+        return set_error(CT_ERR_INVALID_ARG, "b holds non-finite values (NaN or Inf): ||b|| = " +
+                                                 std::to_string(nb0));
+    if (!std::isfinite(nb))
+        return set_error(CT_ERR_INVALID_ARG,
+                         "the discrepancy became non-finite: x0 or b hold NaN or Inf, or the "
+                         "data overflow FP32");
+    return CT_OK;
+}
 
 // e = L o b, stored as S; partial sums of the stored e^2 (one per CTA).
 template <class S>
@@ -856,6 +884,11 @@ struct CglsJob {
 
     // Allocations, NB0, and the first update (i = 1).
     ct_status start() {
+        CT_TRY(alloc());
+        return first();
+    }
+    // The solve's weights and vectors.
+    ct_status alloc() {
         CT_TRY(sv.init(o.precond));
         const cudaStream_t st = sv.st;
         gn = vec_grid(n);
@@ -880,6 +913,10 @@ struct CglsJob {
         // Tikhonov regularisation (Software section): minimise
         // ||L (A x - b)||^2 + lam ||x||^2, Algorithm 1 on [L A W; sqrt(lam) W]
         if (lam > 0.0) CT_TRY(sv.ws.alloc(&zpart, (size_t)gn));
+        return CT_OK;
+    }
+    ct_status first() {
+        const cudaStream_t st = sv.st;
         // NB0 = ||b||; e_b = b - A x0 (the A x0 call is skipped for x0 = 0)
         bool x0nz = false;
         CT_TRY(sv.nonzero(x, &x0nz));
@@ -902,10 +939,45 @@ struct CglsJob {
         i = 1;
         return CT_OK;
     }
+    // Continue a solve from a saved state (x before its pending step, d_x, e_b,
+    // the scalars and the history; FP32 storage): the next update is i + 1.
+    ct_status resume(const CglsCkpt &c) {
+        CT_TRY(alloc());
+        const cudaStream_t st = sv.st;
+        const size_t nb = (size_t)n * sizeof(float), mb = (size_t)m * sizeof(float);
+        CT_CUDA_TRY(cudaMemcpyAsync(x, c.x, nb, cudaMemcpyDeviceToDevice, st));
+        CT_CUDA_TRY(cudaMemcpyAsync(z, c.z, nb, cudaMemcpyDeviceToDevice, st));
+        if (m > 0) CT_CUDA_TRY(cudaMemcpyAsync(e, c.e, mb, cudaMemcpyDeviceToDevice, st));
+        CT_CUDA_TRY(cudaMemcpyAsync(S, c.s, sizeof(CglsS), cudaMemcpyDeviceToDevice, st));
+        const int keep = std::min(c.i, K);
+        if (keep > 0)
+            CT_CUDA_TRY(cudaMemcpyAsync(hist, c.hist.data(), sizeof(double) * (size_t)keep,
+                                        cudaMemcpyHostToDevice, st));
+        i = c.i;
+        return CT_OK;
+    }
+    // Save the state after update i into c (before end() applies the pending
+    // step to x); waits for the stream.
+    ct_status save(CglsCkpt &c) {
+        const cudaStream_t st = sv.st;
+        const size_t nb = (size_t)n * sizeof(float), mb = (size_t)m * sizeof(float);
+        CT_CUDA_TRY(cudaMemcpyAsync(c.x, x, nb, cudaMemcpyDeviceToDevice, st));
+        CT_CUDA_TRY(cudaMemcpyAsync(c.z, z, nb, cudaMemcpyDeviceToDevice, st));
+        if (m > 0) CT_CUDA_TRY(cudaMemcpyAsync(c.e, e, mb, cudaMemcpyDeviceToDevice, st));
+        CT_CUDA_TRY(cudaMemcpyAsync(c.s, S, sizeof(CglsS), cudaMemcpyDeviceToDevice, st));
+        c.hist.assign((size_t)i, 0.0);
+        if (i > 0)
+            CT_CUDA_TRY(cudaMemcpyAsync(c.hist.data(), hist, sizeof(double) * (size_t)i,
+                                        cudaMemcpyDeviceToHost, st));
+        CT_CUDA_TRY(cudaStreamSynchronize(st));
+        c.i = i;
+        return CT_OK;
+    }
     // The stopping rule of Algorithm 1 given the scalars h read back after
     // update i (only read when ERR > 0).
     bool go_on(const CglsS &h) const {
         if (i >= K) return false;
+        if (ERR > 0.0 && !(std::isfinite(h.nb0) && std::isfinite(h.nb))) return false;
         return ERR <= 0.0 || ((h.nb0 > 0.0) && (h.nb / h.nb0 > ERR));
     }
     ct_status keep_going(bool *go) {
@@ -937,15 +1009,18 @@ struct CglsJob {
                                     cudaMemcpyDeviceToHost, st));
         CT_TRY(read_scalars(S, &hs, st));
         sv.report(rep, i, hs.nb0, hs.nb, h);
-        return CT_OK;
+        return finite_or_error(hs.nb0, hs.nb);
     }
 };
 
 template <class ST>
 ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_solver_opts *o,
-                    ct_solver_report *rep, cudaStream_t st) {
+                    ct_solver_report *rep, cudaStream_t st, CglsCkpt *ck = nullptr) {
     CglsJob<ST> job(g, b, x, o, st);
-    CT_TRY(job.start());
+    if (ck && ck->i > 0)
+        CT_TRY(job.resume(*ck));
+    else
+        CT_TRY(job.start());
     // Without per-operator timing or recomputation every update enqueues the
     // same launches with the same arguments (the scalars live on the device),
     // so the first one is captured as a CUDA graph and replayed: one launch
@@ -981,6 +1056,7 @@ ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
         ++job.i;
         CT_TRY(job.keep_going(&go));
     }
+    if (ck) CT_TRY(job.save(*ck));
     return job.end(rep);
 }
 
@@ -1096,7 +1172,7 @@ ct_status lsqr_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
                                     cudaMemcpyDeviceToHost, st));
     CT_TRY(read_scalars(S, &hs, st));
     sv.report(rep, i, hs.nb0, hs.phibar, h);
-    return CT_OK;
+    return finite_or_error(hs.nb0, hs.phibar);
 }
 
 
@@ -1176,12 +1252,17 @@ ct_status sirt_impl(const ct_geometry *g, const float *b, float *x, const ct_sir
                                 cudaMemcpyDeviceToHost, st));
     CT_TRY(read_scalars(S, &hs, st));
     sv.report(rep, i, hs.nb0, hs.nb, h);
-    return CT_OK;
+    return finite_or_error(hs.nb0, hs.nb);
 }
 }  // namespace
 }  // namespace ct
 
 using namespace ct;
+
+// Opaque to callers (include/ct.h): a CGLS state between two updates.
+struct ct_cgls_state {
+    CglsCkpt ck;
+};
 
 // Several CGLS solves advanced in lock step (continuous batching): each
 // ct_batch_step runs one update of every active job, with the A^T of all
@@ -1587,6 +1668,152 @@ ct_status ct_sirt(const ct_geometry *g, const float *d_b, float *d_x, const ct_s
     const ct_status s = sirt_impl(g, d_b, d_x, opts, report, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (s == CT_OK && e != cudaSuccess) return cuda_error(e, "ct_sirt");
+    return s;
+}
+
+// ---- CGLS checkpoint / resume -----------------------------------------------
+
+ct_status ct_cgls_state_create(const ct_geometry *g, ct_cgls_state **out) {
+    clear_error();
+    if (!g || !out) return set_error(CT_ERR_INVALID_ARG, "geometry and out must be non-NULL");
+    *out = nullptr;
+    DeviceGuard dg(g->device);
+    CT_TRY(dg.status());
+    ct_cgls_state *st = new (std::nothrow) ct_cgls_state();
+    if (!st) return set_error(CT_ERR_OOM, "host allocation failed");
+    CglsCkpt &c = st->ck;
+    c.device = g->device;
+    c.n = g->nvox;
+    c.m = g->nrays;
+    cudaError_t e = cudaMalloc(&c.x, (size_t)c.n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c.z, (size_t)c.n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c.e, (size_t)std::max<int64_t>(c.m, 1) * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c.s, sizeof(CglsS));
+    if (e != cudaSuccess) {
+        ct_cgls_state_destroy(st);
+        return e == cudaErrorMemoryAllocation ? set_error(CT_ERR_OOM, "cgls state: out of memory")
+                                              : cuda_error(e, "cgls state allocation");
+    }
+    *out = st;
+    return CT_OK;
+}
+
+void ct_cgls_state_destroy(ct_cgls_state *st) {
+    if (!st) return;
+    {
+        DeviceGuard dg(st->ck.device);
+        if (st->ck.x) cudaFree(st->ck.x);
+        if (st->ck.z) cudaFree(st->ck.z);
+        if (st->ck.e) cudaFree(st->ck.e);
+        if (st->ck.s) cudaFree(st->ck.s);
+    }
+    delete st;
+}
+
+ct_status ct_cgls_state_iterations(const ct_cgls_state *st, int32_t *iterations) {
+    clear_error();
+    if (!st || !iterations) return set_error(CT_ERR_INVALID_ARG, "NULL state or iterations");
+    *iterations = st->ck.i;
+    return CT_OK;
+}
+
+namespace {
+// Serialised form of a state: this header, then x, d_x (n floats each), e_b
+// (m floats), the scalar block and the history (i doubles), native byte order.
+struct CkptHeader {
+    uint32_t magic, version;
+    int64_t n, m;
+    int32_t i, pad;
+    uint64_t scalar_bytes;
+};
+constexpr uint32_t kCkptMagic = 0x47435443u;   // "CTCG"
+constexpr uint32_t kCkptVersion = 1;
+
+int64_t ckpt_bytes(const CglsCkpt &c) {
+    return (int64_t)sizeof(CkptHeader) + (2 * c.n + c.m) * (int64_t)sizeof(float) +
+           (int64_t)sizeof(CglsS) + c.i * (int64_t)sizeof(double);
+}
+}  // namespace
+
+ct_status ct_cgls_state_export(const ct_cgls_state *st, void *host, int64_t capacity,
+                               int64_t *bytes) {
+    clear_error();
+    if (!st || !bytes) return set_error(CT_ERR_INVALID_ARG, "NULL state or bytes");
+    const CglsCkpt &c = st->ck;
+    *bytes = ckpt_bytes(c);
+    if (!host) return CT_OK;
+    if (capacity < *bytes) return set_error(CT_ERR_INVALID_ARG, "export buffer too small");
+    DeviceGuard dg(c.device);
+    CT_TRY(dg.status());
+    char *p = static_cast<char *>(host);
+    CkptHeader h{kCkptMagic, kCkptVersion, c.n, c.m, c.i, 0, sizeof(CglsS)};
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    CT_CUDA_TRY(cudaMemcpy(p, c.x, (size_t)c.n * sizeof(float), cudaMemcpyDeviceToHost));
+    p += c.n * sizeof(float);
+    CT_CUDA_TRY(cudaMemcpy(p, c.z, (size_t)c.n * sizeof(float), cudaMemcpyDeviceToHost));
+    p += c.n * sizeof(float);
+    if (c.m > 0) CT_CUDA_TRY(cudaMemcpy(p, c.e, (size_t)c.m * sizeof(float), cudaMemcpyDeviceToHost));
+    p += c.m * sizeof(float);
+    CT_CUDA_TRY(cudaMemcpy(p, c.s, sizeof(CglsS), cudaMemcpyDeviceToHost));
+    p += sizeof(CglsS);
+    if (c.i > 0) std::memcpy(p, c.hist.data(), sizeof(double) * (size_t)c.i);
+    return CT_OK;
+}
+
+ct_status ct_cgls_state_import(ct_cgls_state *st, const void *host, int64_t bytes) {
+    clear_error();
+    if (!st || !host) return set_error(CT_ERR_INVALID_ARG, "NULL state or buffer");
+    CglsCkpt &c = st->ck;
+    CkptHeader h;
+    if (bytes < (int64_t)sizeof(h)) return set_error(CT_ERR_INVALID_ARG, "state buffer too short");
+    std::memcpy(&h, host, sizeof(h));
+    if (h.magic != kCkptMagic || h.version != kCkptVersion || h.scalar_bytes != sizeof(CglsS))
+        return set_error(CT_ERR_INVALID_ARG, "not a CGLS state of this library version");
+    if (h.n != c.n || h.m != c.m)
+        return set_error(CT_ERR_INVALID_ARG, "state sizes do not match this geometry");
+    if (h.i < 0) return set_error(CT_ERR_INVALID_ARG, "state: negative update count");
+    CglsCkpt probe;
+    probe.n = h.n;
+    probe.m = h.m;
+    probe.i = h.i;
+    if (bytes != ckpt_bytes(probe)) return set_error(CT_ERR_INVALID_ARG, "state buffer size");
+    DeviceGuard dg(c.device);
+    CT_TRY(dg.status());
+    const char *p = static_cast<const char *>(host) + sizeof(h);
+    CT_CUDA_TRY(cudaMemcpy(c.x, p, (size_t)c.n * sizeof(float), cudaMemcpyHostToDevice));
+    p += c.n * sizeof(float);
+    CT_CUDA_TRY(cudaMemcpy(c.z, p, (size_t)c.n * sizeof(float), cudaMemcpyHostToDevice));
+    p += c.n * sizeof(float);
+    if (c.m > 0) CT_CUDA_TRY(cudaMemcpy(c.e, p, (size_t)c.m * sizeof(float), cudaMemcpyHostToDevice));
+    p += c.m * sizeof(float);
+    CT_CUDA_TRY(cudaMemcpy(c.s, p, sizeof(CglsS), cudaMemcpyHostToDevice));
+    p += sizeof(CglsS);
+    c.hist.assign((size_t)h.i, 0.0);
+    if (h.i > 0) std::memcpy(c.hist.data(), p, sizeof(double) * (size_t)h.i);
+    c.i = h.i;
+    return CT_OK;
+}
+
+ct_status ct_cgls_resume(const ct_geometry *g, const float *d_b, float *d_x,
+                         const ct_solver_opts *opts, ct_solver_report *report, ct_cgls_state *state,
+                         void *stream) {
+    clear_error();
+    CT_TRY(check_opts(g, d_b, d_x, opts));
+    if (!state) return set_error(CT_ERR_INVALID_ARG, "state is NULL");
+    CglsCkpt &c = state->ck;
+    if (c.n != g->nvox || c.m != g->nrays || c.device != g->device)
+        return set_error(CT_ERR_INVALID_ARG, "state belongs to another geometry size or device");
+    if (opts->storage != CT_F32)
+        return set_error(CT_ERR_INVALID_ARG, "resumable CGLS supports FP32 storage only");
+    if (opts->max_iter < c.i)
+        return set_error(CT_ERR_INVALID_ARG, "max_iter is below the updates the state holds");
+    DeviceGuard dg(g->device);
+    CT_TRY(dg.status());
+    cudaStream_t st = (cudaStream_t)stream;
+    ct_status s = cgls_impl<float>(g, d_b, d_x, opts, report, st, &c);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (s == CT_OK && e != cudaSuccess) return cuda_error(e, "ct_cgls_resume");
     return s;
 }
 

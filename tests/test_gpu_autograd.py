@@ -70,6 +70,45 @@ def test_batched_apply_matches_single(ct, batch):
     assert torch.equal(AT(gd, b)[5], ct.backproject(gd, b[5].contiguous()))
 
 
+def test_batch_is_one_projector_launch(ct, batch):
+    """The 8 items of a batch take one projector launch per operator (plus a
+    layout transpose per item for A and a combine per item for A^T)."""
+    from paper_2110_13526_gb300.autograd import A, AT
+    g, x, b = batch
+    torch.cuda.synchronize()
+    l0 = ct.kernel_launches()
+    A(g, x)
+    torch.cuda.synchronize()
+    assert ct.kernel_launches() - l0 == 8 + 1
+    l0 = ct.kernel_launches()
+    AT(g, b)
+    torch.cuda.synchronize()
+    assert ct.kernel_launches() - l0 == 1 + 8
+
+
+def test_batch_entry_points_alpha_beta_and_fallback(ct):
+    """alpha/beta epilogues of the batched entry points, and geometries that
+    run item by item (rays advancing along z: ray-major kernels)."""
+    for cfg in (dict(nx=20, ny=18, nz=14, vx=1.0, vy=1.0, vz=1.0, nu=30, nv=40, du=1.0, dv=1.0,
+                     sid=120.0, sdd=200.0, nviews=7),
+                dict(nx=16, ny=16, nz=40, vx=1.0, vy=1.0, vz=1.0, nu=24, nv=70, du=1.5, dv=2.5,
+                     sid=30.0, sdd=60.0, nviews=5)):
+        g = ct.Geometry(**cfg)
+        x = torch.from_numpy(synth.random_field((3,) + g.vol_shape, seed=50)).cuda()
+        y0 = torch.from_numpy(synth.random_field((3,) + g.sino_shape, seed=51)).cuda()
+        out = y0.clone()
+        ct.project_batch(g, x, out=out, alpha=-0.5, beta=2.0)
+        for i in range(3):
+            want = ct.project(g, x[i].contiguous(), out=y0[i].clone(), alpha=-0.5, beta=2.0)
+            assert torch.equal(out[i], want)
+        v0 = torch.from_numpy(synth.random_field((3,) + g.vol_shape, seed=52)).cuda()
+        vout = v0.clone()
+        ct.backproject_batch(g, y0, out=vout, alpha=0.25, beta=-1.0)
+        for i in range(3):
+            want = ct.backproject(g, y0[i].contiguous(), out=v0[i].clone(), alpha=0.25, beta=-1.0)
+            assert ((vout[i] - want).norm() / want.norm()).item() < 1e-6
+
+
 def test_finite_differences_64_voxels(ct, batch):
     g, x, b = batch
     xg = x.clone().requires_grad_(True)
