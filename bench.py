@@ -55,14 +55,23 @@ def parse():
                          "launches, iteration-level scheduling)")
     ap.add_argument("--batch-executors", type=int, default=1,
                     help="serve mode with --batched: batches on their own streams")
+    ap.add_argument("--no-serve-equal-error", dest="serve_equal_error", action="store_false",
+                    help="default mode: skip the FP32/FP16 served streams at equal error")
+    ap.add_argument("--max-iter", type=int, default=50,
+                    help="serve mode: update cap per request (the stop rule is NB/NB0 <= 1e-3)")
+    ap.add_argument("--batch-route", default="load", choices=["load", "size"],
+                    help="serve mode with --batched: a request goes to the least loaded batch, "
+                         "or to the batch of its volume size")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
                     help="serve mode: CGLS Krylov-vector storage")
-    ap.add_argument("--serve-requests", type=int, default=32,
+    ap.add_argument("--serve-requests", type=int, default=128,
                     help="default mode: requests of the served-latency block (0 = skip)")
     ap.add_argument("--workload", default="B256", choices=["B256", "P512"],
                     help="ops mode only: 256^3 (default) or the 512^3, 720-view workload")
     ap.add_argument("--projector", default="siddon", choices=["siddon", "sf_tr", "sf_tt"],
                     help="ops mode only: Siddon rays or separable footprints (TR, TT)")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"],
+                    help="ops mode only: storage of the volume and sinogram (FP32 sums)")
     ap.add_argument("--views", type=int, default=0,
                     help="ops mode only: use this many of the workload's views, evenly spread "
                          "(a smaller case of the same kernels for profiling)")
@@ -388,6 +397,13 @@ def run_ours(a):
             "clocks": clk}
     if a.serve_requests > 0:
         line["served"] = serve_stream(a.serve_requests, 20.0, 8)
+        if a.serve_equal_error:
+            # the served form with reduced-precision storage against FP32 at
+            # equal reconstruction error: every request run to NB/NB0 <= 1e-3
+            line["served_equal_error"] = {
+                "max_iter": 200,
+                "f32": serve_stream(a.serve_requests, 20.0, 8, max_iter=200),
+                "f16": serve_stream(a.serve_requests, 20.0, 8, storage="f16", max_iter=200)}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cb = cpu_baseline(cfg, a.cpu_sample_views, K)
         cb.pop("seconds", None)
@@ -421,9 +437,11 @@ def run_ops(a):
     x_true = torch.from_numpy(synth.voxelize(synth.random_ellipsoids(
         40, PHANTOM_SEED[a.workload], lo, hi), cfg)).to(dev)
     e = torch.from_numpy(synth.random_field(g.sino_shape, seed=7)).to(dev)
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[a.dtype]
+    x_true, e = x_true.to(dt), e.to(dt)
     nnz = ct.count_nnz(g)
-    r = torch.empty(g.vol_shape, device="cuda")
-    p = torch.empty(g.sino_shape, device="cuda")
+    r = torch.empty(g.vol_shape, device="cuda", dtype=dt)
+    p = torch.empty(g.sino_shape, device="cuda", dtype=dt)
     for _ in range(a.warmup):
         ct.project(g, x_true, out=p)
         ct.backproject(g, e, out=r)
@@ -441,7 +459,7 @@ def run_ops(a):
         tb.append(ev[1].elapsed_time(ev[2]))
     mf, mb = statistics.median(tf), statistics.median(tb)
     print(json.dumps({"mode": "ops", "config": {"workload": a.workload, "nnz": nnz,
-                                                "views": cfg["nviews"],
+                                                "views": cfg["nviews"], "dtype": a.dtype,
                                                 "projector": a.projector},
                       "ms_project": mf, "ms_backproject": mb,
                       "gray_voxel_per_s": {"A": nnz / mf / 1e6, "AT": nnz / mb / 1e6},
@@ -451,34 +469,61 @@ def run_ops(a):
     return 0
 
 
-def serve_stream(n_requests: int, rate: float, slots: int, budget_gb: float = 150.0,
-                 storage: str = "f32", batched: bool = False, batch_executors: int = 1):
-    """Serving workload: Poisson arrivals (seed 3), volumes 64..256^3, 60..360
-    views, detector scaled to magnification 1.6, CGLS or LSQR to relative
-    discrepancy 1e-3 or 50 updates; continuous batching over ``slots``
-    streams under an HBM budget.  Returns the stats dict of the run."""
+_SERVE_CACHE = {}
+
+
+def serve_requests(n_requests: int, rate: float):
+    """The requests of the serving stream (built once per process: the
+    phantoms, their projections and the geometries): Poisson arrivals
+    (seed 3), volumes 64..256^3, 60..360 views, detector scaled to
+    magnification 1.6, CGLS or LSQR."""
     import torch
 
     import paper_2110_13526_gb300 as ct
     import synth
-    from paper_2110_13526_gb300.serving import Request, Server
+    from paper_2110_13526_gb300.serving import Request
 
+    key = (n_requests, rate)
+    if key in _SERVE_CACHE:
+        return _SERVE_CACHE[key]
     stream = synth.serving_stream(n_requests, rate, 3)
     reqs, geoms = [], {}
     for s in stream:
         cfg = synth.serving_geometry(s["n"], s["views"])
-        key = (s["n"], s["views"])
-        if key not in geoms:
-            geoms[key] = ct.Geometry(**cfg)
+        gk = (s["n"], s["views"])
+        if gk not in geoms:
+            geoms[gk] = ct.Geometry(**cfg)
         x = torch.from_numpy(synth.serving_phantom(s["n"], s["phantom_seed"])).cuda()
-        b = ct.project(geoms[key], x)
+        b = ct.project(geoms[gk], x)
         reqs.append(Request(s["rid"], cfg, b, s["solver"], s["arrival"], max_iter=50,
-                            err_tol=1e-3, storage=storage))
+                            err_tol=1e-3))
     torch.cuda.synchronize()
+    _SERVE_CACHE[key] = reqs
+    return reqs
+
+
+def serve_stream(n_requests: int, rate: float, slots: int, budget_gb: float = 150.0,
+                 storage: str = "f32", batched: bool = False, batch_executors: int = 1,
+                 batch_route: str = "load", max_iter: int = 50):
+    """Serving workload (serve_requests), each request solved to relative
+    discrepancy 1e-3 or max_iter updates, CGLS Krylov vectors in ``storage``;
+    continuous batching over ``slots`` streams under an HBM budget.  Returns
+    the stats dict of the run."""
+    import dataclasses
+
+    from paper_2110_13526_gb300.serving import Server
+
+    reqs = [dataclasses.replace(r, max_iter=max_iter, storage=storage)
+            for r in serve_requests(n_requests, rate)]
     stats = Server(slots=slots, hbm_budget_bytes=budget_gb * 1e9, batched=batched,
-                   batch_executors=batch_executors).run(reqs)
+                   batch_executors=batch_executors, batch_route=batch_route).run(reqs)
     iters = stats.iterations
+    reached = sum(1 for r in stats.results if r.rel_discrepancy <= 1e-3)
     return {"requests": len(reqs), "rate_per_s": rate, "slots": slots,
+            "arrival_rate_per_s": rate, "served_per_s": len(reqs) / stats.wall_s,
+            "max_iter": max_iter, "reached_1e-3": reached,
+            "max_rel_discrepancy": float(max((r.rel_discrepancy for r in stats.results),
+                                             default=0.0)),
             "p50_s": stats.p50, "p99_s": stats.p99, "wall_s": stats.wall_s,
             "requests_per_s": len(reqs) / stats.wall_s, "solver_iters_per_s": iters / stats.wall_s,
             "max_concurrent": stats.max_concurrent,
@@ -486,13 +531,14 @@ def serve_stream(n_requests: int, rate: float, slots: int, budget_gb: float = 15
             "mean_iterations": iters / max(len(reqs), 1),
             "storage": storage,
             "batched": batched, "batch_executors": batch_executors if batched else 0,
+            "batch_route": batch_route if batched else None,
             "batch_steps": stats.extra.get("batch_steps", 0),
             "mean_rel_discrepancy": float(sum(r.rel_discrepancy for r in stats.results)
                                           / max(len(stats.results), 1)),
             "workload": "Poisson arrivals (seed 3); n in {64,128,192,256}, views in "
                         "{60,120,180,360}, detector 1.5n x 1.125n of 1.6 mm; CGLS/LSQR to "
-                        "1e-3 or 50 updates; 8-ellipsoid phantoms; CGLS Krylov storage "
-                        + storage + " (LSQR FP32)"}
+                        "1e-3 or %d updates; 8-ellipsoid phantoms; CGLS Krylov storage "
+                        % max_iter + storage + " (LSQR FP32)"}
 
 
 def run_precision(a):
@@ -555,7 +601,8 @@ def run_serve(a):
     torch.cuda.set_device(0)
     out = {"mode": "serve"}
     out.update(serve_stream(a.requests, a.rate, a.slots, storage=a.storage, batched=a.batched,
-                            batch_executors=a.batch_executors))
+                            batch_executors=a.batch_executors, batch_route=a.batch_route,
+                            max_iter=a.max_iter))
     print(json.dumps(out))
     return 0
 

@@ -1273,6 +1273,11 @@ struct ct_cgls_state {
 // Side streams over which a batched step spreads the jobs' vector kernels.
 constexpr int kBatchSideStreams = 8;
 
+// Steps with an unchanged set of jobs after which ct_batch captures its step
+// as a CUDA graph (before that, and after every join or leave, it launches
+// the step's kernels directly).
+constexpr int kStableSteps = 3;
+
 struct ct_batch {
     struct Entry {
         int32_t id = 0;
@@ -1296,6 +1301,7 @@ struct ct_batch {
     int nbf = 0, nbd = 0, nfw = 0;      // jobs in each table
     unsigned tbf = 0, tbd = 0, tfw = 0; // tiles in each table
     std::unique_ptr<UpdateGraph> graph;
+    int stable = 0;                     // steps since the set of active jobs last changed
     std::vector<cudaStream_t> side;     // streams of the per-job phases
     cudaEvent_t ev_fork = nullptr;
     std::vector<cudaEvent_t> ev_join;
@@ -1446,8 +1452,26 @@ struct ct_batch {
         int active = 0;
         for (auto &en : jobs) active += !en.done;
         if (active > 0) {
-            if (dirty) CT_TRY(build_tables());
-            if (!graph) {
+            if (dirty) {
+                CT_TRY(build_tables());
+                stable = 0;
+            }
+            // A graph pays only if the same step is replayed: while jobs join
+            // or leave step after step (a busy server), launch the step
+            // directly, and capture it once the set has held for kStableSteps.
+            if (!graph && stable < kStableSteps) {
+                std::vector<int> f0, b0;   // counted below, one A and one A^T per update
+                for (auto &en : jobs) {
+                    f0.push_back(en.job->sv.n_fwd);
+                    b0.push_back(en.job->sv.n_back);
+                }
+                const ct_status ds = step_body();
+                for (size_t k = 0; k < jobs.size(); ++k) {
+                    jobs[k].job->sv.n_fwd = f0[k];
+                    jobs[k].job->sv.n_back = b0[k];
+                }
+                CT_TRY(ds);
+            } else if (!graph) {
                 // the same launches with the same arguments until the set changes
                 graph.reset(new UpdateGraph());
                 std::vector<int> f0, b0;
@@ -1466,7 +1490,8 @@ struct ct_batch {
                     return cs;
                 }
             }
-            CT_TRY(graph->launch(st));
+            if (graph) CT_TRY(graph->launch(st));
+            ++stable;
             // scalars of the jobs that test a tolerance, one wait for all
             if (jobs.size() > s_cap) {
                 if (h_s) CT_CUDA_TRY(cudaFreeHost(h_s));

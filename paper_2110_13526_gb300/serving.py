@@ -13,7 +13,8 @@ the float-atomic summation order of the backprojection.
 
 With ``batched=True`` the FP32 CGLS requests instead join a ct_batch
 (iteration-level continuous batching; ``batch_executors`` batches on their
-own streams, each request to the least loaded): a batch thread advances its
+own streams, each request to the least loaded one, or with
+``batch_route="size"`` to the batch of its volume size): a batch thread advances its
 admitted CGLS jobs one update per step, with the backprojections of all of them in one
 persistent kernel launch and their projections in another, inside a CUDA
 graph; jobs join between steps as they are admitted and leave when their
@@ -63,6 +64,10 @@ class Result:
         return self.end - self.arrival
 
 
+def _vox(geometry: dict) -> int:
+    return geometry["nx"] * geometry["ny"] * geometry["nz"]
+
+
 def footprint_bytes(geometry: dict, solver: str) -> int:
     """Device bytes a solve holds: the library's workspace plus x.
 
@@ -92,11 +97,14 @@ class ServeStats:
 class Server:
     def __init__(self, slots: int = 8, hbm_budget_bytes: float = 150e9, device=None,
                  deterministic: bool = False, batched: bool = False, batch_jobs: int = 32,
-                 batch_executors: int = 1):
+                 batch_executors: int = 1, batch_route: str = "load"):
         if slots < 1:
             raise ValueError("slots must be >= 1")
         if batch_jobs < 1 or batch_executors < 1:
             raise ValueError("batch_jobs and batch_executors must be >= 1")
+        if batch_route not in ("load", "size"):
+            raise ValueError("batch_route must be 'load' or 'size'")
+        self.batch_route = batch_route
         self.slots = slots
         self.batched = batched
         self.batch_jobs = batch_jobs
@@ -126,6 +134,10 @@ class Server:
                 raise ValueError("request %d needs %d bytes, budget %d" % (r.rid, fp, self.budget))
             self.geometry(r.geometry)          # geometries are built before the clock starts
         torch.cuda.synchronize(self.device)
+        # size classes of the batched CGLS requests (batch_route "size"): the
+        # jobs of one batch advance in lock step, so each batch takes volumes
+        # of one size and no small job waits for a large one's updates
+        size_class = {v: c for c, v in enumerate(sorted({_vox(r.geometry) for r in reqs}))}
         cv = threading.Condition()
         state = {"free_slots": self.slots, "bytes": 0, "running": 0, "max_running": 0,
                  "max_bytes": 0, "errors": [], "batch_active": 0, "batch_stop": False,
@@ -246,7 +258,10 @@ class Server:
                         if state["batch_active"] >= self.batch_jobs or state.get("batch_dead"):
                             break
                         req = pending.pop(0)
-                        k = min(range(n_ex), key=lambda j: load[j])   # least loaded executor
+                        if self.batch_route == "size":
+                            k = size_class[_vox(req.geometry)] % n_ex   # one class per batch
+                        else:
+                            k = min(range(n_ex), key=lambda j: load[j])   # least loaded
                         load[k] += 1
                         state["batch_active"] += 1
                         state["bytes"] += fp
