@@ -89,18 +89,22 @@ ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out);
 /* Free the geometry (NULL is a no-op).  No call using it may be in flight. */
 void ct_geometry_destroy(ct_geometry *g);
 
-/* Deterministic accumulation (default off).  When on, every backprojection
- * with this geometry (ct_backproject, the solvers, the preconditioner
- * weights) sums its contributions as 64-bit fixed-point integers: each value
- * is scaled by a power of two chosen from max |input| and a bound on the rays
- * through one voxel, rounded to an integer and added with integer atomics.
- * Integer addition does not depend on order, so results are bitwise
- * reproducible from run to run and independent of other work sharing the
- * GPU; each contribution is rounded to a multiple of at most 2^-61 times the
- * bound on a voxel's sum.  Costs 16 bytes per voxel of workspace and a
- * slower backprojection.  The forward projection, the vector updates and
- * the FP64 reductions are deterministic in both modes.  Change the mode only
- * while no call on this geometry is in flight. */
+/* Deterministic accumulation (default off).  When on, every scatter with
+ * this geometry sums its contributions as 64-bit fixed-point integers: each
+ * value is scaled by a power of two chosen from max |input| and a bound on
+ * the sum, rounded to an integer and added with integer atomics.  Integer
+ * addition does not depend on order, so results are bitwise reproducible
+ * from run to run and independent of other work sharing the GPU; each
+ * contribution is rounded to a multiple of at most 2^-61 times the bound.
+ * Siddon: the backprojections (ct_backproject, the solvers, the
+ * preconditioner weights) scatter; the bound is the rays through one voxel
+ * times the longest chord; 16 bytes per voxel of workspace.  Footprint
+ * projectors: the forward projection scatters; the bound is the voxel count
+ * times the longest footprint amplitude; 8 bytes per ray of workspace (which
+ * ct_project_norm2_noalloc cannot take).  The other direction of each
+ * projector, the vector updates and the FP64 reductions are deterministic in
+ * both modes.  Change the mode only while no call on this geometry is in
+ * flight. */
 ct_status ct_geometry_set_deterministic(ct_geometry *g, int32_t on);
 
 /* Projector of a geometry (Materials and Methods names Siddon, the TT
@@ -117,9 +121,9 @@ ct_status ct_geometry_set_deterministic(ct_geometry *g, int32_t on);
  * The same matrix serves ct_project, ct_backproject (exactly adjoint), the
  * solvers and the preconditioner weights.  The footprint projectors need
  * FP32 storage (CT_ERR_INVALID_ARG for BF16/FP16 in ct_project_ex,
- * ct_backproject_ex and the solvers' storage), cannot be combined with
- * deterministic accumulation (their forward projection scatters with float
- * atomics; their backprojection gathers and is deterministic anyway), and
+ * ct_backproject_ex and the solvers' storage), scatter their forward
+ * projection (float atomics, or int64 fixed point in deterministic mode)
+ * and gather their backprojection (reproducible in both modes), and
  * need ny <= 524280 and the volume's xy extent inside the source circle
  * (every voxel in front of the source).  Change the projector only while no
  * call on this geometry is in flight. */
@@ -196,8 +200,9 @@ ct_status ct_project_norm2(const ct_geometry *g, const float *d_vol, float *d_si
  * must not exceed 262144, where V = nviews rounded up to a multiple of the
  * view group G = ceil(nviews / floor(65535 / ceil(nv/8))) (G = 1, V = nviews,
  * unless nviews * ceil(nv/8) > 65535); else CT_ERR_INVALID_ARG with a message
- * giving the count.  The footprint projectors need at most 1216 partials.
- * The first call on a device looks up that array's device address
+ * giving the count.  The footprint projectors need at most 1216 partials;
+ * a deterministic footprint geometry (which sums in int64 workspace) is
+ * rejected with CT_ERR_INVALID_ARG.  The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress) with the device current; make that first call before
  * any stream capture.  The address stays cached for the life of the process:
  * do not call this entry point on a device after a device reset

@@ -514,6 +514,14 @@ class Batch:
         _check(lib().ct_batch_remove(self.handle, int(job)))
         self._jobs.pop(job, None)
 
+    def cancel(self, job: int) -> torch.Tensor:
+        """Stop a job between steps, finished or not: it leaves the batch with
+        its pending update applied; returns its x (the iterate after its last
+        update)."""
+        _, _, x, host, _ = self._jobs[job]
+        self.remove(job)
+        return x.cpu() if host else x
+
     @property
     def handle(self):
         if self._h is None:

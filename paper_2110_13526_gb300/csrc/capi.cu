@@ -77,7 +77,7 @@ DeviceGuard::~DeviceGuard() {
 
 ct_status back_scratch_alloc(const ct_geometry *g, Workspace &ws, float *acc_t, BackScratch *s) {
     *s = BackScratch{};
-    if (!g->deterministic) {
+    if (!fixed_back(g)) {
         if (acc_t) {
             s->acc_t = acc_t;
             return CT_OK;
@@ -104,7 +104,7 @@ ct_status backproject_impl(const ct_geometry *g, const BackScratch &s, const flo
                            const float *w, double *partials, cudaStream_t st) {
     const ProjGeom &pg = g->pg;
     const int64_t n = g->nvox;
-    if (!g->deterministic) {
+    if (!fixed_back(g)) {
         // column-major Siddon kernels accumulate in acc_t only, and the
         // combine applies beta; the others accumulate into out itself
         const bool zfast_only = pg.proj == CT_PROJ_SIDDON && pg.cm;
@@ -401,6 +401,9 @@ ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out) {
     g->pg.proj = CT_PROJ_SIDDON;
     g->pg.sf_view = nullptr;
     g->pg.sf_ku = g->pg.sf_kv = g->pg.sf_cu = g->pg.sf_cv = g->pg.sf_oz = 0.f;
+    g->pg.sf_det = 0;
+    g->pg.sf_row_bound = 0.0;
+    g->pg.sf_ws = nullptr;
     g->d_sf = nullptr;
     g->pg.cm = cm_eligible(d, colq) ? 1 : 0;
     set_launch_order(g->pg);
@@ -532,7 +535,7 @@ ct_status ct_backproject_ex(const ct_geometry *g, const void *d_sino, int32_t si
     Workspace ws(st);
     Coef c;
     c.alpha = alpha;
-    if (g->deterministic && g->nrays > 0 && alpha != 0.f) {
+    if (fixed_back(g) && g->nrays > 0 && alpha != 0.f) {
         BackScratch bs;
         CT_TRY(back_scratch_alloc(g, ws, nullptr, &bs));
         CT_CUDA_TRY(cudaMemsetAsync(bs.q, 0, 2 * (size_t)n * sizeof(long long), st));
@@ -555,11 +558,8 @@ ct_status ct_backproject_ex(const ct_geometry *g, const void *d_sino, int32_t si
 ct_status ct_geometry_set_deterministic(ct_geometry *g, int32_t on) {
     clear_error();
     CT_TRY(check_geom(g));
-    if (on && g->pg.proj != CT_PROJ_SIDDON)
-        return set_error(CT_ERR_INVALID_ARG,
-                         "deterministic mode needs the Siddon projector (the footprint "
-                         "projectors scatter their forward projection with float atomics)");
     g->deterministic = on ? 1 : 0;
+    g->pg.sf_det = (on && g->pg.proj != CT_PROJ_SIDDON) ? 1 : 0;
     return CT_OK;
 }
 
@@ -569,9 +569,6 @@ ct_status ct_geometry_set_projector(ct_geometry *g, int32_t kind) {
     if (kind != CT_PROJ_SIDDON && kind != CT_PROJ_SF_TR && kind != CT_PROJ_SF_TT)
         return set_error(CT_ERR_INVALID_ARG, "unknown projector");
     if (kind != CT_PROJ_SIDDON) {
-        if (g->deterministic)
-            return set_error(CT_ERR_INVALID_ARG,
-                             "footprint projectors cannot run in deterministic mode");
         if (g->desc.ny > 65535 * 8)
             return set_error(CT_ERR_INVALID_ARG, "footprint projectors need ny <= 524280");
         // every voxel corner in front of the source in every view: the
@@ -609,8 +606,10 @@ ct_status ct_geometry_set_projector(ct_geometry *g, int32_t kind) {
             g->pg.sf_oz = scal[4];
         }
         g->pg.sf_view = g->d_sf;
+        g->pg.sf_row_bound = sf_row_bound(g->desc);
     }
     g->pg.proj = kind;
+    g->pg.sf_det = (g->deterministic && kind != CT_PROJ_SIDDON) ? 1 : 0;
     return CT_OK;
 }
 

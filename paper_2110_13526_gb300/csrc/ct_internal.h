@@ -70,6 +70,10 @@ struct ProjGeom {
     int proj;                // ct_projector
     const float4 *sf_view;   // footprint projectors: 2 float4 per view (sf_view_constants)
     float sf_ku, sf_kv, sf_cu, sf_cv, sf_oz;
+    int sf_det;              // footprint A sums in int64 fixed point (deterministic geometry)
+    double sf_row_bound;     // bound on one detector cell's sum of A_ij (fixed-point scale)
+    void *sf_ws;             // scratch of sf_det_ws_bytes(pg) bytes, or NULL (sf_forward then
+                             // allocates its own on the stream)
     int vgroup;              // launch order of A: views per group (set_launch_order)
     int vgroup_bt;           // launch order of A^T
     int nvb;                 // row blocks of the projector grid
@@ -231,6 +235,12 @@ ct_status launch_backward_det(const ProjGeom &pg, const float *e, const float *r
 // such that |alpha| max|e rho| bound 2^k <= 2^62.  part: vec_grid(m) floats.
 ct_status launch_det_scale(const void *e, int edt, const float *rho, int64_t m, double bound,
                            Coef c, float *part, float *scale, double *inv, cudaStream_t st);
+// The same scale for a forward projection: max|x| over the n voxels (x NULL:
+// 1) times max|rho| over the m rays (rho NULL: 1).  part: vec_grid(n) +
+// vec_grid(m) floats.
+ct_status launch_det_scale_fwd(const float *x, int64_t n, const float *rho, int64_t m,
+                               double bound, Coef c, float *part, float *scale, double *inv,
+                               cudaStream_t st);
 // out = beta out + (acc + transpose(acc_t)) inv; optional partials of (w out)^2.
 ct_status launch_combine_det(const ProjGeom &pg, float *out, float beta, const long long *acc,
                              const long long *acc_t, const double *inv, const float *w,
@@ -257,6 +267,12 @@ void sf_view_constants(const ct_geometry_desc &d, const std::vector<double> &ang
 ct_status sf_forward(const ProjGeom &pg, const float *vol, float *p, const float *rho, Coef c,
                      double *partials, cudaStream_t st);
 int64_t sf_forward_partials(const ProjGeom &pg);
+// Scratch of a fixed-point footprint forward projection (pg.sf_det): int64
+// sums of every ray, the scale and the maxima partials.
+size_t sf_det_ws_bytes(const ProjGeom &pg);
+// Bound on one detector cell's sum over voxels of A_ij for the footprint
+// projectors of geometry d (every voxel in front of the source).
+double sf_row_bound(const ct_geometry_desc &d);
 // acc += alpha (A o ...)^T (rho o e), power 1 or 2 (e NULL: e = 1), caller's layout.
 ct_status sf_backward(const ProjGeom &pg, const float *e, const float *rho, Coef c, float *acc,
                       int power, cudaStream_t st);
@@ -314,6 +330,11 @@ struct BackScratch {
     float *scale = nullptr;      // 1 float
     double *inv = nullptr;       // 1 double
 };
+// Backprojections of g sum in int64 fixed point: a deterministic geometry
+// with the Siddon projector (the footprint A^T gathers, in a fixed order).
+inline bool fixed_back(const ct_geometry *g) {
+    return g->deterministic && g->pg.proj == CT_PROJ_SIDDON;
+}
 // acc_t may be a caller buffer of nvox floats (reused between calls).
 ct_status back_scratch_alloc(const ct_geometry *g, Workspace &ws, float *acc_t, BackScratch *s);
 // Bound on one voxel's backprojected sum per unit |alpha e rho| (power 1:

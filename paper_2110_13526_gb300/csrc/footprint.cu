@@ -151,10 +151,15 @@ __device__ __forceinline__ void coef_sf(const Coef &c, float &alpha) {
 }
 
 // out[view][v][u] += alpha * rho * A x over the columns (i, j) of one view.
-template <bool HAS_RHO, bool UNIT_VOL, bool TT>
+// DET: each contribution is scaled by det_scale[0] (a power of two), rounded
+// to an integer and added to the int64 sums qacc instead, which makes the
+// result independent of the order of the additions.
+template <bool HAS_RHO, bool UNIT_VOL, bool TT, bool DET>
 __global__ void __launch_bounds__(256) k_sf_forward(ProjGeom g, const float *__restrict__ vol,
                                                     float *__restrict__ out,
-                                                    const float *__restrict__ rho, Coef cf) {
+                                                    const float *__restrict__ rho, Coef cf,
+                                                    long long *__restrict__ qacc,
+                                                    const float *__restrict__ det_scale) {
     const int i = blockIdx.x * 32 + threadIdx.x;
     const int j = blockIdx.y * 8 + threadIdx.y;
     const int view = blockIdx.z;
@@ -163,6 +168,7 @@ __global__ void __launch_bounds__(256) k_sf_forward(ProjGeom g, const float *__r
     if (!sf_column<TT>(g, view, i, j, c)) return;
     float alpha;
     coef_sf(cf, alpha);
+    const float scale = DET ? __ldg(det_scale) : 1.f;
     const size_t vbase = (size_t)view * g.nv * g.nu;
     const size_t plane = (size_t)g.nx * g.ny;
     for (int k0 = c.ku0; k0 <= c.ku1; k0 += kSfKUF) {
@@ -193,7 +199,11 @@ __global__ void __launch_bounds__(256) k_sf_forward(ProjGeom g, const float *__r
                         CT_IN_BOUNDS(k0 + q, g.nu) && CT_IN_BOUNDS(l, g.nv)) {
                         float val = base * fu[q];
                         if (HAS_RHO) val *= rho[row + k0 + q];
-                        atomicAdd(out + row + k0 + q, val);
+                        if (DET)
+                            atomicAdd(reinterpret_cast<unsigned long long *>(qacc) + row + k0 + q,
+                                      (unsigned long long)__float2ll_rn(val * scale));
+                        else
+                            atomicAdd(out + row + k0 + q, val);
                     }
                 }
             }
@@ -301,6 +311,20 @@ __global__ void __launch_bounds__(256) k_sf_count(ProjGeom g, unsigned long long
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(n, cnt);
 }
 
+// p = beta p + q inv (beta from c; beta 0: p is not read), int64 sums q of
+// a fixed-point forward projection.
+__global__ void k_sf_combine_det(float *__restrict__ p, const long long *__restrict__ q,
+                                 const double *__restrict__ inv, int64_t m, Coef c) {
+    const double s = __ldg(inv);
+    const float beta = c.dev ? (float)c.dev[1] : c.beta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float val = (float)((double)q[i] * s);
+        if (beta != 0.f) val = fmaf(beta, p[i], val);
+        p[i] = val;
+    }
+}
+
 // out = beta * out + acc (volumes in the caller's layout).
 __global__ void k_sf_axpby(float *__restrict__ out, const float *__restrict__ acc, int64_t n,
                            float beta) {
@@ -341,14 +365,29 @@ int64_t sf_forward_partials(const ProjGeom &pg) {
     return (int64_t)vec_grid((int64_t)pg.nviews * pg.nv * pg.nu);
 }
 
-ct_status sf_forward(const ProjGeom &pg, const float *vol, float *p, const float *rho, Coef c,
-                     double *partials, cudaStream_t st) {
-    const int64_t m = (int64_t)pg.nviews * pg.nv * pg.nu;
-    if (c.dev) CT_TRY(launch_scale_dev(p, m, c.dev + 1, st));
-    else CT_TRY(launch_scale(p, m, c.beta, st));
+namespace {
+// Byte offsets in the fixed-point forward scratch: int64 sums of the m rays,
+// the inverse scale (double), the scale (float), the maxima partials.
+struct SfDetLayout {
+    size_t q, inv, scale, part, bytes;
+    explicit SfDetLayout(const ProjGeom &pg) {
+        const int64_t m = (int64_t)pg.nviews * pg.nv * pg.nu;
+        const int64_t n = (int64_t)pg.nx * pg.ny * pg.nz;
+        q = 0;
+        inv = (size_t)m * sizeof(long long);
+        scale = inv + 16;
+        part = scale + 16;
+        bytes = part + (size_t)(vec_grid(n) + vec_grid(m)) * sizeof(float);
+    }
+};
+
+template <bool DET>
+ct_status sf_forward_launch(const ProjGeom &pg, const float *vol, float *p, const float *rho,
+                            Coef c, long long *qacc, const float *det_scale, cudaStream_t st) {
     const dim3 gr = sf_cols_grid(pg, pg.nviews), bl(32, 8);
     const bool tt = pg.proj == CT_PROJ_SF_TT, hr = rho != nullptr, unit = vol == nullptr;
-#define CT_SFF(HR, UV, TT_) k_sf_forward<HR, UV, TT_><<<gr, bl, 0, st>>>(pg, vol, p, rho, c)
+#define CT_SFF(HR, UV, TT_) \
+    k_sf_forward<HR, UV, TT_, DET><<<gr, bl, 0, st>>>(pg, vol, p, rho, c, qacc, det_scale)
     if (tt) {
         if (hr) { if (unit) CT_SFF(true, true, true); else CT_SFF(true, false, true); }
         else    { if (unit) CT_SFF(false, true, true); else CT_SFF(false, false, true); }
@@ -358,6 +397,57 @@ ct_status sf_forward(const ProjGeom &pg, const float *vol, float *p, const float
     }
 #undef CT_SFF
     CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+}  // namespace
+
+size_t sf_det_ws_bytes(const ProjGeom &pg) { return SfDetLayout(pg).bytes; }
+
+double sf_row_bound(const ct_geometry_desc &d) {
+    // A_ij = l_j Fbar_u Fbar_v with both cell averages of unit-height
+    // footprints at most 1, so a cell's sum is at most (voxels) * max l_j.
+    // l = |d| min(vx / |d_x|, vy / |d_y|) <= sqrt(2) max(vx, vy) |d| / |d_xy|
+    // for d = centre - source, and |d| / |d_xy| <= sqrt(1 + z^2 / r^2) with
+    // z the largest |z| of a voxel centre and r = SID - (largest xy radius of
+    // the volume's corners) the smallest distance in the xy plane.
+    double rmax = 0.0;
+    for (int cx = 0; cx < 2; ++cx)
+        for (int cy = 0; cy < 2; ++cy) {
+            const double x = (cx ? 0.5 : -0.5) * d.nx * d.vx + d.off_x;
+            const double y = (cy ? 0.5 : -0.5) * d.ny * d.vy + d.off_y;
+            rmax = std::max(rmax, std::sqrt(x * x + y * y));
+        }
+    const double r = d.sid - rmax;
+    const double z = std::fabs(d.off_z) + 0.5 * std::max(d.nz - 1, 0) * d.vz;
+    const double lmax = std::sqrt(2.0) * std::max(d.vx, d.vy) * std::sqrt(1.0 + (z * z) / (r * r));
+    // 2x slack covers the FP32 rounding of the footprint factors
+    return 2.0 * lmax * (double)d.nx * (double)d.ny * (double)std::max(d.nz, 1);
+}
+
+ct_status sf_forward(const ProjGeom &pg, const float *vol, float *p, const float *rho, Coef c,
+                     double *partials, cudaStream_t st) {
+    const int64_t m = (int64_t)pg.nviews * pg.nv * pg.nu;
+    if (!pg.sf_det) {
+        if (c.dev) CT_TRY(launch_scale_dev(p, m, c.dev + 1, st));
+        else CT_TRY(launch_scale(p, m, c.beta, st));
+        CT_TRY(sf_forward_launch<false>(pg, vol, p, rho, c, nullptr, nullptr, st));
+    } else {
+        // int64 fixed point: sums, then p = beta p + sums * 2^-k
+        const SfDetLayout lay(pg);
+        Workspace ws(st);
+        char *base = static_cast<char *>(pg.sf_ws);
+        if (!base) CT_TRY(ws.alloc(reinterpret_cast<void **>(&base), lay.bytes));
+        long long *q = reinterpret_cast<long long *>(base + lay.q);
+        double *inv = reinterpret_cast<double *>(base + lay.inv);
+        float *scale = reinterpret_cast<float *>(base + lay.scale);
+        float *part = reinterpret_cast<float *>(base + lay.part);
+        const int64_t n = (int64_t)pg.nx * pg.ny * pg.nz;
+        CT_CUDA_TRY(cudaMemsetAsync(q, 0, (size_t)m * sizeof(long long), st));
+        CT_TRY(launch_det_scale_fwd(vol, n, rho, m, pg.sf_row_bound, c, part, scale, inv, st));
+        CT_TRY(sf_forward_launch<true>(pg, vol, p, rho, c, q, scale, st));
+        k_sf_combine_det<<<vec_grid(m), kVecThreads, 0, st>>>(p, q, inv, m, c);
+        CT_CHECK_LAUNCH();
+    }
     if (partials) CT_TRY(launch_norm2(p, nullptr, m, partials, st));
     return CT_OK;
 }

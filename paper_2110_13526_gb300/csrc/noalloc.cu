@@ -65,6 +65,10 @@ extern "C" ct_status ct_project_norm2_noalloc(const ct_geometry *g, const float 
         return CT_OK;
     }
     if (!d_vol || !d_sino) return set_error(CT_ERR_INVALID_ARG, "NULL vector");
+    if (g->pg.sf_det)
+        return set_error(CT_ERR_INVALID_ARG,
+                         "ct_project_norm2_noalloc: a deterministic footprint geometry sums "
+                         "in int64 scratch of 8 bytes per ray; use ct_project_norm2");
     const int64_t np = forward_direct_partials(g->pg);
     if (np > kNoAllocMaxPartials)
         return set_error(CT_ERR_INVALID_ARG,

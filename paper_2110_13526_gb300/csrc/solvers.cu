@@ -535,7 +535,7 @@ ct_status check_opts(const ct_geometry *g, const float *b, float *x, const ct_so
 // Common state of one solve: workspace vectors, weights, timing, op counts.
 struct Solve {
     const ct_geometry *g;
-    const ProjGeom &pg;
+    ProjGeom pg;                  // g's, with the scratch of this solve's projections
     cudaStream_t st;
     Workspace ws;
     OpTimer tm;
@@ -552,6 +552,7 @@ struct Solve {
     ct_status init(int precond) {
         CT_TRY(ws.alloc(&T, (size_t)n));
         CT_TRY(back_scratch_alloc(g, ws, T, &bs));
+        if (pg.sf_det) CT_TRY(ws.alloc(&pg.sf_ws, sf_det_ws_bytes(pg)));
         int64_t np = std::max<int64_t>(forward_partials(pg), transpose_grid_count(pg));
         np = std::max<int64_t>(np, std::max(vec_grid(n), vec_grid(m)));
         CT_TRY(ws.alloc(&part, (size_t)np));
@@ -613,7 +614,7 @@ struct Solve {
     // then overwrites gout (beta 0) instead of adding to a cleared one.
     bool zfast_only() const { return pg.proj == CT_PROJ_SIDDON && pg.cm; }
     ct_status back_pre(const void *e, int edt, float *gout, Coef c) {
-        if (!g->deterministic) {
+        if (!fixed_back(g)) {
             if (!zfast_only())
                 CT_CUDA_TRY(cudaMemsetAsync(gout, 0, (size_t)n * sizeof(float), st));
             CT_CUDA_TRY(cudaMemsetAsync(T, 0, (size_t)n * sizeof(float), st));
@@ -625,7 +626,7 @@ struct Solve {
     }
     ct_status back_proj(const void *e, int edt, float *gout, Coef c) {
         CT_TRY(tm.mark(tm.back));
-        if (!g->deterministic)
+        if (!fixed_back(g))
             CT_TRY(launch_backward_typed(pg, e, edt, L, c, gout, T, 1, false, nullptr, st));
         else
             CT_TRY(launch_backward_typed(pg, e, edt, L, c, bs.q, bs.q + n, 1, true, bs.scale, st));
@@ -634,7 +635,7 @@ struct Solve {
         return CT_OK;
     }
     ct_status back_post(float *gout, const float *wnorm, double *partials) {
-        if (!g->deterministic)
+        if (!fixed_back(g))
             return launch_combine(pg, gout, T, wnorm, partials, st, zfast_only() ? 0.f : 1.f);
         return launch_combine_det(pg, gout, 0.f, bs.q, bs.q + n, bs.inv, wnorm, partials, st);
     }
@@ -649,11 +650,11 @@ struct Solve {
     ct_status back_job(const float *e, Coef c, BatchJob *b) const {
         CT_TRY(batch_job_grid(pg, true, b));
         b->in = e;
-        b->out = g->deterministic ? static_cast<void *>(bs.q + n) : static_cast<void *>(T);
+        b->out = fixed_back(g) ? static_cast<void *>(bs.q + n) : static_cast<void *>(T);
         b->rho = L;
         b->c = c;
         b->partials = nullptr;
-        b->det_scale = g->deterministic ? bs.scale : nullptr;
+        b->det_scale = fixed_back(g) ? bs.scale : nullptr;
         return CT_OK;
     }
     ct_status back(const float *e, float *gout, Coef c, const float *wnorm, double *partials) {
@@ -1351,7 +1352,7 @@ struct ct_batch {
             BatchJob bb{}, fb{};
             CT_TRY(j.back_job(&bb));
             CT_TRY(j.fwd_job(&fb));
-            (j.sv.g->deterministic ? bd : bf).push_back(bb);
+            (fixed_back(j.sv.g) ? bd : bf).push_back(bb);
             fw.push_back(fb);
         }
         auto offsets = [&](std::vector<BatchJob> &v, unsigned *total) -> ct_status {

@@ -420,12 +420,7 @@ __global__ void k_absmax_partials(const TE *__restrict__ e, const float *__restr
 // scale = 2^k with k the largest integer such that |alpha| max|e rho| * bound
 // * 2^k <= 2^62 (clamped to [-126, 126]); out[0] = scale (float), and the
 // exact inverse 2^-k goes to inv[0] (double).
-__global__ void k_det_scale(const float *__restrict__ part, int np, double bound, Coef c,
-                            float *__restrict__ out, double *__restrict__ inv) {
-    float m = 0.f;
-    for (int i = 0; i < np; ++i) m = fmaxf(m, part[i]);
-    const double alpha = c.dev ? fabs(c.dev[0]) : fabs((double)c.alpha);
-    const double top = (double)m * alpha * bound;
+__device__ void det_scale_of(double top, float *__restrict__ out, double *__restrict__ inv) {
     int k = 126;
     if (top > 0.0 && top < 1e300) {
         int ex = 0;
@@ -435,6 +430,25 @@ __global__ void k_det_scale(const float *__restrict__ part, int np, double bound
     }
     out[0] = __int_as_float((k + 127) << 23);
     inv[0] = __longlong_as_double((long long)(1023 - k) << 52);
+}
+
+__global__ void k_det_scale(const float *__restrict__ part, int np, double bound, Coef c,
+                            float *__restrict__ out, double *__restrict__ inv) {
+    float m = 0.f;
+    for (int i = 0; i < np; ++i) m = fmaxf(m, part[i]);
+    const double alpha = c.dev ? fabs(c.dev[0]) : fabs((double)c.alpha);
+    det_scale_of((double)m * alpha * bound, out, inv);
+}
+
+// Forward projection: the maxima of |x| (part[0, npx)) and |rho|
+// (part[npx, npx + npr); npr 0: rho = 1) multiply.
+__global__ void k_det_scale_fwd(const float *__restrict__ part, int npx, int npr, double bound,
+                                Coef c, float *__restrict__ out, double *__restrict__ inv) {
+    float mx = 0.f, mr = npr > 0 ? 0.f : 1.f;
+    for (int i = 0; i < npx; ++i) mx = fmaxf(mx, part[i]);
+    for (int i = 0; i < npr; ++i) mr = fmaxf(mr, part[npx + i]);
+    const double alpha = c.dev ? fabs(c.dev[0]) : fabs((double)c.alpha);
+    det_scale_of((double)mx * (double)mr * alpha * bound, out, inv);
 }
 
 // out = beta * out + (acc + transpose(acc_t)) * inv; optional partials of
@@ -491,6 +505,21 @@ ct_status launch_det_scale(const void *e, int edt, const float *rho, int64_t m, 
     }
     CT_CHECK_LAUNCH();
     k_det_scale<<<1, 1, 0, st>>>(part, gb, bound, c, scale, inv);
+    CT_CHECK_LAUNCH();
+    return CT_OK;
+}
+
+ct_status launch_det_scale_fwd(const float *x, int64_t n, const float *rho, int64_t m,
+                               double bound, Coef c, float *part, float *scale, double *inv,
+                               cudaStream_t st) {
+    const int gx = vec_grid(n), gr = rho ? vec_grid(m) : 0;
+    k_absmax_partials<<<gx, kVecThreads, 0, st>>>(x, nullptr, n, part);
+    CT_CHECK_LAUNCH();
+    if (rho) {
+        k_absmax_partials<<<gr, kVecThreads, 0, st>>>(rho, nullptr, m, part + gx);
+        CT_CHECK_LAUNCH();
+    }
+    k_det_scale_fwd<<<1, 1, 0, st>>>(part, gx, gr, bound, c, scale, inv);
     CT_CHECK_LAUNCH();
     return CT_OK;
 }

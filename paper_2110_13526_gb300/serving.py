@@ -22,6 +22,18 @@ stopping rule fires.  LSQR and reduced-storage requests keep the per-slot
 streams.  A batched job's result is that of ct_cgls alone (bitwise with a
 deterministic geometry).
 
+Cancellation: ``Server.cancel(rid)`` (from any thread while ``run`` runs),
+or ``Request.cancel_after`` seconds after arrival (a client that gives up).
+A queued request leaves the queue without running; a batched CGLS job
+leaves its batch at the next step boundary with the iterate it has; a
+per-slot CGLS solve with ``cancel_chunk = k > 0`` runs as a resumable state
+in chunks of k updates (ct_cgls_resume, bitwise the uninterrupted solve
+with a deterministic geometry) and stops at the next chunk boundary; any
+other running solve runs to its end and is marked cancelled.  Each
+cancelled request yields a Result with ``cancelled`` set (x the iterate it
+reached, or None if it never ran); latency percentiles cover the requests
+that were not cancelled.
+
 Latency of a request = completion time - arrival time.
 """
 from __future__ import annotations
@@ -34,7 +46,7 @@ from typing import Dict, List, Optional, Tuple
 import numpy as np
 import torch
 
-from . import Batch, Geometry, cgls, lsqr
+from . import Batch, CglsState, Geometry, cgls, lsqr
 
 
 @dataclass
@@ -47,17 +59,19 @@ class Request:
     max_iter: int = 50
     err_tol: float = 1e-3
     storage: str = "f32"           # CGLS Krylov-vector storage ("f32", "bf16", "f16")
+    cancel_after: Optional[float] = None   # the client cancels this long after arrival
 
 
 @dataclass
 class Result:
     rid: int
-    x: torch.Tensor
+    x: Optional[torch.Tensor]
     iterations: int
     rel_discrepancy: float
     arrival: float
     start: float
     end: float
+    cancelled: bool = False
 
     @property
     def latency(self) -> float:
@@ -68,18 +82,23 @@ def _vox(geometry: dict) -> int:
     return geometry["nx"] * geometry["ny"] * geometry["nz"]
 
 
-def footprint_bytes(geometry: dict, solver: str) -> int:
+def footprint_bytes(geometry: dict, solver: str, deterministic: bool = False) -> int:
     """Device bytes a solve holds: the library's workspace plus x.
 
     CGLS: x, z, g, transposed scratch (4 volumes) + e, p (2 sinograms);
     LSQR: x, v, w, g, transposed scratch (5 volumes) + u (1 sinogram);
-    plus per-view and per-column constants and FP64 partial sums."""
+    plus per-view and per-column constants and FP64 partial sums.  A
+    deterministic geometry adds its int64 sums: 16 bytes per voxel (Siddon
+    backprojection) or 8 bytes per ray (footprint forward projection)."""
     n = geometry["nx"] * geometry["ny"] * geometry["nz"]
     m = geometry["nviews"] * geometry["nu"] * geometry["nv"]
     vols, sinos = (4, 2) if solver == "cgls" else (5, 1)   # FP32 storage (an upper bound)
     cols = geometry["nviews"] * geometry["nu"] * 36 + geometry["nviews"] * 48
     partials = 8 * (m // 256 + n // 1024 + 4096)
-    return 4 * (vols * n + sinos * m) + cols + partials
+    det = 0
+    if deterministic:
+        det = 16 * n if geometry.get("projector", "siddon") == "siddon" else 8 * m + 4 * (n + m) // 256
+    return 4 * (vols * n + sinos * m) + cols + partials + det
 
 
 @dataclass
@@ -97,9 +116,14 @@ class ServeStats:
 class Server:
     def __init__(self, slots: int = 8, hbm_budget_bytes: float = 150e9, device=None,
                  deterministic: bool = False, batched: bool = False, batch_jobs: int = 32,
-                 batch_executors: int = 1, batch_route: str = "load"):
+                 batch_executors: int = 1, batch_route: str = "load", cancel_chunk: int = 0):
         if slots < 1:
             raise ValueError("slots must be >= 1")
+        if cancel_chunk < 0:
+            raise ValueError("cancel_chunk must be >= 0")
+        self.cancel_chunk = cancel_chunk
+        self._cancelled: set = set()
+        self._cv: Optional[threading.Condition] = None
         if batch_jobs < 1 or batch_executors < 1:
             raise ValueError("batch_jobs and batch_executors must be >= 1")
         if batch_route not in ("load", "size"):
@@ -126,10 +150,20 @@ class Server:
                 self._geoms[key] = g
             return g
 
+    def cancel(self, rid: int) -> None:
+        """Cancel request rid (queued or running) of the current or next run."""
+        cv = self._cv
+        if cv is None:
+            self._cancelled.add(rid)
+            return
+        with cv:
+            self._cancelled.add(rid)
+            cv.notify_all()
+
     def run(self, requests: List[Request]) -> ServeStats:
         reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
         for r in reqs:
-            fp = footprint_bytes(r.geometry, r.solver)
+            fp = footprint_bytes(r.geometry, r.solver, self.deterministic)
             if fp > self.budget:
                 raise ValueError("request %d needs %d bytes, budget %d" % (r.rid, fp, self.budget))
             self.geometry(r.geometry)          # geometries are built before the clock starts
@@ -139,6 +173,10 @@ class Server:
         # of one size and no small job waits for a large one's updates
         size_class = {v: c for c, v in enumerate(sorted({_vox(r.geometry) for r in reqs}))}
         cv = threading.Condition()
+        self._cv = cv
+        cancelled = self._cancelled
+        timers = sorted((r.arrival + r.cancel_after, r.rid) for r in reqs
+                        if r.cancel_after is not None)
         state = {"free_slots": self.slots, "bytes": 0, "running": 0, "max_running": 0,
                  "max_bytes": 0, "errors": [], "batch_active": 0, "batch_stop": False,
                  "batch_steps": 0}
@@ -157,7 +195,23 @@ class Server:
                 s = streams[si]
                 g = self.geometry(req.geometry)
                 with torch.cuda.stream(s):
-                    if req.solver == "cgls":
+                    if (req.solver == "cgls" and req.storage == "f32"
+                            and self.cancel_chunk > 0):
+                        # a resumable state, advanced chunk by chunk
+                        cs = CglsState(g)
+                        try:
+                            total = 0
+                            while True:
+                                total = min(total + self.cancel_chunk, req.max_iter)
+                                x, rep = cs.run(req.b, total, err_tol=req.err_tol, stream=s)
+                                if rep.iterations < total or total >= req.max_iter:
+                                    break
+                                with cv:
+                                    if req.rid in cancelled:
+                                        break
+                        finally:
+                            cs.close()
+                    elif req.solver == "cgls":
                         x, rep = cgls(g, req.b, max_iter=req.max_iter, err_tol=req.err_tol,
                                       stream=s, storage=req.storage)
                     else:
@@ -165,8 +219,10 @@ class Server:
                                       stream=s)
                     s.synchronize()
                 t_end = time.perf_counter() - t0
+                with cv:
+                    was = req.rid in cancelled
                 res = Result(req.rid, x, rep.iterations, rep.nb / rep.nb0 if rep.nb0 else 0.0,
-                             req.arrival, t_start, t_end)
+                             req.arrival, t_start, t_end, cancelled=was)
             except Exception as e:  # reported after the run
                 res = None
                 with cv:
@@ -186,7 +242,18 @@ class Server:
             another's."""
             inbox = inboxes[k]
             live = {}                                     # job id -> (request, bytes, start)
+            done_upd = {}                                 # job id -> x updates so far
             new: List[Tuple[Request, int, float]] = []    # taken from the inbox, not yet added
+
+            def leave(req, fp, res):
+                with cv:
+                    results.append(res)
+                    state["bytes"] -= fp
+                    state["batch_active"] -= 1
+                    load[k] -= 1
+                    state["running"] -= 1
+                    cv.notify_all()
+
             try:
                 torch.cuda.set_device(self.device)
                 s = torch.cuda.Stream(device=self.device)
@@ -200,28 +267,43 @@ class Server:
                                 break
                             new.extend(inbox)
                             inbox.clear()
+                        with cv:
+                            gone = {r.rid for r, _, _ in new if r.rid in cancelled}
+                            gone |= {live[j][0].rid for j in live if live[j][0].rid in cancelled}
                         while new:
-                            req = new[0][0]
+                            req, fp, t_start = new.pop(0)
+                            if req.rid in gone:               # cancelled before it ran
+                                now = time.perf_counter() - t0
+                                leave(req, fp, Result(req.rid, None, 0, float("nan"),
+                                                      req.arrival, now, now, cancelled=True))
+                                continue
                             jid = bt.add(self.geometry(req.geometry), req.b,
                                          max_iter=req.max_iter, err_tol=req.err_tol)
-                            live[jid] = new.pop(0)
-                        if any(not bt.done(j) for j in live):
+                            live[jid] = (req, fp, t_start)
+                            done_upd[jid] = 1                 # the first update runs in add
+                        for j in [j for j in live if live[j][0].rid in gone]:
+                            x = bt.cancel(j)                  # leaves between steps
+                            req, fp, t_start = live.pop(j)
+                            leave(req, fp, Result(req.rid, x, done_upd.pop(j), float("nan"),
+                                                  req.arrival, t_start,
+                                                  time.perf_counter() - t0, cancelled=True))
+                        active = [j for j in live if not bt.done(j)]
+                        if active:
                             bt.step()
+                            for j in active:
+                                done_upd[j] += 1
                             with cv:
                                 state["batch_steps"] += 1
                         for j in [j for j in live if bt.done(j)]:
                             x, rep = bt.result(j)
                             req, fp, t_start = live.pop(j)
-                            res = Result(req.rid, x, rep.iterations,
-                                         rep.nb / rep.nb0 if rep.nb0 else 0.0, req.arrival,
-                                         t_start, time.perf_counter() - t0)
+                            done_upd.pop(j, None)
                             with cv:
-                                results.append(res)
-                                state["bytes"] -= fp
-                                state["batch_active"] -= 1
-                                load[k] -= 1
-                                state["running"] -= 1
-                                cv.notify_all()
+                                was = req.rid in cancelled
+                            leave(req, fp, Result(req.rid, x, rep.iterations,
+                                                  rep.nb / rep.nb0 if rep.nb0 else 0.0,
+                                                  req.arrival, t_start,
+                                                  time.perf_counter() - t0, cancelled=was))
                     bt.close()
             except Exception as e:  # reported after the run
                 with cv:
@@ -248,9 +330,18 @@ class Server:
                 while i < len(reqs) and reqs[i].arrival <= now:
                     pending.append(reqs[i])
                     i += 1
+                # clients that give up; queued requests cancelled leave the queue
+                while timers and timers[0][0] <= now:
+                    cancelled.add(timers.pop(0)[1])
+                    cv.notify_all()
+                for r in [r for r in pending if r.rid in cancelled]:
+                    pending.remove(r)
+                    results.append(Result(r.rid, None, 0, float("nan"), r.arrival, now, now,
+                                          cancelled=True))
                 # admit in arrival order while a slot (or the batch) and the budget allow
                 while pending:
-                    fp = footprint_bytes(pending[0].geometry, pending[0].solver)
+                    fp = footprint_bytes(pending[0].geometry, pending[0].solver,
+                                         self.deterministic)
                     if state["bytes"] + fp > self.budget:
                         break
                     if (self.batched and pending[0].solver == "cgls"
@@ -289,7 +380,11 @@ class Server:
                     break
                 wait = None
                 if i < len(reqs):
-                    wait = max(0.0, reqs[i].arrival - (time.perf_counter() - t0))
+                    wait = reqs[i].arrival
+                if timers:
+                    wait = timers[0][0] if wait is None else min(wait, timers[0][0])
+                if wait is not None:
+                    wait = max(0.0, wait - (time.perf_counter() - t0))
                 cv.wait(timeout=wait if wait is not None else 0.5)
         for t in threads:
             t.join()
@@ -298,16 +393,19 @@ class Server:
             cv.notify_all()
         for t in bthreads:
             t.join()
+        self._cv = None
+        self._cancelled = set()
         wall = time.perf_counter() - t0
         if state["errors"]:
             raise RuntimeError("requests failed: %s" % state["errors"])
         results.sort(key=lambda r: r.rid)
-        lat = np.array([r.latency for r in results])
+        lat = np.array([r.latency for r in results if not r.cancelled])
         return ServeStats(results, wall, state["max_running"], state["max_bytes"],
                           iterations=sum(r.iterations for r in results),
                           p50=float(np.percentile(lat, 50)) if len(lat) else 0.0,
                           p99=float(np.percentile(lat, 99)) if len(lat) else 0.0,
-                          extra={"batch_steps": state["batch_steps"]})
+                          extra={"batch_steps": state["batch_steps"],
+                                 "cancelled": sum(r.cancelled for r in results)})
 
 
 def serving_geometry(n: int, views: int) -> dict:

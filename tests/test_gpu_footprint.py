@@ -146,11 +146,85 @@ def test_rejected_combinations(ct):
         ct.cgls(g, bd, max_iter=3, storage="bf16")
     with pytest.raises(RuntimeError, match="CT_ERR_INVALID_ARG"):
         ct.project(g, torch.zeros(g.vol_shape, device="cuda", dtype=torch.float16))
-    with pytest.raises(RuntimeError, match="CT_ERR_INVALID_ARG"):
-        ct.Geometry(**cfg, projector="sf_tt", deterministic=True)
-    gd = ct.Geometry(**cfg, deterministic=True)
-    assert ct.lib().ct_geometry_set_projector(gd.handle, 2) == 1      # CT_ERR_INVALID_ARG
     assert ct.lib().ct_geometry_set_projector(g.handle, 7) == 1       # unknown projector
     # a volume reaching the source: the footprint's depth division is undefined
     with pytest.raises(RuntimeError, match="source circle"):
         ct.Geometry(**dict(cfg, sid=12.0, sdd=40.0), projector="sf_tt")
+
+
+@pytest.mark.parametrize("kind", ["sf_tr", "sf_tt"])
+@pytest.mark.parametrize("name", ["ragged", "fine"])
+def test_deterministic_forward(ct, name, kind):
+    """Deterministic mode sums the footprint forward projection in int64 fixed
+    point: bitwise equal from call to call, within the parity bar of the
+    oracle, and within FP32 rounding of the float-atomic sums.  Either order
+    of setting the mode and the projector gives the same geometry."""
+    cfg = CASES[name]
+    og = oracle.OGeom(**cfg)
+    gf = ct.Geometry(**cfg, projector=kind)
+    gd = ct.Geometry(**cfg, projector=kind, deterministic=True)
+    g2 = ct.Geometry(**cfg)
+    assert ct.lib().ct_geometry_set_deterministic(g2.handle, 1) == 0
+    assert ct.lib().ct_geometry_set_projector(g2.handle, ct.PROJECTORS[kind]) == 0
+    k = kind[3:]
+    x = synth.random_field(gd.vol_shape, seed=60)          # signed: sums cancel
+    xd = torch.from_numpy(x).cuda()
+    want = ofp.project(og, x.astype(np.float64), k)
+    p1 = ct.project(gd, xd)
+    for _ in range(3):
+        assert torch.equal(ct.project(gd, xd), p1)
+    assert torch.equal(ct.project(g2, xd), p1)
+    assert rel(p1.cpu().numpy(), want) < TOL
+    assert rel(p1.cpu().numpy(), ct.project(gf, xd).cpu().numpy()) < 1e-6
+    # epilogue, the unit volume behind the row sums, the norm
+    o0 = torch.from_numpy(synth.random_field(gd.sino_shape, seed=61)).cuda()
+    out = o0.clone()
+    ct.project(gd, xd, out=out, alpha=-0.5, beta=2.0)
+    assert rel(out.cpu().numpy(), -0.5 * want + 2.0 * o0.cpu().numpy()) < TOL
+    out2 = o0.clone()
+    ct.project(gd, xd, out=out2, alpha=-0.5, beta=2.0)
+    assert torch.equal(out, out2)
+    wr, _ = ct.precond_weights(gd, "rowcol")
+    wr2, _ = ct.precond_weights(gd, "rowcol")
+    assert torch.equal(wr, wr2)
+    p, n2 = ct.project_norm2(gd, xd)
+    assert torch.equal(p, p1)
+    assert float(n2) == float((p1.double() ** 2).sum()) or \
+        float(n2) == pytest.approx(float((p1.double() ** 2).sum()), rel=1e-12)
+    # the backprojection gathers in both modes: the same bits
+    y = torch.from_numpy(synth.random_field(gd.sino_shape, seed=62)).cuda()
+    assert torch.equal(ct.backproject(gd, y), ct.backproject(gf, y))
+
+
+@pytest.mark.parametrize("precond", ["none", "rowcol"])
+def test_deterministic_solvers_on_footprints(ct, precond):
+    """CGLS, LSQR and a CGLS state resumed from bytes on a deterministic SF-TT
+    geometry: bitwise equal between runs, and within the solver bar of the
+    oracle."""
+    cfg = CASES["offcentre"]
+    og = oracle.OGeom(**cfg)
+    g = ct.Geometry(**cfg, projector="sf_tt", deterministic=True)
+    op = SFOperator(og, "tt")
+    x_true = synth.voxelize(synth.random_ellipsoids(5, 3, *synth.box_of(cfg),
+                                                    axis_range=(3.0, 9.0)), cfg)
+    b32 = synth.gaussian_noise(op.A(x_true.astype(np.float64)), 0.01, seed=63).astype(np.float32)
+    bd = torch.from_numpy(b32).cuda()
+    x1, r1 = ct.cgls(g, bd, max_iter=10, precond=precond)
+    x2, r2 = ct.cgls(g, bd, max_iter=10, precond=precond)
+    assert torch.equal(x1, x2) and r1.history == r2.history
+    if precond == "none":
+        ref = ocgls(op, b32.astype(np.float64), K=10)
+        assert rel(x1.cpu().numpy(), ref.x) < 1e-4
+        np.testing.assert_allclose(r1.history, ref.history, rtol=1e-4)
+    l1, _ = ct.lsqr(g, bd, max_iter=8, precond=precond)
+    l2, _ = ct.lsqr(g, bd, max_iter=8, precond=precond)
+    assert torch.equal(l1, l2)
+    s = ct.CglsState(g)
+    s.run(bd, 4, precond=precond)
+    blob = s.to_bytes()
+    s.close()
+    s2 = ct.CglsState(g)
+    s2.from_bytes(blob)
+    x10, rep = s2.run(bd, 10, precond=precond)
+    s2.close()
+    assert torch.equal(x10, x1) and rep.history == r1.history

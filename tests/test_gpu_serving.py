@@ -95,11 +95,15 @@ def test_hbm_budget_limits_admission(ct):
 
 @pytest.mark.parametrize("batched", [False, True])
 def test_deterministic_results_bitwise_equal_alone_and_in_the_mix(ct, batched):
-    """With fixed-point backprojection every solve is bitwise reproducible, so
-    a result computed among concurrent jobs equals the one computed alone --
-    also when the CGLS requests share batched projector launches."""
+    """With fixed-point sums every solve is bitwise reproducible, so a result
+    computed among concurrent jobs equals the one computed alone -- also when
+    the CGLS requests share batched projector launches, and for requests on
+    the SF-TT footprint projector, whose forward projection sums in fixed
+    point in this mode."""
     from paper_2110_13526_gb300.serving import Server
     reqs = make_requests(ct, n_req=8, rate=200.0, seed=13)
+    for r in reqs[1::3]:
+        r.geometry = dict(r.geometry, projector="sf_tt")
     stats = Server(slots=4, deterministic=True, batched=batched).run(reqs)
     assert stats.max_concurrent >= 2
     if batched:
@@ -110,3 +114,39 @@ def test_deterministic_results_bitwise_equal_alone_and_in_the_mix(ct, batched):
         x_alone, rep = fn(g, req.b, max_iter=req.max_iter, err_tol=req.err_tol)
         assert res.iterations == rep.iterations
         assert torch.equal(res.x, x_alone), req.rid
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_cancelled_requests(ct, batched):
+    """Cancellation is host logic and faults nothing: a request cancelled
+    before it runs (Server.cancel before the run, or a client that gives up
+    at arrival) yields x None and no updates; a long CGLS request cancelled
+    while it runs stops early (batched: at a step boundary; per slot: at a
+    chunk boundary of the resumable state) with x bitwise equal to ct_cgls
+    run alone for the updates it reached; every other request is bitwise
+    its solve alone."""
+    from paper_2110_13526_gb300.serving import Server
+    reqs = make_requests(ct, n_req=6, rate=1000.0, seed=17)
+    for r in reqs:
+        r.solver, r.err_tol = "cgls", 0.0
+    long_req, early, queued = reqs[0], reqs[1], reqs[-1]
+    long_req.max_iter, long_req.cancel_after = 5000, 0.2
+    early.cancel_after = 0.0
+    srv = Server(slots=2, deterministic=True, batched=batched, cancel_chunk=8)
+    srv.cancel(queued.rid)
+    stats = srv.run(reqs)
+    res = {r.rid: r for r in stats.results}
+    assert len(res) == len(reqs) and stats.extra["cancelled"] == 3
+    for r in (early, queued):
+        assert res[r.rid].cancelled and res[r.rid].x is None and res[r.rid].iterations == 0
+    lr = res[long_req.rid]
+    assert lr.cancelled and 1 <= lr.iterations < 5000 and torch.isfinite(lr.x).all()
+    g = ct.Geometry(**long_req.geometry, deterministic=True)
+    x_alone, rep = ct.cgls(g, long_req.b, max_iter=lr.iterations)
+    assert torch.equal(lr.x, x_alone)
+    for r in reqs[2:-1]:
+        assert not res[r.rid].cancelled
+        g = ct.Geometry(**r.geometry, deterministic=True)
+        x_alone, rep = ct.cgls(g, r.b, max_iter=r.max_iter)
+        assert res[r.rid].iterations == rep.iterations
+        assert torch.equal(res[r.rid].x, x_alone), r.rid

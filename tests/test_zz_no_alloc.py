@@ -106,3 +106,17 @@ def test_noalloc_rejects_geometry_beyond_static_scratch(ct):
     assert st == 1
     msg = L.ct_last_error()
     assert b"static scratch" in msg and b"262208" in msg
+
+
+def test_noalloc_rejects_deterministic_footprint_geometry(ct):
+    """A deterministic footprint geometry sums its projection in int64
+    workspace, which the allocation-free entry point cannot take."""
+    L = ct.lib()
+    g = ct.Geometry(**CFG, projector="sf_tt", deterministic=True)
+    vol = torch.zeros(g.vol_shape, device="cuda")
+    sino = torch.empty(g.sino_shape, device="cuda")
+    nrm = torch.zeros((), dtype=torch.float64, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = L.ct_project_norm2_noalloc(g.handle, _p(vol), _p(sino), ctypes.c_float(1.0),
+                                    ctypes.c_float(0.0), _p(nrm), stream)
+    assert st == 1 and b"int64" in L.ct_last_error()
