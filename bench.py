@@ -169,8 +169,8 @@ class ClockSampler:
 
 def ncu_counters(kernel: str):
     """The committed ncu counters of a projector kernel (DRAM bytes per launch,
-    L1 and L2 hit rates), or None when the kernel source changed since they
-    were taken."""
+    L1 and L2 hit rates, the fraction of issue slots busy), or None when the
+    kernel source changed since they were taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_2110_13526_gb300", "csrc", "projector.cu")
     try:
@@ -201,6 +201,7 @@ def kernel_report(kernel: str, seconds: float, nnz: int, algo_bytes: float) -> d
             "effective_gbs": algo_bytes / seconds / 1e9,
             "dram_gbs": dram / seconds / 1e9 if dram is not None else None,
             "l1_hit_rate": ent.get("l1_hit_rate"), "l2_hit_rate": ent.get("l2_hit_rate"),
+            "issue_busy": ent.get("issue_active"),
             "counters": "ncu" if ent else None}
 
 
@@ -373,6 +374,7 @@ def run_ours(a):
             "dram_gbs": dram / t_dom / 1e9 if dram is not None else None,
             "dram_frac": dram / t_dom / 1e9 / peak if dram is not None else None,
             "l1_hit_rate": ent.get("l1_hit_rate"), "l2_hit_rate": ent.get("l2_hit_rate"),
+            "issue_busy": ent.get("issue_active"),
             "kernel": kname, "peak_source": peak_kind,
             "ms_per_launch": t_dom * 1e3,
             "algorithmic_bytes_per_launch": by_dom}

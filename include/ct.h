@@ -280,16 +280,22 @@ typedef struct {
  * NULL) receives NB / NB0 after each x update, up to history_cap entries.
  * For LSQR, NB is the recurrence estimate phi_bar of the discrepancy.  With
  * preconditioning the discrepancy is the weighted one, || R^-1/2 (b - A x) ||
- * for ROWCOL. */
+ * for ROWCOL.  history_nr (HOST, caller-owned, may be NULL; history_cap
+ * entries) receives for each x update the norm of the least-squares
+ * gradient at the iterate before it (x0 for the first): ||A^T e_b||, the
+ * NR of Algorithm 1 for CGLS (computed), the Paige-Saunders estimate
+ * phi_bar alpha |c| for LSQR; with preconditioning ||W A^T L e||, with
+ * Tikhonov the regularised gradient.  SIRT leaves it untouched. */
 typedef struct {
     int32_t iterations;   /* i of Algorithm 1: x updates done               */
     double nb0, nb;       /* NB0 = ||b|| and the final NB                   */
     double *history_nb;   /* in: host array or NULL                         */
-    int32_t history_cap;  /* in: its length                                 */
+    int32_t history_cap;  /* in: its length (also of history_nr)            */
     int32_t n_forward;    /* operator calls made: A                         */
     int32_t n_back;       /* operator calls made: A^T                       */
     double ms_forward;    /* with opts.timing: total device time in A, ms   */
     double ms_back;       /* with opts.timing: total device time in A^T, ms */
+    double *history_nr;   /* in: host array or NULL (see above)             */
 } ct_solver_report;
 
 /* CGLS with delayed residual computation (Algorithm 1, with the direction

@@ -20,7 +20,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from dataclasses import dataclass
+from dataclasses import dataclass, field
 from typing import Optional, Sequence
 
 import torch
@@ -87,7 +87,7 @@ class _Report(ctypes.Structure):
                 ("nb", ctypes.c_double), ("history_nb", ctypes.POINTER(ctypes.c_double)),
                 ("history_cap", ctypes.c_int32), ("n_forward", ctypes.c_int32),
                 ("n_back", ctypes.c_int32), ("ms_forward", ctypes.c_double),
-                ("ms_back", ctypes.c_double)]
+                ("ms_back", ctypes.c_double), ("history_nr", ctypes.POINTER(ctypes.c_double))]
 
 
 @dataclass
@@ -100,6 +100,25 @@ class SolveReport:
     n_back: int
     ms_forward: float
     ms_back: float
+    # ||A^T e_b|| at the iterate before each update (CGLS: NR, computed; LSQR:
+    # the Paige-Saunders estimate); empty for SIRT
+    history_nr: list = field(default_factory=list)
+
+
+def _new_report(cap: int):
+    """A ct_solver_report with host history arrays of cap entries."""
+    cap = max(int(cap), 1)
+    hist, hist_nr = (ctypes.c_double * cap)(), (ctypes.c_double * cap)()
+    dp = ctypes.POINTER(ctypes.c_double)
+    rep = _Report(0, 0.0, 0.0, ctypes.cast(hist, dp), cap, 0, 0, 0.0, 0.0,
+                  ctypes.cast(hist_nr, dp))
+    return rep, hist, hist_nr
+
+
+def _solve_report(rep, hist, hist_nr, with_nr: bool = True) -> "SolveReport":
+    k = rep.iterations
+    return SolveReport(k, rep.nb0, rep.nb, list(hist[:k]), rep.n_forward, rep.n_back,
+                       rep.ms_forward, rep.ms_back, list(hist_nr[:k]) if with_nr else [])
 
 
 _lib = None
@@ -421,14 +440,10 @@ def _solve(fn, g: Geometry, b, x0, max_iter, err_tol, precond, recompute_every, 
     opts = SolverOpts(int(max_iter), float(err_tol), _PRECOND[precond], float(tikhonov),
                       int(recompute_every), 1 if timing else 0,
                       DTYPES[_torch_dtype(storage)])
-    hist = (ctypes.c_double * int(max_iter))()
-    rep = _Report(0, 0.0, 0.0, ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)),
-                  int(max_iter), 0, 0, 0.0, 0.0)
+    rep, hist, hist_nr = _new_report(max_iter)
     _check(fn(g.handle, _ptr(bd), _ptr(x), ctypes.byref(opts), ctypes.byref(rep),
               _stream(stream)))
-    r = SolveReport(rep.iterations, rep.nb0, rep.nb, list(hist[:rep.iterations]),
-                    rep.n_forward, rep.n_back, rep.ms_forward, rep.ms_back)
-    return (x.cpu() if host else x), r
+    return (x.cpu() if host else x), _solve_report(rep, hist, hist_nr)
 
 
 def cgls(g: Geometry, b: torch.Tensor, x0: Optional[torch.Tensor] = None, max_iter: int = 20,
@@ -497,15 +512,12 @@ class Batch:
         """(x, SolveReport) of a finished job (None while it runs); by default
         the job then leaves the batch."""
         _, _, x, host, k = self._jobs[job]
-        hist = (ctypes.c_double * max(k, 1))()
-        rep = _Report(0, 0.0, 0.0, ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)),
-                      max(k, 1), 0, 0, 0.0, 0.0)
+        rep, hist, hist_nr = _new_report(k)
         d = ctypes.c_int32(0)
         _check(lib().ct_batch_poll(self.handle, int(job), ctypes.byref(d), ctypes.byref(rep)))
         if not d.value:
             return None
-        r = SolveReport(rep.iterations, rep.nb0, rep.nb, list(hist[:rep.iterations]),
-                        rep.n_forward, rep.n_back, rep.ms_forward, rep.ms_back)
+        r = _solve_report(rep, hist, hist_nr)
         if remove:
             self.remove(job)
         return (x.cpu() if host else x), r
@@ -555,14 +567,10 @@ def sirt(g: Geometry, b: torch.Tensor, x0: Optional[torch.Tensor] = None, max_it
     else:
         x = _dev(x0, g.vol_shape, "x0", g.device).clone()
     opts = SirtOpts(int(max_iter), float(err_tol), float(relax), 1 if timing else 0)
-    hist = (ctypes.c_double * max(int(max_iter), 1))()
-    rep = _Report(0, 0.0, 0.0, ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)),
-                  max(int(max_iter), 1), 0, 0, 0.0, 0.0)
+    rep, hist, hist_nr = _new_report(max_iter)
     _check(lib().ct_sirt(g.handle, _ptr(bd), _ptr(x), ctypes.byref(opts), ctypes.byref(rep),
                          _stream(stream)))
-    r = SolveReport(rep.iterations, rep.nb0, rep.nb, list(hist[:rep.iterations]),
-                    rep.n_forward, rep.n_back, rep.ms_forward, rep.ms_back)
-    return (x.cpu() if host else x), r
+    return (x.cpu() if host else x), _solve_report(rep, hist, hist_nr, with_nr=False)
 
 
 class CglsState:
@@ -594,15 +602,10 @@ class CglsState:
              else _dev(x0, g.vol_shape, "x0", g.device).clone())
         opts = SolverOpts(int(max_iter), float(err_tol), _PRECOND[precond], float(tikhonov), 0, 0,
                           DTYPES[torch.float32])
-        cap = max(int(max_iter), 1)
-        hist = (ctypes.c_double * cap)()
-        rep = _Report(0, 0.0, 0.0, ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)), cap, 0, 0,
-                      0.0, 0.0)
+        rep, hist, hist_nr = _new_report(max_iter)
         _check(lib().ct_cgls_resume(g.handle, _ptr(bd), _ptr(x), ctypes.byref(opts),
                                     ctypes.byref(rep), self._h, _stream(stream)))
-        r = SolveReport(rep.iterations, rep.nb0, rep.nb, list(hist[:rep.iterations]),
-                        rep.n_forward, rep.n_back, rep.ms_forward, rep.ms_back)
-        return (x.cpu() if host else x), r
+        return (x.cpu() if host else x), _solve_report(rep, hist, hist_nr)
 
     def to_bytes(self) -> bytes:
         n = ctypes.c_int64()

@@ -433,6 +433,7 @@ ct_status ct_geometry_sizes(const ct_geometry *g, int64_t *n_vox, int64_t *n_ray
 
 ct_status ct_project(const ct_geometry *g, const float *d_vol, float *d_sino, float alpha,
                      float beta, void *stream) {
+    CT_TRACE("ct_project");
     clear_error();
     CT_TRY(check_geom(g));
     if (g->nrays == 0) return CT_OK;
@@ -452,6 +453,7 @@ ct_status ct_project(const ct_geometry *g, const float *d_vol, float *d_sino, fl
 
 ct_status ct_project_norm2(const ct_geometry *g, const float *d_vol, float *d_sino, float alpha,
                            float beta, double *d_norm2, void *stream) {
+    CT_TRACE("ct_project_norm2");
     clear_error();
     CT_TRY(check_geom(g));
     if (!d_norm2) return set_error(CT_ERR_INVALID_ARG, "d_norm2 is NULL");
@@ -481,6 +483,7 @@ ct_status ct_project_norm2(const ct_geometry *g, const float *d_vol, float *d_si
 
 ct_status ct_backproject(const ct_geometry *g, const float *d_sino, float *d_vol, float alpha,
                          float beta, void *stream) {
+    CT_TRACE("ct_backproject");
     clear_error();
     CT_TRY(check_geom(g));
     if (!d_vol) return set_error(CT_ERR_INVALID_ARG, "NULL vector");
@@ -499,6 +502,7 @@ ct_status ct_backproject(const ct_geometry *g, const float *d_sino, float *d_vol
 
 ct_status ct_project_ex(const ct_geometry *g, const void *d_vol, int32_t vol_dtype, void *d_sino,
                         int32_t sino_dtype, float alpha, float beta, void *stream) {
+    CT_TRACE("ct_project_ex");
     clear_error();
     CT_TRY(check_geom(g));
     if (dtype_size(vol_dtype) == 0 || dtype_size(sino_dtype) == 0)
@@ -522,6 +526,7 @@ ct_status ct_project_ex(const ct_geometry *g, const void *d_vol, int32_t vol_dty
 ct_status ct_backproject_ex(const ct_geometry *g, const void *d_sino, int32_t sino_dtype,
                             void *d_vol, int32_t vol_dtype, float alpha, float beta,
                             void *stream) {
+    CT_TRACE("ct_backproject_ex");
     clear_error();
     CT_TRY(check_geom(g));
     if (dtype_size(vol_dtype) == 0 || dtype_size(sino_dtype) == 0)
@@ -637,6 +642,7 @@ int32_t ct_debug_bounds_build(void) {
 }
 
 ct_status ct_count_nnz(const ct_geometry *g, int64_t *out, void *stream) {
+    CT_TRACE("ct_count_nnz");
     clear_error();
     CT_TRY(check_geom(g));
     if (!out) return set_error(CT_ERR_INVALID_ARG, "out is NULL");
@@ -656,6 +662,7 @@ ct_status ct_count_nnz(const ct_geometry *g, int64_t *out, void *stream) {
 
 ct_status ct_precond_weights(const ct_geometry *g, int32_t kind, float *d_vol_w, float *d_sino_w,
                              void *stream) {
+    CT_TRACE("ct_precond_weights");
     clear_error();
     CT_TRY(check_geom(g));
     if (kind != CT_PRECOND_JACOBI && kind != CT_PRECOND_ROWCOL)

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -133,6 +134,20 @@ void note_launches(long long n);
         ::ct::note_launch();                            \
         CT_CUDA_TRY(cudaGetLastError());                \
     } while (0)
+
+// ---- tracing ------------------------------------------------------------------
+// An NVTX range named after a C-ABI call, open for the call's host-side
+// duration (the enqueue, and the wait of the blocking calls).  Nsight tools
+// attached to the process show it (ncu can filter kernels by it with
+// --nvtx --nvtx-include); without a tool it costs a pointer check.
+class TraceRange {
+public:
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+#define CT_TRACE(name) ::ct::TraceRange ct_trace_range_(name)
 
 // ---- stream-ordered device workspace ---------------------------------------
 // Allocations are freed on the same stream when the Workspace goes out of

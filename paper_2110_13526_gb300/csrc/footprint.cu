@@ -21,11 +21,13 @@
 // computes the transaxial footprint once and walks the column in z, adding
 // its contributions to the detector cells with float reductions (the 32
 // lanes of a warp are 32 neighbouring columns, whose footprints are
-// neighbouring cells).  A^T gathers: one thread per column segment of kSfZB
-// voxels loops over all views and sums the cells under each voxel's
+// neighbouring cells); in deterministic mode the contributions are added as
+// int64 fixed point instead.  A^T gathers: one thread per column segment of
+// kSfZB voxels loops over all views and sums the cells under each voxel's
 // footprint into shared memory, so every voxel is written once, without
-// reductions, and the transaxial footprint of a column is computed once per
-// view and segment.
+// reductions; the transaxial footprint of a column and the u-weighted sums
+// of the detector rows under the segment are computed once per view and
+// segment.  Ramp reciprocals are taken once per trapezoid, not per cell.
 // Coordinates are relative to the volume centre (per-view constants computed
 // in FP64 on the host), which keeps the FP32 breakpoints accurate.
 #include "ct_debug.cuh"
@@ -39,14 +41,16 @@ namespace ct {
 namespace {
 
 // Transaxial cells kept in registers per pass (footprints wider than that
-// take several passes): A 4, A^T 8 (measured at 256^3, 1 mm voxels and
+// take several passes), in A and A^T (measured at 256^3, 1 mm voxels and
 // pixels, magnification 1.6: footprints of 2-4 cells).
 constexpr int kSfKUF = 4;
-constexpr int kSfZB = 16;  // voxels per A^T thread (a column segment; sums in shared memory)
+constexpr int kSfZB = 16;    // voxels per A^T thread (a column segment; sums in shared memory)
+constexpr int kSfRows = 32;  // detector rows under one A^T segment kept in shared memory
 
 struct SfColumn {
     float tau[4];          // sorted transaxial breakpoints (pixel index units)
     float qa, qb;          // SDD / (dv t) at the two axial depths (TR: both the centre's)
+    float r01, r23;        // 1 / (2 ramp width) of the transaxial trapezoid
     float m;               // min(hx / |d_x|, hy / |d_y|)
     float dxy2;            // d_x^2 + d_y^2
     int ku0, ku1;          // cells overlapping the footprint, clipped to the detector
@@ -68,19 +72,25 @@ __device__ __forceinline__ void sort4(float &a, float &b, float &c, float &d) {
 #undef CT_CSWAP
 }
 
+// 1 / (2 w): the factor of a ramp of width w in trap_cell, taken once per
+// trapezoid (a zero width gives infinity, which trap_cell never reaches: an
+// empty ramp has no overlap with any cell).
+__device__ __forceinline__ float half_rcp(float w) { return 0.5f / w; }
+
 // Integral of the unit trapezoid t0 <= t1 <= t2 <= t3 over [a, b], summed
-// piece by piece (no difference of large antiderivatives).
-__device__ __forceinline__ float trap_cell(float t0, float t1, float t2, float t3, float a,
-                                           float b) {
+// piece by piece (no difference of large antiderivatives); r01 and r23 are
+// half_rcp of the two ramp widths.
+__device__ __forceinline__ float trap_cell(float t0, float t1, float t2, float t3, float r01,
+                                           float r23, float a, float b) {
     float r = 0.f;
     float x1 = fmaxf(a, t0), x2 = fminf(b, t1);
-    if (x2 > x1) r += (x2 - x1) * (x2 + x1 - 2.f * t0) / (2.f * (t1 - t0));
+    if (x2 > x1) r += (x2 - x1) * (x2 + x1 - 2.f * t0) * r01;
     x1 = fmaxf(a, t1);
     x2 = fminf(b, t2);
     if (x2 > x1) r += x2 - x1;
     x1 = fmaxf(a, t2);
     x2 = fminf(b, t3);
-    if (x2 > x1) r += (x2 - x1) * (2.f * t3 - x1 - x2) / (2.f * (t3 - t2));
+    if (x2 > x1) r += (x2 - x1) * (2.f * t3 - x1 - x2) * r23;
     return r;
 }
 
@@ -106,6 +116,8 @@ __device__ __forceinline__ bool sf_column(const ProjGeom &g, int view, int i, in
     c.tau[2] = u[2];
     c.tau[3] = u[3];
     sort4(c.tau[0], c.tau[1], c.tau[2], c.tau[3]);
+    c.r01 = half_rcp(c.tau[1] - c.tau[0]);
+    c.r23 = half_rcp(c.tau[3] - c.tau[2]);
     if (TT) {
         const float tmin = fminf(fminf(t[0], t[1]), fminf(t[2], t[3]));
         const float tmax = fmaxf(fmaxf(t[0], t[1]), fmaxf(t[2], t[3]));
@@ -125,10 +137,11 @@ __device__ __forceinline__ bool sf_column(const ProjGeom &g, int view, int i, in
     return c.ku0 <= c.ku1;
 }
 
-// Axial footprint and amplitude of voxel k of the column.
+// Axial footprint (breakpoints vb, half_rcp of its ramps) and amplitude of
+// voxel k of the column.
 template <bool TT>
 __device__ __forceinline__ void sf_axial(const ProjGeom &g, const SfColumn &c, int k, float *vb,
-                                         float &amp) {
+                                         float &amp, float &r01, float &r23) {
     const float rz = ((float)k - 0.5f * (float)(g.nz - 1)) * g.hz;
     const float z = g.sf_oz + rz;
     const float zlo = z - 0.5f * g.hz, zhi = z + 0.5f * g.hz;
@@ -138,10 +151,13 @@ __device__ __forceinline__ void sf_axial(const ProjGeom &g, const SfColumn &c, i
         vb[2] = fmaf(zhi, c.qa, g.sf_cv);
         vb[3] = fmaf(zhi, c.qb, g.sf_cv);
         sort4(vb[0], vb[1], vb[2], vb[3]);
+        r01 = half_rcp(vb[1] - vb[0]);
+        r23 = half_rcp(vb[3] - vb[2]);
     } else {
         const float p = fmaf(zlo, c.qa, g.sf_cv), q = fmaf(zhi, c.qa, g.sf_cv);
         vb[0] = vb[1] = fminf(p, q);
         vb[2] = vb[3] = fmaxf(p, q);
+        r01 = r23 = 0.f;
     }
     amp = c.m * sqrtf(fmaf(z, z, c.dxy2));
 }
@@ -176,20 +192,20 @@ __global__ void __launch_bounds__(256) k_sf_forward(ProjGeom g, const float *__r
         const int nk = min(kSfKUF, c.ku1 - k0 + 1);
 #pragma unroll
         for (int q = 0; q < kSfKUF; ++q)
-            fu[q] = q < nk ? trap_cell(c.tau[0], c.tau[1], c.tau[2], c.tau[3],
+            fu[q] = q < nk ? trap_cell(c.tau[0], c.tau[1], c.tau[2], c.tau[3], c.r01, c.r23,
                                        (float)(k0 + q) - 0.5f, (float)(k0 + q) + 0.5f)
                            : 0.f;
         for (int k = 0; k < g.nz; ++k) {
             const size_t vi = (size_t)k * plane + (size_t)j * g.nx + i;
             const float xv = UNIT_VOL || !CT_IN_BOUNDS(vi, plane * g.nz) ? 1.f : vol[vi];
             if (xv == 0.f) continue;
-            float vb[4], amp;
-            sf_axial<TT>(g, c, k, vb, amp);
+            float vb[4], amp, vr01, vr23;
+            sf_axial<TT>(g, c, k, vb, amp, vr01, vr23);
             const int kv0 = max(0, (int)floorf(vb[0] + 0.5f));
             const int kv1 = min(g.nv - 1, (int)floorf(vb[3] + 0.5f));
             for (int l = kv0; l <= kv1; ++l) {
-                const float fv = trap_cell(vb[0], vb[1], vb[2], vb[3], (float)l - 0.5f,
-                                           (float)l + 0.5f);
+                const float fv = trap_cell(vb[0], vb[1], vb[2], vb[3], vr01, vr23,
+                                           (float)l - 0.5f, (float)l + 0.5f);
                 if (fv == 0.f) continue;
                 const float base = alpha * amp * fv * xv;
                 const size_t row = vbase + (size_t)l * g.nu;
@@ -215,12 +231,15 @@ __global__ void __launch_bounds__(256) k_sf_forward(ProjGeom g, const float *__r
 // (e == NULL: e = 1).  A CTA covers 32 x 8 voxel columns and kSfZB voxels of
 // each column, one thread per column, with its kSfZB sums in shared memory:
 // the transaxial footprint of a column and view is computed once for the
-// whole segment, in passes of kSfKUF cells kept in registers.
+// whole segment, in passes of kSfKUF cells kept in registers, and so is the
+// u-weighted sum of each detector row under the segment (up to kSfRows rows
+// in shared memory; a segment spanning more rows sums them per voxel).
 template <bool HAS_RHO, int POWER, bool TT>
 __global__ void __launch_bounds__(256) k_sf_backward(ProjGeom g, const float *__restrict__ e,
                                                      const float *__restrict__ rho, Coef cf,
                                                      float *__restrict__ acc) {
     __shared__ float sacc[kSfZB][256];
+    __shared__ float srow[kSfRows][256];
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int i = blockIdx.x * 32 + threadIdx.x;
     const int j = blockIdx.y * 8 + threadIdx.y;
@@ -238,30 +257,46 @@ __global__ void __launch_bounds__(256) k_sf_backward(ProjGeom g, const float *__
                 const int nk = min(kSfKUF, c.ku1 - k0 + 1);
 #pragma unroll
                 for (int q = 0; q < kSfKUF; ++q)
-                    fu[q] = q < nk ? trap_cell(c.tau[0], c.tau[1], c.tau[2], c.tau[3],
-                                               (float)(k0 + q) - 0.5f, (float)(k0 + q) + 0.5f)
+                    fu[q] = q < nk ? trap_cell(c.tau[0], c.tau[1], c.tau[2], c.tau[3], c.r01,
+                                               c.r23, (float)(k0 + q) - 0.5f,
+                                               (float)(k0 + q) + 0.5f)
                                    : 0.f;
+                auto row_sum = [&](int l) -> float {
+                    const size_t row = vbase + (size_t)l * g.nu + k0;
+                    float su = 0.f;
+#pragma unroll
+                    for (int q = 0; q < kSfKUF; ++q) {
+                        if (q < nk && fu[q] != 0.f &&
+                            CT_IN_BOUNDS(k0 + q, g.nu) && CT_IN_BOUNDS(l, g.nv)) {
+                            float w = e ? e[row + q] : 1.f;
+                            if (HAS_RHO) w *= rho[row + q];
+                            su = POWER == 1 ? fmaf(fu[q], w, su) : fmaf(fu[q] * fu[q], w, su);
+                        }
+                    }
+                    return su;
+                };
+                // rows under the segment (v grows with z): their u-weighted
+                // sums once each, shared by the voxels above them
+                float vb[4], amp, vr01, vr23;
+                sf_axial<TT>(g, c, kz0, vb, amp, vr01, vr23);
+                const int lf = max(0, (int)floorf(vb[0] + 0.5f));
+                sf_axial<TT>(g, c, kz0 + nzs - 1, vb, amp, vr01, vr23);
+                const int ll = min(g.nv - 1, (int)floorf(vb[3] + 0.5f));
+                const bool cached = ll - lf < kSfRows;
+                if (cached)
+                    for (int l = lf; l <= ll; ++l) srow[l - lf][tid] = row_sum(l);
                 for (int dz = 0; dz < nzs; ++dz) {
-                    float vb[4], amp;
-                    sf_axial<TT>(g, c, kz0 + dz, vb, amp);
+                    sf_axial<TT>(g, c, kz0 + dz, vb, amp, vr01, vr23);
                     const int kv0 = max(0, (int)floorf(vb[0] + 0.5f));
                     const int kv1 = min(g.nv - 1, (int)floorf(vb[3] + 0.5f));
                     float s = 0.f;
                     for (int l = kv0; l <= kv1; ++l) {
-                        const float fv = trap_cell(vb[0], vb[1], vb[2], vb[3], (float)l - 0.5f,
-                                                   (float)l + 0.5f);
+                        const float fv = trap_cell(vb[0], vb[1], vb[2], vb[3], vr01, vr23,
+                                                   (float)l - 0.5f, (float)l + 0.5f);
                         if (fv == 0.f) continue;
-                        const size_t row = vbase + (size_t)l * g.nu + k0;
-                        float su = 0.f;
-#pragma unroll
-                        for (int q = 0; q < kSfKUF; ++q) {
-                            if (q < nk && fu[q] != 0.f &&
-                                CT_IN_BOUNDS(k0 + q, g.nu) && CT_IN_BOUNDS(l, g.nv)) {
-                                float w = e ? e[row + q] : 1.f;
-                                if (HAS_RHO) w *= rho[row + q];
-                                su = POWER == 1 ? fmaf(fu[q], w, su) : fmaf(fu[q] * fu[q], w, su);
-                            }
-                        }
+                        const unsigned r = (unsigned)(l - lf);
+                        const float su =
+                            cached && r < (unsigned)kSfRows ? srow[r][tid] : row_sum(l);
                         s = POWER == 1 ? fmaf(fv, su, s) : fmaf(fv * fv, su, s);
                     }
                     if (s != 0.f)
@@ -292,16 +327,16 @@ __global__ void __launch_bounds__(256) k_sf_count(ProjGeom g, unsigned long long
         if (sf_column<TT>(g, view, i, j, c)) {
             int nu_nz = 0;
             for (int k = c.ku0; k <= c.ku1; ++k)
-                nu_nz += trap_cell(c.tau[0], c.tau[1], c.tau[2], c.tau[3], (float)k - 0.5f,
-                                   (float)k + 0.5f) > 0.f;
+                nu_nz += trap_cell(c.tau[0], c.tau[1], c.tau[2], c.tau[3], c.r01, c.r23,
+                                   (float)k - 0.5f, (float)k + 0.5f) > 0.f;
             for (int k = 0; k < g.nz; ++k) {
-                float vb[4], amp;
-                sf_axial<TT>(g, c, k, vb, amp);
+                float vb[4], amp, vr01, vr23;
+                sf_axial<TT>(g, c, k, vb, amp, vr01, vr23);
                 const int kv0 = max(0, (int)floorf(vb[0] + 0.5f));
                 const int kv1 = min(g.nv - 1, (int)floorf(vb[3] + 0.5f));
                 int nv_nz = 0;
                 for (int l = kv0; l <= kv1; ++l)
-                    nv_nz += trap_cell(vb[0], vb[1], vb[2], vb[3], (float)l - 0.5f,
+                    nv_nz += trap_cell(vb[0], vb[1], vb[2], vb[3], vr01, vr23, (float)l - 0.5f,
                                        (float)l + 0.5f) > 0.f;
                 cnt += (unsigned long long)(nu_nz * nv_nz);
             }

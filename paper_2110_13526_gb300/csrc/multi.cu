@@ -48,6 +48,7 @@ ct_status run_jobs(std::vector<BatchJob> &jobs, bool backward, Workspace &ws, cu
 
 extern "C" ct_status ct_project_batch(const ct_geometry *g, const float *d_vols, float *d_sinos,
                                       int32_t nbatch, float alpha, float beta, void *stream) {
+    CT_TRACE("ct_project_batch");
     clear_error();
     CT_TRY(check_batch(g, nbatch, d_vols, d_sinos));
     if (nbatch == 0 || g->nrays == 0) return CT_OK;
@@ -83,6 +84,7 @@ extern "C" ct_status ct_project_batch(const ct_geometry *g, const float *d_vols,
 extern "C" ct_status ct_backproject_batch(const ct_geometry *g, const float *d_sinos,
                                           float *d_vols, int32_t nbatch, float alpha, float beta,
                                           void *stream) {
+    CT_TRACE("ct_backproject_batch");
     clear_error();
     if (!g) return set_error(CT_ERR_INVALID_ARG, "geometry is NULL");
     if (nbatch < 0) return set_error(CT_ERR_INVALID_ARG, "nbatch must be >= 0");

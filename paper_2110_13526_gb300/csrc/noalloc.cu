@@ -54,6 +54,7 @@ using namespace ct;
 extern "C" ct_status ct_project_norm2_noalloc(const ct_geometry *g, const float *d_vol,
                                               float *d_sino, float alpha, float beta,
                                               double *d_norm2, void *stream) {
+    CT_TRACE("ct_project_norm2_noalloc");
     clear_error();
     if (!g) return set_error(CT_ERR_INVALID_ARG, "geometry is NULL");
     if (!d_norm2) return set_error(CT_ERR_INVALID_ARG, "d_norm2 is NULL");

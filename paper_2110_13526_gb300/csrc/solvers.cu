@@ -92,7 +92,8 @@ struct CglsCkpt {
     int64_t n = 0, m = 0;
     float *x = nullptr, *z = nullptr, *e = nullptr;
     CglsS *s = nullptr;
-    std::vector<double> hist;
+    std::vector<double> hist;      // NB / NB0 after each update
+    std::vector<double> hist_nr;   // ||r_x|| before each update
     int i = 0;   // updates done
 };
 
@@ -335,15 +336,18 @@ __global__ void __launch_bounds__(1024) k_cgls_np2(const double *__restrict__ p,
     }
 }
 
-// NB = ||e_b||; history[i] = NB / NB0.
+// NB = ||e_b||; history[i] = NB / NB0 and (hist_nr not NULL) hist_nr[i] =
+// NR = ||r_x|| of the update, the gradient norm at the iterate before it.
 __global__ void __launch_bounds__(1024) k_cgls_nb(const double *__restrict__ p, int64_t n,
-                                                  CglsS *S, double *hist, int i) {
+                                                  CglsS *S, double *hist, int i,
+                                                  double *hist_nr) {
     __shared__ double sh[32];
     const double t = sum_partials(p, n, sh);
     if (threadIdx.x == 0) {
         S->nb = sqrt(t);
         const int k = i >= 0 ? i : S->it++;   // i < 0: the slot counter on the device
         hist[k] = safe_div(S->nb, S->nb0);
+        if (hist_nr) hist_nr[k] = sqrt(S->nr2_old);
     }
 }
 
@@ -368,6 +372,7 @@ __global__ void k_sirt_update(float *__restrict__ x, const float *__restrict__ g
 // ---- LSQR ------------------------------------------------------------------
 struct LsqrS {
     double nb0, alpha, beta, inv_beta, inv_alpha, rhobar, phibar, x_step, w_step, tmp;
+    double nrb;           // ||A^T r|| estimate at the current iterate (phibar alpha |c|)
     double coef_fwd[2];   // projector epilogue: u = 1 * L A t - alpha / beta_old * u
     double coef_back[2];  // backprojector scale: 1 / beta
     int it;               // next history slot (k_lsqr_rot with i < 0)
@@ -403,6 +408,7 @@ __global__ void __launch_bounds__(1024) k_lsqr_alpha0(const double *__restrict__
         S->inv_alpha = safe_div(1.0, S->alpha);
         S->rhobar = S->alpha;
         S->phibar = S->beta;
+        S->nrb = S->alpha * S->beta;   // ||A^T r_0|| = alpha_1 beta_1
     }
 }
 
@@ -445,9 +451,12 @@ __global__ void k_lsqr_v(float *__restrict__ v, const float *__restrict__ g,
 }
 
 // Plane rotation of the bidiagonal (Paige & Saunders): rho, c, s, theta,
-// rhobar, phi, phibar; history[i] = phibar / NB0.
+// rhobar, phi, phibar; history[i] = phibar / NB0, hist_nr[i] = the estimate
+// of ||A^T r|| before this update, and the estimate after it,
+// phibar_{k+1} alpha_{k+1} |c_k|, is kept for the next one.
 __global__ void __launch_bounds__(1024) k_lsqr_rot(const double *__restrict__ p, int64_t n,
-                                                   LsqrS *S, double *hist, int i) {
+                                                   LsqrS *S, double *hist, int i,
+                                                   double *hist_nr) {
     __shared__ double sh[32];
     const double t = sum_partials(p, n, sh);
     if (threadIdx.x == 0) {
@@ -466,6 +475,8 @@ __global__ void __launch_bounds__(1024) k_lsqr_rot(const double *__restrict__ p,
         S->inv_alpha = safe_div(1.0, alpha);
         const int k = i >= 0 ? i : S->it++;   // i < 0: the slot counter on the device
         hist[k] = safe_div(S->phibar, S->nb0);
+        if (hist_nr) hist_nr[k] = S->nrb;
+        S->nrb = S->phibar * alpha * fabs(c);
     }
 }
 
@@ -688,7 +699,8 @@ struct Solve {
         *out = (h != 0.0);
         return CT_OK;
     }
-    void report(ct_solver_report *r, int iters, double nb0, double nb, const std::vector<double> &h) {
+    void report(ct_solver_report *r, int iters, double nb0, double nb, const std::vector<double> &h,
+                const std::vector<double> *h_nr = nullptr) {
         if (!r) return;
         r->iterations = iters;
         r->nb0 = nb0;
@@ -700,6 +712,10 @@ struct Solve {
         if (r->history_nb && r->history_cap > 0) {
             const int k = std::min<int>(iters, r->history_cap);
             for (int j = 0; j < k; ++j) r->history_nb[j] = h[(size_t)j];
+        }
+        if (r->history_nr && h_nr && r->history_cap > 0) {
+            const int k = std::min<int>(std::min<int>(iters, r->history_cap), (int)h_nr->size());
+            for (int j = 0; j < k; ++j) r->history_nr[j] = (*h_nr)[(size_t)j];
         }
     }
 };
@@ -861,7 +877,7 @@ struct CglsJob {
     }
     // NB = ||e_b|| into S and the history
     ct_status finish() {
-        k_cgls_nb<<<1, 1024, 0, sv.st>>>(sv.part, gm, S, hist, -1);
+        k_cgls_nb<<<1, 1024, 0, sv.st>>>(sv.part, gm, S, hist, -1, hist + K);
         CT_CHECK_LAUNCH();
         return CT_OK;
     }
@@ -909,7 +925,7 @@ struct CglsJob {
         CT_TRY(sv.ws.alloc(&e, (size_t)std::max<int64_t>(m, 1)));
         CT_TRY(sv.ws.alloc(&p, (size_t)std::max<int64_t>(m, 1)));
         CT_TRY(sv.ws.alloc(&S, 1));
-        CT_TRY(sv.ws.alloc(&hist, (size_t)K));
+        CT_TRY(sv.ws.alloc(&hist, 2 * (size_t)K));   // NB / NB0, then NR, per update
         CT_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(CglsS), st));
         // Tikhonov regularisation (Software section): minimise
         // ||L (A x - b)||^2 + lam ||x||^2, Algorithm 1 on [L A W; sqrt(lam) W]
@@ -951,9 +967,12 @@ struct CglsJob {
         if (m > 0) CT_CUDA_TRY(cudaMemcpyAsync(e, c.e, mb, cudaMemcpyDeviceToDevice, st));
         CT_CUDA_TRY(cudaMemcpyAsync(S, c.s, sizeof(CglsS), cudaMemcpyDeviceToDevice, st));
         const int keep = std::min(c.i, K);
-        if (keep > 0)
+        if (keep > 0) {
             CT_CUDA_TRY(cudaMemcpyAsync(hist, c.hist.data(), sizeof(double) * (size_t)keep,
                                         cudaMemcpyHostToDevice, st));
+            CT_CUDA_TRY(cudaMemcpyAsync(hist + K, c.hist_nr.data(), sizeof(double) * (size_t)keep,
+                                        cudaMemcpyHostToDevice, st));
+        }
         i = c.i;
         return CT_OK;
     }
@@ -967,9 +986,13 @@ struct CglsJob {
         if (m > 0) CT_CUDA_TRY(cudaMemcpyAsync(c.e, e, mb, cudaMemcpyDeviceToDevice, st));
         CT_CUDA_TRY(cudaMemcpyAsync(c.s, S, sizeof(CglsS), cudaMemcpyDeviceToDevice, st));
         c.hist.assign((size_t)i, 0.0);
-        if (i > 0)
+        c.hist_nr.assign((size_t)i, 0.0);
+        if (i > 0) {
             CT_CUDA_TRY(cudaMemcpyAsync(c.hist.data(), hist, sizeof(double) * (size_t)i,
                                         cudaMemcpyDeviceToHost, st));
+            CT_CUDA_TRY(cudaMemcpyAsync(c.hist_nr.data(), hist + K, sizeof(double) * (size_t)i,
+                                        cudaMemcpyDeviceToHost, st));
+        }
         CT_CUDA_TRY(cudaStreamSynchronize(st));
         c.i = i;
         return CT_OK;
@@ -1005,11 +1028,13 @@ struct CglsJob {
         const cudaStream_t st = sv.st;
         k_vol_axpy<<<gn, kVecThreads, 0, st>>>(x, z, n, &S->a_pend);
         CT_CHECK_LAUNCH();
-        std::vector<double> h((size_t)K, 0.0);
+        std::vector<double> h((size_t)K, 0.0), h_nr((size_t)K, 0.0);
         CT_CUDA_TRY(cudaMemcpyAsync(h.data(), hist, sizeof(double) * (size_t)i,
                                     cudaMemcpyDeviceToHost, st));
+        CT_CUDA_TRY(cudaMemcpyAsync(h_nr.data(), hist + K, sizeof(double) * (size_t)i,
+                                    cudaMemcpyDeviceToHost, st));
         CT_TRY(read_scalars(S, &hs, st));
-        sv.report(rep, i, hs.nb0, hs.nb, h);
+        sv.report(rep, i, hs.nb0, hs.nb, h, &h_nr);
         return finite_or_error(hs.nb0, hs.nb);
     }
 };
@@ -1044,6 +1069,7 @@ ct_status cgls_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
         sv.n_back = b0;
     }
     while (go) {
+        CT_TRACE("cgls update");
         if (graph.exec) {
             CT_TRY(graph.launch(st));
             sv.n_fwd += dfwd;
@@ -1079,7 +1105,7 @@ ct_status lsqr_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
     CT_TRY(sv.ws.alloc(&gv, (size_t)n));
     if (sv.W) CT_TRY(sv.ws.alloc(&t, (size_t)n));
     CT_TRY(sv.ws.alloc(&S, 1));
-    CT_TRY(sv.ws.alloc(&hist, (size_t)K));
+    CT_TRY(sv.ws.alloc(&hist, 2 * (size_t)std::max(K, 1)));   // phibar / NB0, then NR
     CT_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(LsqrS), st));
     Coef sub;
     sub.alpha = -1.f;
@@ -1136,7 +1162,7 @@ ct_status lsqr_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
         CT_TRY(sv.back(u, gv, cb, nullptr, nullptr));
         k_lsqr_v<<<gn, kVecThreads, 0, s>>>(v, gv, sv.W, n, S, sv.part);
         CT_CHECK_LAUNCH();
-        k_lsqr_rot<<<1, 1024, 0, s>>>(sv.part, gn, S, hist, -1);
+        k_lsqr_rot<<<1, 1024, 0, s>>>(sv.part, gn, S, hist, -1, hist + K);
         CT_CHECK_LAUNCH();
         k_lsqr_update<<<gn, kVecThreads, 0, s>>>(x, v, wv, sv.W, n, S);
         CT_CHECK_LAUNCH();
@@ -1167,12 +1193,15 @@ ct_status lsqr_impl(const ct_geometry *g, const float *b, float *x, const ct_sol
             go = hs.nb0 > 0.0 && hs.phibar / hs.nb0 > ERR;
         }
     }
-    std::vector<double> h((size_t)K, 0.0);
-    if (i > 0)
+    std::vector<double> h((size_t)K, 0.0), h_nr((size_t)K, 0.0);
+    if (i > 0) {
         CT_CUDA_TRY(cudaMemcpyAsync(h.data(), hist, sizeof(double) * (size_t)i,
                                     cudaMemcpyDeviceToHost, st));
+        CT_CUDA_TRY(cudaMemcpyAsync(h_nr.data(), hist + K, sizeof(double) * (size_t)i,
+                                    cudaMemcpyDeviceToHost, st));
+    }
     CT_TRY(read_scalars(S, &hs, st));
-    sv.report(rep, i, hs.nb0, hs.phibar, h);
+    sv.report(rep, i, hs.nb0, hs.phibar, h, &h_nr);
     return finite_or_error(hs.nb0, hs.phibar);
 }
 
@@ -1239,7 +1268,7 @@ ct_status sirt_impl(const ct_geometry *g, const float *b, float *x, const ct_sir
         // e = b - A x; NB = ||e||
         CT_TRY(copy_b(nullptr));
         CT_TRY(project_residual(sv.part));
-        k_cgls_nb<<<1, 1024, 0, st>>>(sv.part, nfp, S, hist, i);
+        k_cgls_nb<<<1, 1024, 0, st>>>(sv.part, nfp, S, hist, i, nullptr);
         CT_CHECK_LAUNCH();
         ++i;
         go = i < K;
@@ -1286,7 +1315,7 @@ struct ct_batch {
         bool done = false;
         bool batched = false;           // its projectors run in the batched launches
         ct_solver_report rep{};
-        std::vector<double> hist;
+        std::vector<double> hist, hist_nr;
     };
     int device = 0;
     cudaStream_t st = nullptr;
@@ -1533,8 +1562,10 @@ struct ct_batch {
     // The job's stopping rule fired: finish x and keep the report.
     ct_status retire(Entry &en) {
         en.hist.assign((size_t)en.job->K, 0.0);
+        en.hist_nr.assign((size_t)en.job->K, 0.0);
         en.rep = ct_solver_report{};
         en.rep.history_nb = en.hist.data();
+        en.rep.history_nr = en.hist_nr.data();
         en.rep.history_cap = en.job->K;
         CT_TRY(en.job->end(&en.rep));
         en.done = true;
@@ -1570,6 +1601,7 @@ ct_status ct_batch_destroy(ct_batch *b) {
 
 ct_status ct_batch_add_cgls(ct_batch *b, const ct_geometry *g, const float *d_b, float *d_x,
                             const ct_solver_opts *opts, int32_t *job) {
+    CT_TRACE("ct_batch_add_cgls");
     clear_error();
     if (!b || !job) return set_error(CT_ERR_INVALID_ARG, "NULL batch or job");
     CT_TRY(check_opts(g, d_b, d_x, opts));
@@ -1599,6 +1631,7 @@ ct_status ct_batch_add_cgls(ct_batch *b, const ct_geometry *g, const float *d_b,
 }
 
 ct_status ct_batch_step(ct_batch *b, int32_t *n_active) {
+    CT_TRACE("ct_batch_step");
     clear_error();
     if (!b || !n_active) return set_error(CT_ERR_INVALID_ARG, "NULL batch or n_active");
     DeviceGuard dg(b->device);
@@ -1613,15 +1646,15 @@ ct_status ct_batch_poll(ct_batch *b, int32_t job, int32_t *done, ct_solver_repor
     if (!en) return set_error(CT_ERR_INVALID_ARG, "batch: unknown job");
     *done = en->done ? 1 : 0;
     if (en->done && report) {
-        double *hn = report->history_nb;
+        double *hn = report->history_nb, *hr = report->history_nr;
         const int32_t cap = report->history_cap;
         *report = en->rep;
         report->history_nb = hn;
+        report->history_nr = hr;
         report->history_cap = cap;
-        if (hn && cap > 0) {
-            const int k = std::min<int>(cap, std::min<int>(en->rep.iterations, (int)en->hist.size()));
-            for (int j = 0; j < k; ++j) hn[j] = en->hist[(size_t)j];
-        }
+        const int k = std::min<int>(cap, std::min<int>(en->rep.iterations, (int)en->hist.size()));
+        for (int j = 0; hn && j < k; ++j) hn[j] = en->hist[(size_t)j];
+        for (int j = 0; hr && j < k; ++j) hr[j] = en->hist_nr[(size_t)j];
     }
     return CT_OK;
 }
@@ -1644,6 +1677,7 @@ ct_status ct_batch_remove(ct_batch *b, int32_t job) {
 
 ct_status ct_cgls(const ct_geometry *g, const float *d_b, float *d_x, const ct_solver_opts *opts,
                   ct_solver_report *report, void *stream) {
+    CT_TRACE("ct_cgls");
     clear_error();
     CT_TRY(check_opts(g, d_b, d_x, opts));
     DeviceGuard dg(g->device);
@@ -1662,6 +1696,7 @@ ct_status ct_cgls(const ct_geometry *g, const float *d_b, float *d_x, const ct_s
 
 ct_status ct_lsqr(const ct_geometry *g, const float *d_b, float *d_x, const ct_solver_opts *opts,
                   ct_solver_report *report, void *stream) {
+    CT_TRACE("ct_lsqr");
     clear_error();
     CT_TRY(check_opts(g, d_b, d_x, opts));
     if (opts->tikhonov_lambda != 0.0)
@@ -1679,6 +1714,7 @@ ct_status ct_lsqr(const ct_geometry *g, const float *d_b, float *d_x, const ct_s
 
 ct_status ct_sirt(const ct_geometry *g, const float *d_b, float *d_x, const ct_sirt_opts *opts,
                   ct_solver_report *report, void *stream) {
+    CT_TRACE("ct_sirt");
     clear_error();
     if (!g) return set_error(CT_ERR_INVALID_ARG, "geometry is NULL");
     if (!opts) return set_error(CT_ERR_INVALID_ARG, "opts is NULL");
@@ -1745,7 +1781,8 @@ ct_status ct_cgls_state_iterations(const ct_cgls_state *st, int32_t *iterations)
 
 namespace {
 // Serialised form of a state: this header, then x, d_x (n floats each), e_b
-// (m floats), the scalar block and the history (i doubles), native byte order.
+// (m floats), the scalar block, the NB / NB0 history and the NR history (i
+// doubles each), native byte order.
 struct CkptHeader {
     uint32_t magic, version;
     int64_t n, m;
@@ -1753,11 +1790,11 @@ struct CkptHeader {
     uint64_t scalar_bytes;
 };
 constexpr uint32_t kCkptMagic = 0x47435443u;   // "CTCG"
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;
 
 int64_t ckpt_bytes(const CglsCkpt &c) {
     return (int64_t)sizeof(CkptHeader) + (2 * c.n + c.m) * (int64_t)sizeof(float) +
-           (int64_t)sizeof(CglsS) + c.i * (int64_t)sizeof(double);
+           (int64_t)sizeof(CglsS) + 2 * c.i * (int64_t)sizeof(double);
 }
 }  // namespace
 
@@ -1783,7 +1820,11 @@ ct_status ct_cgls_state_export(const ct_cgls_state *st, void *host, int64_t capa
     p += c.m * sizeof(float);
     CT_CUDA_TRY(cudaMemcpy(p, c.s, sizeof(CglsS), cudaMemcpyDeviceToHost));
     p += sizeof(CglsS);
-    if (c.i > 0) std::memcpy(p, c.hist.data(), sizeof(double) * (size_t)c.i);
+    if (c.i > 0) {
+        std::memcpy(p, c.hist.data(), sizeof(double) * (size_t)c.i);
+        p += c.i * sizeof(double);
+        std::memcpy(p, c.hist_nr.data(), sizeof(double) * (size_t)c.i);
+    }
     return CT_OK;
 }
 
@@ -1816,7 +1857,12 @@ ct_status ct_cgls_state_import(ct_cgls_state *st, const void *host, int64_t byte
     CT_CUDA_TRY(cudaMemcpy(c.s, p, sizeof(CglsS), cudaMemcpyHostToDevice));
     p += sizeof(CglsS);
     c.hist.assign((size_t)h.i, 0.0);
-    if (h.i > 0) std::memcpy(c.hist.data(), p, sizeof(double) * (size_t)h.i);
+    c.hist_nr.assign((size_t)h.i, 0.0);
+    if (h.i > 0) {
+        std::memcpy(c.hist.data(), p, sizeof(double) * (size_t)h.i);
+        p += h.i * sizeof(double);
+        std::memcpy(c.hist_nr.data(), p, sizeof(double) * (size_t)h.i);
+    }
     c.i = h.i;
     return CT_OK;
 }
@@ -1824,6 +1870,7 @@ ct_status ct_cgls_state_import(ct_cgls_state *st, const void *host, int64_t byte
 ct_status ct_cgls_resume(const ct_geometry *g, const float *d_b, float *d_x,
                          const ct_solver_opts *opts, ct_solver_report *report, ct_cgls_state *state,
                          void *stream) {
+    CT_TRACE("ct_cgls_resume");
     clear_error();
     CT_TRY(check_opts(g, d_b, d_x, opts));
     if (!state) return set_error(CT_ERR_INVALID_ARG, "state is NULL");

@@ -329,3 +329,40 @@ def test_streaming_norms_are_fp64_accurate(ct, small, spread):
     _, rep = ct.cgls(g, torch.from_numpy(b32).cuda(), max_iter=1)
     want = float(np.sqrt(np.sum(b32.astype(np.float64) ** 2)))
     assert rep.nb0 == pytest.approx(want, rel=1e-12)
+
+
+@pytest.mark.parametrize("solver", ["cgls", "lsqr"])
+def test_gradient_norm_history(ct, small, solver):
+    """history_nr: ||A^T (b - A x_{k-1})|| at the iterate before each update,
+    against the same norm of the FP64 oracle's iterates (CGLS computes it;
+    LSQR carries the Paige-Saunders estimate, exact in exact arithmetic).
+    Batched and resumed CGLS report the same values."""
+    cfg, og, _, b = small
+    g = ct.Geometry(**cfg)
+    K = 10
+    fn, ofn = (ct.cgls, ocgls) if solver == "cgls" else (ct.lsqr, olsqr)
+    x, rep = fn(g, torch.from_numpy(b).cuda(), max_iter=K)
+    op = oracle.Operator(og)
+    ref = ofn(op, b.astype(np.float64), K=K, keep_iterates=True)
+    prev = [np.zeros(og.vol_shape)] + list(ref.iterates[:-1])
+    want = [float(np.linalg.norm(op.AT(b.astype(np.float64) - op.A(xk)))) for xk in prev]
+    assert len(rep.history_nr) == K
+    np.testing.assert_allclose(rep.history_nr, want, rtol=2e-3 if solver == "cgls" else 1e-2)
+    assert want[-1] < 0.5 * want[0]          # the gradient shrinks
+    if solver == "cgls":
+        bt = ct.Batch()
+        j = bt.add(g, torch.from_numpy(b).cuda(), max_iter=K)
+        while not bt.done(j):
+            bt.step()
+        _, rb = bt.result(j)
+        bt.close()
+        np.testing.assert_allclose(rb.history_nr, rep.history_nr, rtol=1e-5)
+        st = ct.CglsState(g)
+        st.run(torch.from_numpy(b).cuda(), 4)
+        blob = st.to_bytes()
+        st.close()
+        st2 = ct.CglsState(g)
+        st2.from_bytes(blob)
+        _, rr = st2.run(torch.from_numpy(b).cuda(), K)
+        st2.close()
+        np.testing.assert_allclose(rr.history_nr, rep.history_nr, rtol=1e-5)
