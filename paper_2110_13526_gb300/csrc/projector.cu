@@ -641,8 +641,9 @@ __device__ __forceinline__ bool cm_setup(const ProjGeom &g, int view, int u, int
 }
 
 // Column-major slab walk; fn(offset, length in slabs, p) is called for the
-// segments of each slab, and may touch memory only where p is set (the
-// offset is then inside the volume).  Must be called by all 32 lanes of the
+// segments of each slab (with WS the lengths times ws, a per-lane weight),
+// and may touch memory only where p is set (the offset is then inside the
+// volume).  Must be called by all 32 lanes of the
 // warp, which hold rows of one column; ci = view * nu + u is the column.
 //
 // The warp walks the slabs any of its rays may touch.  Slabs that lie wholly
@@ -660,9 +661,10 @@ __device__ __forceinline__ bool cm_setup(const ProjGeom &g, int view, int u, int
 // Everything the exit slabs need beyond the loop state is re-derived after
 // the interior from the column's parameters, so that it holds no registers
 // during the loop (the forward kernel runs at 32 registers a thread).
-template <int DZ, class Fn>
+template <int DZ, bool WS, class Fn>
 __device__ __forceinline__ void walk_cm_dir(const ProjGeom &g, int ci, const CmRay &r, bool ok,
-                                            int kb, int ke, int k_mid0, int k_mid1, Fn &&fn) {
+                                            int kb, int ke, int k_mid0, int k_mid1, Fn &&fn,
+                                            float ws) {
     // state of both lines at the start of slab kb
     const long long X = r.X0 + (r.x_up ? (long long)kb * r.dX : -(long long)kb * r.dX);
     const long long Z = r.Z0 + (r.z_up ? (long long)kb * r.dZ : -(long long)kb * r.dZ);
@@ -699,9 +701,10 @@ __device__ __forceinline__ void walk_cm_dir(const ProjGeom &g, int ci, const CmR
         const bool a0 = (unsigned)ai < (unsigned)Na, a1 = (unsigned)(ai + da) < (unsigned)Na;
         const bool z0 = (unsigned)zi < (unsigned)g.nz, z1 = (unsigned)(zi + dz) < (unsigned)g.nz;
         const bool mx = sx <= sz;   // the middle segment is past the lateral crossing
-        fn((int)o, l1, a0 && z0 && l1 > 0.f);
-        fn((int)(o + (mx ? astep : dzu)), l2, (mx ? (a1 && z0) : (a0 && z1)) && l2 > 0.f);
-        fn((int)(o + (cx ? astep : 0u) + (cz ? dzu : 0u)), l3,
+        fn((int)o, WS ? ws * l1 : l1, a0 && z0 && l1 > 0.f);
+        fn((int)(o + (mx ? astep : dzu)), WS ? ws * l2 : l2,
+           (mx ? (a1 && z0) : (a0 && z1)) && l2 > 0.f);
+        fn((int)(o + (cx ? astep : 0u) + (cz ? dzu : 0u)), WS ? ws * l3 : l3,
            (cx ? a1 : a0) && (cz ? z1 : z0) && l3 > 0.f);
         phi -= dX;
         psi -= dZ;
@@ -719,21 +722,43 @@ __device__ __forceinline__ void walk_cm_dir(const ProjGeom &g, int ci, const CmR
     // they are formed as int sums: the z neighbour (o + dz) is then a
     // constant displacement of o's address when DZ is fixed.
     const int dzi = DZ != 0 ? DZ : (int)dzu, ast = (int)astep;
+    // With WS a two-segment slab hands fn ws sz and ws (1 - sz) straight
+    // from the z step scaled by ws.
+    const float kzw = WS ? ws * kz : kz;
     auto interior = [&]() {
         const bool cz = psi < dZ;
-        const float sz = cz ? fmaf(one_plus_frac(psi), kz, -kz) : 1.f;
-        psi -= dZ;
-        const int oi = (int)o;
-        if (phi >= dX) {   // no lateral crossing (warp-uniform)
-            fn(oi, sz, true);
-            fn(oi + dzi, 1.f - sz, cz);
+        if constexpr (WS) {
+            const float fz = one_plus_frac(psi);
+            psi -= dZ;
+            const int oi = (int)o;
+            if (phi >= dX) {   // no lateral crossing (warp-uniform)
+                const float szw = cz ? fmaf(fz, kzw, -kzw) : ws;
+                fn(oi, szw, true);
+                fn(oi + dzi, ws - szw, cz);
+            } else {
+                const float sz = cz ? fmaf(fz, kz, -kz) : 1.f;
+                const float sx = fmaf(one_plus_frac(phi), kx, -kx);
+                const float s1 = fminf(sx, sz), s2 = fmaxf(sx, sz);
+                fn(oi, ws * s1, true);
+                fn(sx <= sz ? oi + ast : oi + dzi, ws * (s2 - s1), true);
+                fn(oi + ast + (cz ? dzi : 0), ws * (1.f - s2), cz);
+                o += astep;
+            }
         } else {
-            const float sx = fmaf(one_plus_frac(phi), kx, -kx);
-            const float s1 = fminf(sx, sz), s2 = fmaxf(sx, sz);
-            fn(oi, s1, true);
-            fn(sx <= sz ? oi + ast : oi + dzi, s2 - s1, true);
-            fn(oi + ast + (cz ? dzi : 0), 1.f - s2, cz);
-            o += astep;
+            const float sz = cz ? fmaf(one_plus_frac(psi), kz, -kz) : 1.f;
+            psi -= dZ;
+            const int oi = (int)o;
+            if (phi >= dX) {   // no lateral crossing (warp-uniform)
+                fn(oi, sz, true);
+                fn(oi + dzi, 1.f - sz, cz);
+            } else {
+                const float sx = fmaf(one_plus_frac(phi), kx, -kx);
+                const float s1 = fminf(sx, sz), s2 = fmaxf(sx, sz);
+                fn(oi, s1, true);
+                fn(sx <= sz ? oi + ast : oi + dzi, s2 - s1, true);
+                fn(oi + ast + (cz ? dzi : 0), 1.f - s2, cz);
+                o += astep;
+            }
         }
         phi -= dX;
         o += sstep + (cz ? dzu : 0u);
@@ -769,9 +794,9 @@ __device__ __forceinline__ void walk_cm_dir(const ProjGeom &g, int ci, const CmR
 // the warp that hold a ray move the same way along z (every warp but the one
 // holding the column's horizontal row): the z neighbour of a voxel is then a
 // constant offset from its address.
-template <class Fn>
+template <bool WS = false, class Fn>
 __device__ __forceinline__ void walk_cm(const ProjGeom &g, int ci, const CmRay &r, bool ok,
-                                        Fn &&fn) {
+                                        Fn &&fn, float ws = 1.f) {
     const unsigned full = 0xffffffffu;
     const int kb = __reduce_min_sync(full, ok ? r.k_lo : INT_MAX);
     const int ke = __reduce_max_sync(full, ok ? r.k_hi : -1);
@@ -779,11 +804,11 @@ __device__ __forceinline__ void walk_cm(const ProjGeom &g, int ci, const CmRay &
     const int k_mid0 = max(kb, __reduce_max_sync(full, ok ? r.k_in0 : INT_MIN));
     const int k_mid1 = min(ke, __reduce_min_sync(full, ok ? r.k_in1 : INT_MAX));
     if (__all_sync(full, !ok || r.z_up))
-        walk_cm_dir<1>(g, ci, r, ok, kb, ke, k_mid0, k_mid1, fn);
+        walk_cm_dir<1, WS>(g, ci, r, ok, kb, ke, k_mid0, k_mid1, fn, ws);
     else if (__all_sync(full, !ok || !r.z_up))
-        walk_cm_dir<-1>(g, ci, r, ok, kb, ke, k_mid0, k_mid1, fn);
+        walk_cm_dir<-1, WS>(g, ci, r, ok, kb, ke, k_mid0, k_mid1, fn, ws);
     else
-        walk_cm_dir<0>(g, ci, r, ok, kb, ke, k_mid0, k_mid1, fn);
+        walk_cm_dir<0, WS>(g, ci, r, ok, kb, ke, k_mid0, k_mid1, fn, ws);
 }
 
 // One tile of p = alpha * rho o (A vol) + beta * p from the [y][x][z] copy
@@ -891,12 +916,17 @@ __device__ __forceinline__ void backward_cm_tile(const ProjGeom &g, uint3 bid,
             red_add_u64_if(base + o, __float2ll_rn(val * scale),
                            p && nz && CT_IN_BOUNDS(o, nvox));
         });
+    } else if constexpr (POWER == 1) {
+        // the walk hands over the contributions w l themselves
+        float *base = static_cast<float *>(acc_z);
+        walk_cm<true>(g, view * g.nu + u, r, ok, [&](int o, float wl, bool p) {
+            red_add_if(base + o, wl, p && nz && CT_IN_BOUNDS(o, nvox));
+        }, w);
     } else {
         float *base = static_cast<float *>(acc_z);
         walk_cm(g, view * g.nu + u, r, ok, [&](int o, float l, bool p) {
             const float lm = l * ls;
-            red_add_if(base + o, POWER == 1 ? w * l : w * lm * lm,
-                       p && nz && CT_IN_BOUNDS(o, nvox));
+            red_add_if(base + o, w * lm * lm, p && nz && CT_IN_BOUNDS(o, nvox));
         });
     }
 }
