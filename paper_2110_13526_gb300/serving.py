@@ -28,7 +28,9 @@ A queued request leaves the queue without running; a batched CGLS job
 leaves its batch at the next step boundary with the iterate it has; a
 per-slot CGLS solve with ``cancel_chunk = k > 0`` runs as a resumable state
 in chunks of k updates (ct_cgls_resume, bitwise the uninterrupted solve
-with a deterministic geometry) and stops at the next chunk boundary; any
+with a deterministic geometry) and stops at the next chunk boundary (the
+state's device buffers are allocated and freed per solve, and freeing waits
+for the device, so the option costs every other slot a short stall); any
 other running solve runs to its end and is marked cancelled.  Each
 cancelled request yields a Result with ``cancelled`` set (x the iterate it
 reached, or None if it never ran); latency percentiles cover the requests
