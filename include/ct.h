@@ -81,9 +81,9 @@ typedef struct {
 
 /* Create a geometry on the current CUDA device.  Requires nx, ny, nz >= 1,
  * nu, nv, nviews >= 0, positive pitches, 0 < sid < sdd, fewer than 2^31
- * voxels, nx * ny < 2^31, nz <= 65535, nviews <= 65535 and nv <= 524280
- * (CUDA grid limits); anything else is CT_ERR_INVALID_ARG.  *out receives the
- * handle. */
+ * voxels, nx * ny < 2^31, nx, ny, nz <= 65535 (the walks' integer lines stay
+ * inside int64), nviews <= 65535 and nv <= 524280 (CUDA grid limits);
+ * anything else is CT_ERR_INVALID_ARG.  *out receives the handle. */
 ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out);
 
 /* Free the geometry (NULL is a no-op).  No call using it may be in flight. */

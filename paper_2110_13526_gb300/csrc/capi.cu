@@ -159,7 +159,7 @@ ct_status check_geom(const ct_geometry *g) {
     return CT_OK;
 }
 
-// Per-view ray constants, FP64 on the host, stored FP32 in voxel units.
+// Per-view ray constants, FP64, in voxel units.
 void view_constants(const ct_geometry_desc &d, const std::vector<double> &ang,
                     std::vector<ViewConst> &out) {
     const double h[3] = {d.vx, d.vy, d.vz};
@@ -179,10 +179,10 @@ void view_constants(const ct_geometry_desc &d, const std::vector<double> &ang,
         }
         ViewConst &vc = out[k];
         for (int a = 0; a < 3; ++a) {
-            vc.s[a] = (float)((src[a] - lo[a]) / h[a]);
-            vc.p00[a] = (float)((pc[a] - lo[a]) / h[a]);
-            vc.eu[a] = (float)(d.du * eu[a] / h[a]);
-            vc.ev[a] = (float)(d.dv * ev[a] / h[a]);
+            vc.s[a] = (src[a] - lo[a]) / h[a];
+            vc.p00[a] = (pc[a] - lo[a]) / h[a];
+            vc.eu[a] = d.du * eu[a] / h[a];
+            vc.ev[a] = d.dv * ev[a] / h[a];
         }
     }
 }
@@ -190,19 +190,14 @@ void view_constants(const ct_geometry_desc &d, const std::vector<double> &ang,
 // x * 2^44 rounded to the nearest integer (ColFixed).
 long long q44(double x) { return std::llround(std::ldexp(x, 44)); }
 
-// Per-column ray parameters (see ColParams), in FP64, stored FP32, and the
-// same lines in fixed point for the column-major kernels (ColFixed).
+// Per-column ray lines (ColFixed), computed in FP64 and stored in fixed point.
 void column_params(const ct_geometry_desc &d, const std::vector<double> &ang,
-                   std::vector<float4> &ca_out, std::vector<float4> &cb_out,
-                   std::vector<int> &fl_out, std::vector<ColFixed> &cq_out) {
+                   std::vector<ColFixed> &cq_out) {
     const double h[3] = {d.vx, d.vy, d.vz};
     const int N[3] = {d.nx, d.ny, d.nz};
     const double lo[3] = {-0.5 * d.nx * d.vx + d.off_x, -0.5 * d.ny * d.vy + d.off_y,
                           -0.5 * d.nz * d.vz + d.off_z};
     const size_t ncol = ang.size() * (size_t)d.nu;
-    ca_out.resize(ncol);
-    cb_out.resize(ncol);
-    fl_out.resize(ncol);
     cq_out.resize(ncol);
     for (size_t k = 0; k < ang.size(); ++k) {
         const double c = std::cos(ang[k]), s = std::sin(ang[k]);
@@ -235,9 +230,6 @@ void column_params(const ct_geometry_desc &d, const std::vector<double> &ang,
             const double adx = std::fabs(Ds);
             const size_t i = k * (size_t)d.nu + (size_t)u;
             if (adx == 0.0) {  // degenerate: never hits (pixel at the source)
-                ca_out[i] = make_float4(0.f, 1e30f, 0.f, 0.f);
-                cb_out[i] = make_float4(1e30f, 0.f, 0.f, -1.f);
-                fl_out[i] = 0;
                 cq_out[i] = ColFixed{0, q44(65536.0), 0, 0, q44(65536.0), 0, 0.f, -1.f, 0, 0};
                 continue;
             }
@@ -249,13 +241,15 @@ void column_params(const ct_geometry_desc &d, const std::vector<double> &ang,
             const double Z1 = (sig0 - S[ax]) * EVz / Ds;
             const double wsrc = (rev ? Ns - S[ax] : S[ax]) - cs;
             const double wpix = (rev ? Ns - P[ax] : P[ax]) - cs;
-            ca_out[i] = make_float4((float)A, (float)XI0, (float)C0, (float)C1);
-            cb_out[i] = make_float4((float)Z0, (float)Z1, (float)wsrc, (float)wpix);
-            fl_out[i] = (ax == 0 ? 1 : 0) | (rev ? 2 : 0);
+            const int fl = (ax == 0 ? 1 : 0) | (rev ? 2 : 0);
             const double lim = 65536.0;   // a ray this far out misses the volume
-            cq_out[i] = ColFixed{q44(A), q44(std::fmin(std::fmax(XI0, -lim), lim)), q44(C0),
-                                 q44(0.5 * C1), q44(std::fmin(std::fmax(Z0, -lim), lim)),
-                                 q44(0.5 * Z1), (float)wsrc, (float)wpix, fl_out[i], 0};
+            // z lines held in Q.44 only while c0 + vc2 c1h stays far inside int64
+            const bool zfit = std::fabs(C0) < 1e5 && std::fabs(C1) * (double)(d.nv + 1) < 1e5;
+            cq_out[i] = ColFixed{q44(A), q44(std::fmin(std::fmax(XI0, -lim), lim)),
+                                 zfit ? q44(C0) : 0, zfit ? q44(0.5 * C1) : 0,
+                                 zfit ? q44(std::fmin(std::fmax(Z0, -lim), lim)) : 0,
+                                 zfit ? q44(0.5 * Z1) : 0, (float)wsrc, (float)wpix,
+                                 fl | (zfit ? 0 : 4), 0};
         }
     }
 }
@@ -272,6 +266,7 @@ static bool cm_eligible(const ct_geometry_desc &d, const std::vector<ColFixed> &
     if (d.nx > 32768 || d.ny > 32768 || d.nz > 32768) return false;
     const long long one = 1LL << 44, m = (long long)std::max(d.nv - 1, 0);
     for (const ColFixed &q : colq) {
+        if (q.flags & 4) return false;
         const double cf = std::fabs((double)q.c0) + (double)m * std::fabs((double)q.c1h);
         const double zf = (double)m * std::fabs((double)q.z1h);
         if (cf > 2.0 * (double)one || zf > std::ldexp(1.0, 60)) return false;
@@ -303,8 +298,8 @@ ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out) {
     const int64_t nvox = (int64_t)d.nx * d.ny * d.nz;
     if (nvox >= (int64_t(1) << 31))
         return set_error(CT_ERR_INVALID_ARG, "volume must hold fewer than 2^31 voxels");
-    if (d.nz > 65535 || d.nviews > 65535)
-        return set_error(CT_ERR_INVALID_ARG, "nz and nviews must be <= 65535");
+    if (d.nx > 65535 || d.ny > 65535 || d.nz > 65535 || d.nviews > 65535)
+        return set_error(CT_ERR_INVALID_ARG, "nx, ny, nz and nviews must be <= 65535");
     if (d.nv > 65535 * 8)
         return set_error(CT_ERR_INVALID_ARG, "nv must be <= 524280");
     if ((int64_t)d.nx * d.ny >= (int64_t(1) << 31))
@@ -353,33 +348,19 @@ ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out) {
     }
     std::vector<ViewConst> vcs;
     view_constants(d, g->angles, vcs);
-    std::vector<float4> cola, colb;
-    std::vector<int> colf;
     std::vector<ColFixed> colq;
-    column_params(d, g->angles, cola, colb, colf, colq);
+    column_params(d, g->angles, colq);
     g->d_cols = nullptr;
-    const size_t ncol = cola.size();
-    // device layout: col_a, col_b (float4 each), col_q (ColFixed), col_flags
-    const size_t off_b = ncol * sizeof(float4), off_q = 2 * ncol * sizeof(float4);
-    const size_t off_f = off_q + ncol * sizeof(ColFixed);
+    const size_t ncol = colq.size();
     if (d.nviews > 0) {
         e = cudaMalloc(&g->d_views, sizeof(ViewConst) * vcs.size());
         if (e == cudaSuccess)
             e = cudaMemcpy(g->d_views, vcs.data(), sizeof(ViewConst) * vcs.size(),
                            cudaMemcpyHostToDevice);
         if (e == cudaSuccess && ncol > 0) {
-            e = cudaMalloc(&g->d_cols, off_f + ncol * sizeof(int));
-            char *base = (char *)g->d_cols;
+            e = cudaMalloc(&g->d_cols, ncol * sizeof(ColFixed));
             if (e == cudaSuccess)
-                e = cudaMemcpy(base, cola.data(), ncol * sizeof(float4), cudaMemcpyHostToDevice);
-            if (e == cudaSuccess)
-                e = cudaMemcpy(base + off_b, colb.data(), ncol * sizeof(float4),
-                               cudaMemcpyHostToDevice);
-            if (e == cudaSuccess)
-                e = cudaMemcpy(base + off_q, colq.data(), ncol * sizeof(ColFixed),
-                               cudaMemcpyHostToDevice);
-            if (e == cudaSuccess)
-                e = cudaMemcpy(base + off_f, colf.data(), ncol * sizeof(int),
+                e = cudaMemcpy(g->d_cols, colq.data(), ncol * sizeof(ColFixed),
                                cudaMemcpyHostToDevice);
         }
         if (e != cudaSuccess) {
@@ -390,11 +371,7 @@ ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out) {
         }
     }
     g->pg.views = g->d_views;
-    char *cb = (char *)g->d_cols;
-    g->pg.col_a = cb ? (const float4 *)cb : nullptr;
-    g->pg.col_b = cb ? (const float4 *)(cb + off_b) : nullptr;
-    g->pg.col_q = cb ? (const ColFixed *)(cb + off_q) : nullptr;
-    g->pg.col_flags = cb ? (const int *)(cb + off_f) : nullptr;
+    g->pg.col_q = (const ColFixed *)g->d_cols;
     g->pg.nx = d.nx; g->pg.ny = d.ny; g->pg.nz = d.nz;
     g->pg.nu = d.nu; g->pg.nv = d.nv; g->pg.nviews = d.nviews;
     g->pg.hx = (float)d.vx; g->pg.hy = (float)d.vy; g->pg.hz = (float)d.vz;

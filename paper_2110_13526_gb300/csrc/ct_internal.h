@@ -15,16 +15,17 @@ namespace ct {
 // Per-view ray constants in VOXEL units, relative to the volume box's low
 // corner: a point q (mm) maps to (q - box_lo) / h per axis.  A ray of pixel
 // (u, v) runs from s to p00 + uc * eu + vc * ev, where p00 is the centre of
-// the pixel grid, uc = u - (nu-1)/2 and vc = v - (nv-1)/2.
+// the pixel grid, uc = u - (nu-1)/2 and vc = v - (nv-1)/2.  FP64: the
+// ray-major kernels set up the rays that advance mostly along z from them.
 struct ViewConst {
-    float s[3];
-    float p00[3];
-    float eu[3];
-    float ev[3];
+    double s[3];
+    double p00[3];
+    double eu[3];
+    double ev[3];
 };
 
-// Per detector column (view, u) ray parameters, computed in FP64 on the host
-// and stored FP32.  For a flat detector whose v axis is the rotation axis,
+// Per detector column (view, u) ray parameters, computed in FP64 on the host.
+// For a flat detector whose v axis is the rotation axis,
 // the in-plane direction of ray (u, v) depends on u only, so the slab axis s
 // (x or y, whichever the ray advances along faster), the walk direction and
 // the lateral slope A are per column; the z terms are affine in v.
@@ -35,14 +36,10 @@ struct ViewConst {
 // minus Na/2, zeta = z coordinate minus Nz/2 (integer halves).  On the ray:
 //   xi(w)   = XI0 + A w,            zeta(w) = (Z0 + vc Z1) + (C0 + vc C1) w,
 // with vc = v - (nv-1)/2, and w runs from wsrc (source) to wpix (pixel).
-struct ColParams {
-    float4 a;  // A, XI0, C0, C1
-    float4 b;  // Z0, Z1, wsrc, wpix
-};
-
-// The same column lines for the column-major kernels in Q.44 fixed point
-// (value * 2^44, rounded to the nearest int64), which the walk turns into
-// exact integer lines (projector.cu).  A row v has vc2 = 2 v - (nv - 1) and
+//
+// The lines are stored in Q.44 fixed point (value * 2^44, rounded to the
+// nearest int64), which the walks turn into exact integer lines
+// (projector.cu).  A row v has vc2 = 2 v - (nv - 1) and
 //   C = (c0 + vc2 c1h) 2^-44,   Z0 + vc Z1 = (z0 + vc2 z1h) 2^-44,
 // so the per-row slope and offset are exact integer sums.  XI0 and Z0 are
 // clamped to +-2^16 voxels (such a ray misses every volume the column-major
@@ -51,18 +48,17 @@ struct __align__(16) ColFixed {
     long long a, xi;     // A, XI0
     long long c0, c1h;   // C0, C1 / 2
     long long z0, z1h;   // Z0, Z1 / 2
-    float wsrc, wpix;    // as in ColParams (FP32)
-    int flags;           // bit 0: slab axis is x (else y); bit 1: walk reversed
+    float wsrc, wpix;    // FP32
+    int flags;           // bit 0: slab axis is x (else y); bit 1: walk reversed;
+                         // bit 2: the z lines do not fit Q.44 (c0 = c1h = 0):
+                         // every ray of the column is set up as advancing along z
     int pad;
 };
 
 // Everything a projector kernel needs, passed by value.
 struct ProjGeom {
     const ViewConst *views;  // device array [nviews] (rays advancing along z)
-    const float4 *col_a;     // device arrays [nviews * nu]: ColParams::a
-    const float4 *col_b;     //                               ColParams::b
-    const int *col_flags;    // bit 0: slab axis is x (else y); bit 1: walk reversed
-    const ColFixed *col_q;   // device array [nviews * nu]: column-major kernels
+    const ColFixed *col_q;   // device array [nviews * nu]: the column lines (all walks)
     int nx, ny, nz;
     int nu, nv, nviews;
     float hx, hy, hz;        // voxel pitch, mm
@@ -96,7 +92,7 @@ struct ct_geometry {
     int device;
     int64_t nvox, nrays;
     ct::ViewConst *d_views;      // device
-    void *d_cols;                // device: col_a, col_b, col_flags in one allocation
+    void *d_cols;                // device: the column table (ColFixed)
     ct::ProjGeom pg;
     int deterministic;           // backprojections accumulate in int64 fixed point
     float4 *d_sf;                // device: footprint-projector view constants (or NULL)

@@ -9,19 +9,19 @@
 // time.  In voxel units the lateral coordinates along the ray are affine in
 // the slab coordinate sigma, xi(sigma) = xi0 + A sigma and zeta(sigma) =
 // ze0 + C sigma with |A|, |C| <= 1, so inside one slab the ray crosses at
-// most one plane of each lateral axis: at most three voxels per slab.  Every
-// plane crossing is computed directly from its plane index (no incremental
-// parameter that drifts), and the crossing order inside a slab decides the
-// middle voxel.  Summing (segment length in sigma) * value and multiplying by
-// the ray's mm-per-sigma factor gives exactly the Siddon line integral up to
-// FP32 rounding of the crossing positions.
+// most one plane of each lateral axis: at most three voxels per slab.  The
+// crossing order inside a slab decides the middle voxel.  Summing (segment
+// length in slabs) * value and multiplying by the ray's mm-per-slab factor
+// gives the Siddon line integral.
 //
-// Precision.  All coordinates are relative to the volume centre (shifted by
-// integer plane counts, so floors stay exact), which keeps them below N/2 in
-// magnitude; the ray parameters come from a per-column table computed in FP64
-// on the host (ColParams), because a ray's in-plane direction depends on its
-// detector column only.  Anchoring rays at the source (hundreds of voxels
-// away) in FP32 instead costs an order of magnitude in accuracy.
+// Precision.  Both lateral lines of a ray are exact integer lines in Q.32
+// fixed point, X(k) = X0 +- k dX, rounded once from FP64 (a per-column table
+// computed on the host, since a ray's in-plane direction depends on its
+// detector column only, and an exact integer sum per row; an FP64 setup for
+// the rays that advance mostly along z).  A slab crosses a plane iff the
+// distance to it, phi mod 2^32, is below dX, at the fraction phi / dX of the
+// slab; integer steps do not drift, so a crossing is off by at most 2^-33
+// voxel per slab walked plus 2^-23 of a slab, wherever it lies in the volume.
 //
 // Coherence.  The slab loop is warp-synchronous (the loop index is the same
 // physical slab for all lanes), and a warp's 32 rays are neighbours on the
@@ -31,11 +31,11 @@
 //    detector column; they share the in-plane walk and differ in z, and read
 //    a copy of the volume laid out [y][x][z] (z fastest).  See the column-
 //    major section below.
-//  * ray-major (geometries with rays that advance mostly along z): the lanes
-//    are 32 adjacent columns of one row and differ along the lateral axis
-//    that varies with u: x for rays advancing along y (the caller's layout
-//    [z][y][x]) and y for rays advancing along x, which read a copy laid out
-//    [z][x][y].
+//  * ray-major (geometries with rays that advance mostly along z, the nnz
+//    counter and the allocation-free projection): the lanes are 32 adjacent
+//    columns of one row and differ along the lateral axis that varies with
+//    u: x for rays advancing along y or z (the caller's layout [z][y][x])
+//    and y for rays advancing along x, which read a copy laid out [z][x][y].
 // Either way the warp's gathers (and the backprojector's reductions) fall on
 // one or two 128-byte lines.
 #include <algorithm>
@@ -69,217 +69,250 @@ constexpr int kWideGroupFwd = 65535;
 constexpr double kPairRowVox = 0.75;
 constexpr int kWideGroupBack = 16;
 
+// Slab coordinate at which the Q.32 line X(k) = X0 + k s reaches the integer
+// plane P (s: signed slope per slab, in units of 2^-32).
+__device__ __forceinline__ float plane_k(int P, long long X0, float s) {
+    return __ll2float_rn(((long long)P << 32) - X0) / s;
+}
+
+// 1 + q 2^-32 truncated to a float in [1, 2): the exponent bits of 1.0f
+// (0x7f << 23) funnel-shifted in above the top 23 bits of q.
+__device__ __forceinline__ float one_plus_frac(unsigned q) {
+    return __uint_as_float(__funnelshift_r(q, 0x7fu, 9));
+}
+
+// ---- ray-major kernels: one ray per lane, exact integer lines ---------------
+// Each lane walks its own ray slab by slab along the axis it advances along
+// fastest, with two lateral lines in Q.32 fixed point, X(k) = X0 +- k dX
+// (the same exact integer lines as the column-major walk below): for a ray
+// advancing along x or y, the in-plane lateral axis (the column's line from
+// the host table) and z (the row's line, an exact integer sum); for a ray
+// advancing along z, x and y, rounded to Q.44 from an FP64 setup of the ray.
+// A slab holds at most three segments.  Offsets index the kernel's copy of
+// the volume: [z][y][x] for rays advancing along y or z, [z][x][y]
+// (transposed) for rays advancing along x, so adjacent lanes (adjacent
+// columns of one row) touch adjacent words along their in-plane lateral axis.
 struct Ray {
-    int soff0 = 0, sstep = 0;   // memory offset of walk slab k: soff0 + k * sstep + i + j * bstride
-    int bstride = 0;            // stride of lateral axis b (lateral a has stride 1)
-    int cs = 0;                 // walk slab k spans w in [k - cs, k + 1 - cs]
-    float fa_lo = 0.f, fa_hi = 0.f, fb_lo = 0.f, fb_hi = 0.f;  // centred index ranges
-    float xi0 = 0.f, A = 0.f, invA = 0.f;
-    float ze0 = 0.f, C = 0.f, invC = 0.f;
-    float w_in = 0.f, w_out = 0.f;
-    int k_first = INT_MAX, k_last = -1;
-    float lsig = 0.f;           // mm of ray per unit w
-    bool transposed = false;    // walks the [z][x][y] copy
+    long long X0 = 0, Y0 = 0;        // lines a and b at the start of slab 0 (Q.32)
+    unsigned dX = 0u, dY = 0u;       // |slope| per slab (Q.32)
+    bool x_up = false, y_up = false; // lines increasing along the walk
+    float kx = 0.f, ky = 0.f;        // slabs per unit of each line (1 / slope)
+    int Na = 0, Nb = 0, ca = 0, cb = 0;  // lateral sizes and centres
+    int Ns = 0, sstride = 0, astride = 0, bstride = 0;  // slab count, memory strides
+    bool rev = false;                // walk runs towards decreasing slab index
+    float ksrc = 0.f, kpix = 0.f;    // slab coordinate of the source and of the pixel
+    int k_lo = INT_MAX, k_hi = -1;   // slabs that may hold a part of the ray
+    int k_in0 = INT_MIN, k_in1 = INT_MAX;  // slabs wholly inside the volume
+    float lsig = 0.f;                // mm of ray per slab
+    bool transposed = false;         // offsets index the [z][x][y] copy
 };
 
-// Clip to the box and the source..pixel segment; fills the walk range and
-// the mm-per-w factor.  Ns, Na, Nb: sizes along the slab and lateral axes.
-__device__ __forceinline__ bool ray_clip(Ray &r, int Ns, int Na, int Nb, int ca, int cb,
-                                         float wsrc, float wpix, float hs, float ha, float hb) {
-    r.invA = 1.f / r.A;
-    r.invC = 1.f / r.C;
-    r.fa_lo = (float)(-ca);
-    r.fa_hi = (float)(Na - 1 - ca);
-    r.fb_lo = (float)(-cb);
-    r.fb_hi = (float)(Nb - 1 - cb);
-    float lo = fmaxf((float)(-r.cs), wsrc), hi = fminf((float)(Ns - r.cs), wpix);
-    if (r.A != 0.f) {
-        const float t0 = ((float)(-ca) - r.xi0) * r.invA, t1 = ((float)(Na - ca) - r.xi0) * r.invA;
-        lo = fmaxf(lo, fminf(t0, t1));
-        hi = fminf(hi, fmaxf(t0, t1));
-    } else if (!(r.xi0 >= (float)(-ca) && r.xi0 < (float)(Na - ca))) {
-        return false;
-    }
-    if (r.C != 0.f) {
-        const float t0 = ((float)(-cb) - r.ze0) * r.invC, t1 = ((float)(Nb - cb) - r.ze0) * r.invC;
-        lo = fmaxf(lo, fminf(t0, t1));
-        hi = fminf(hi, fmaxf(t0, t1));
-    } else if (!(r.ze0 >= (float)(-cb) && r.ze0 < (float)(Nb - cb))) {
-        return false;
-    }
-    if (!(lo < hi)) return false;
-    r.w_in = lo;
-    r.w_out = hi;
-    r.k_first = max(0, (int)floorf(lo) + r.cs);
-    r.k_last = min(Ns - 1, (int)ceilf(hi) - 1 + r.cs);
-    if (r.k_first > r.k_last) return false;
-    const float la = r.A * (ha / hs), lb = r.C * (hb / hs);
-    r.lsig = hs * sqrtf(fmaf(la, la, fmaf(lb, lb, 1.f)));
-    return true;
+// Q.44 (value * 2^44) -> the Q.32 line at the start of slab 0, its step and
+// direction; cs is the centre slab.
+__device__ __forceinline__ void ray_line(long long a, long long xi, int cs, long long &X0,
+                                         unsigned &dX, bool &up) {
+    X0 = (xi - a * cs) >> 12;
+    dX = (unsigned)min(((unsigned long long)llabs(a) + 2048ull) >> 12, 0xffffffffull);
+    up = a > 0 && dX != 0u;
 }
 
 // Ray (u, v) of one view; returns false if it misses the volume box.
-// Rays advancing mostly along x or y use the per-column FP64-derived
-// parameters; the rare rays advancing mostly along z (very large cone angles)
-// are set up from the per-view constants in FP32.
 __device__ __forceinline__ bool ray_setup(const ProjGeom &g, int view, int u, int v, Ray &r) {
-    const float vc = (float)v - 0.5f * (float)(g.nv - 1);
-    const size_t ci = (size_t)view * g.nu + u;
-    const float4 pa = __ldg(g.col_a + ci);
-    const float4 pb = __ldg(g.col_b + ci);
-    const int fl = __ldg(g.col_flags + ci);
-    const float C = fmaf(vc, pa.w, pa.z);
-    if (fabsf(C) <= 1.f) {
-        int Ns, Na, sstride;
-        float hs, ha;
-        if (fl & 1) {            // slabs along x; lateral a = y; transposed copy [z][x][y]
-            Ns = g.nx; Na = g.ny; sstride = g.ny; hs = g.hx; ha = g.hy;
+    const longlong2 *q = reinterpret_cast<const longlong2 *>(g.col_q + ((size_t)view * g.nu + u));
+    const longlong2 qa = __ldg(q), qc = __ldg(q + 1), qz = __ldg(q + 2);
+    const float4 qw = __ldg(reinterpret_cast<const float4 *>(q + 3));
+    const int fl = __float_as_int(qw.z);
+    const long long vc2 = 2LL * v - (g.nv - 1);
+    const long long c = qc.x + vc2 * qc.y;
+    float hs, ha, hb, wsrc, wpix;
+    int cs;
+    if (!(fl & 4) && llabs(c) <= (1LL << 44)) {
+        // advancing along x or y: line a = the column's lateral line, b = z
+        if (fl & 1) {   // slabs along x, lateral y: [z][x][y]
+            r.Ns = g.nx; r.Na = g.ny; r.sstride = g.ny; hs = g.hx; ha = g.hy;
             r.transposed = true;
-        } else {                 // slabs along y; lateral a = x
-            Ns = g.ny; Na = g.nx; sstride = g.nx; hs = g.hy; ha = g.hx;
+        } else {        // slabs along y, lateral x: [z][y][x]
+            r.Ns = g.ny; r.Na = g.nx; r.sstride = g.nx; hs = g.hy; ha = g.hx;
             r.transposed = false;
         }
-        const int Nb = g.nz, ca = Na / 2, cb = Nb / 2;
-        r.cs = Ns / 2;
+        r.Nb = g.nz;
+        r.astride = 1;
         r.bstride = g.nx * g.ny;
-        if (fl & 2) {
-            r.soff0 = (Ns - 1) * sstride;
-            r.sstep = -sstride;
-        } else {
-            r.soff0 = 0;
-            r.sstep = sstride;
-        }
-        r.soff0 += ca + cb * r.bstride;
-        r.A = pa.x;
-        r.xi0 = pa.y;
-        r.C = C;
-        r.ze0 = fmaf(vc, pb.y, pb.x);
-        return ray_clip(r, Ns, Na, Nb, ca, cb, pb.z, pb.w, hs, ha, g.hz);
-    }
-    // slabs along z; lateral a = x, b = y; main layout
-    const ViewConst *vcp = g.views + view;
-    const float uc = (float)u - 0.5f * (float)(g.nu - 1);
-    float S[3], D[3];
-    for (int a = 0; a < 3; ++a) {
-        S[a] = __ldg(&vcp->s[a]);
-        const float p = fmaf(vc, __ldg(&vcp->ev[a]), fmaf(uc, __ldg(&vcp->eu[a]), __ldg(&vcp->p00[a])));
-        D[a] = p - S[a];
-    }
-    const int Ns = g.nz, Na = g.nx, Nb = g.ny, ca = Na / 2, cb = Nb / 2;
-    const int sstride = g.nx * g.ny;
-    r.cs = Ns / 2;
-    r.bstride = g.nx;
-    r.transposed = false;
-    const bool rev = D[2] < 0.f;
-    if (rev) {
-        r.soff0 = (Ns - 1) * sstride;
-        r.sstep = -sstride;
+        hb = g.hz;
+        r.rev = (fl & 2) != 0;
+        cs = r.Ns / 2;
+        ray_line(qa.x, qa.y, cs, r.X0, r.dX, r.x_up);
+        ray_line(c, qz.x + vc2 * qz.y, cs, r.Y0, r.dY, r.y_up);
+        wsrc = qw.x;
+        wpix = qw.y;
     } else {
-        r.soff0 = 0;
-        r.sstep = sstride;
+        // advancing along z: slabs along z, lines x (a) and y (b), [z][y][x]
+        const ViewConst &vw = g.views[view];
+        const double uc = (double)u - 0.5 * (double)(g.nu - 1);
+        const double vc = (double)v - 0.5 * (double)(g.nv - 1);
+        double S[3], D[3];
+        for (int a = 0; a < 3; ++a) {
+            S[a] = vw.s[a];
+            D[a] = fma(vc, vw.ev[a], fma(uc, vw.eu[a], vw.p00[a])) - S[a];
+        }
+        if (!(D[2] != 0.0)) return false;
+        r.Ns = g.nz; r.Na = g.nx; r.Nb = g.ny;
+        r.sstride = g.nx * g.ny; r.astride = 1; r.bstride = g.nx;
+        hs = g.hz; ha = g.hx; hb = g.hy;
+        r.transposed = false;
+        r.rev = D[2] < 0.0;
+        cs = r.Ns / 2;
+        const double sig0 = r.rev ? (double)(r.Ns - cs) : (double)cs;
+        const double adz = fabs(D[2]), t = (sig0 - S[2]) / D[2];
+        const double lim = 65536.0;   // a ray this far out misses the volume
+        const double xi = fmin(fmax(S[0] - (double)(g.nx / 2) + t * D[0], -lim), lim);
+        const double yi = fmin(fmax(S[1] - (double)(g.ny / 2) + t * D[1], -lim), lim);
+        ray_line(__double2ll_rn(ldexp(D[0] / adz, 44)), __double2ll_rn(ldexp(xi, 44)), cs, r.X0,
+                 r.dX, r.x_up);
+        ray_line(__double2ll_rn(ldexp(D[1] / adz, 44)), __double2ll_rn(ldexp(yi, 44)), cs, r.Y0,
+                 r.dY, r.y_up);
+        wsrc = (float)((r.rev ? (double)r.Ns - S[2] : S[2]) - (double)cs);
+        wpix = (float)((r.rev ? (double)r.Ns - (S[2] + D[2]) : S[2] + D[2]) - (double)cs);
     }
-    r.soff0 += ca + cb * r.bstride;
-    const float ad = fabsf(D[2]);
-    if (!(ad > 0.f)) return false;
-    const float sig0 = rev ? (float)(Ns - r.cs) : (float)r.cs;
-    const float t0 = (sig0 - S[2]) / D[2];
-    r.A = D[0] / ad;
-    r.C = D[1] / ad;
-    r.xi0 = fmaf(t0, D[0], S[0] - (float)ca);
-    r.ze0 = fmaf(t0, D[1], S[1] - (float)cb);
-    const float wsrc = (rev ? (float)Ns - S[2] : S[2]) - (float)r.cs;
-    const float wpix = (rev ? (float)Ns - (S[2] + D[2]) : S[2] + D[2]) - (float)r.cs;
-    return ray_clip(r, Ns, Na, Nb, ca, cb, wsrc, wpix, g.hz, g.hx, g.hy);
+    r.ca = r.Na / 2;
+    r.cb = r.Nb / 2;
+    const float af = (float)r.dX * 0x1p-32f, bf = (float)r.dY * 0x1p-32f;
+    r.kx = 1.f / af;
+    r.ky = 1.f / bf;
+    r.ksrc = wsrc + (float)cs;
+    r.kpix = wpix + (float)cs;
+    // slab ranges from the integer lines, as in cm_setup below
+    float e = fmaxf(0.f, r.ksrc), x = fminf((float)r.Ns, r.kpix);
+    bool ok = true;
+    if (r.dX != 0u) {
+        const float s = r.x_up ? (float)r.dX : -(float)r.dX;
+        const float t0 = plane_k(-r.ca, r.X0, s), t1 = plane_k(r.Na - r.ca, r.X0, s);
+        e = fmaxf(e, fminf(t0, t1));
+        x = fminf(x, fmaxf(t0, t1));
+    } else {
+        ok = r.X0 >= ((long long)(-r.ca) << 32) && r.X0 < ((long long)(r.Na - r.ca) << 32);
+    }
+    if (r.dY != 0u) {
+        const float s = r.y_up ? (float)r.dY : -(float)r.dY;
+        const float t0 = plane_k(-r.cb, r.Y0, s), t1 = plane_k(r.Nb - r.cb, r.Y0, s);
+        e = fmaxf(e, fminf(t0, t1));
+        x = fminf(x, fmaxf(t0, t1));
+    } else {
+        ok = ok && r.Y0 >= ((long long)(-r.cb) << 32) && r.Y0 < ((long long)(r.Nb - r.cb) << 32);
+    }
+    ok = ok && e < x;
+    e = fminf(fmaxf(e, -2.f), (float)r.Ns + 2.f);
+    x = fminf(fmaxf(x, -2.f), (float)r.Ns + 2.f);
+    const float de = fmaf(fabsf(e), 0x1p-16f, 0x1p-16f), dx = fmaf(fabsf(x), 0x1p-16f, 0x1p-16f);
+    r.k_lo = max(0, (int)floorf(e - de));
+    r.k_hi = min(r.Ns - 1, (int)floorf(x + dx));
+    r.k_in0 = (int)ceilf(e + de);
+    r.k_in1 = (int)floorf(x - dx) - 1;
+    ok = ok && r.k_lo <= r.k_hi;
+    const float la = af * (ha / hs), lb = bf * (hb / hs);
+    r.lsig = hs * sqrtf(fmaf(la, la, fmaf(lb, lb, 1.f)));
+    return ok;
 }
 
-// Warp-synchronous slab walk.  fn(offset, w_length, p) is called for the
-// segments of each slab.  p says whether the segment may be accessed: when p
-// is set the offset is inside the volume (the length may still be zero or a
-// rounding-size negative, which contributes nothing); when p is clear fn
-// must not touch memory.
-// Must be called by all 32 lanes of the warp.
-//
-// Per lane the walk keeps an integer voxel offset and, per lateral axis, the
-// w of the next plane crossing; a crossing moves the offset by the axis
-// stride and recomputes the next crossing directly from its plane index (the
-// same expression the box clip uses, so a lane never steps through the exit
-// face).  All per-lane decisions are selects, so lanes never diverge.  A slab
-// in which no lane of the warp crosses a z plane (the common case: rows of a
-// warp cross the same z planes at nearly the same slab) has at most one
-// lateral crossing per lane and takes the short path; otherwise the whole
-// warp takes the general path with up to three segments.  Lanes outside
-// their own range, or without a ray, clamp their slab to an empty interval;
-// the interior slabs, which every lane of a full warp covers entirely, skip
-// that clamp.
+// Warp-synchronous slab walk; fn(offset, length in slabs, p) is called for
+// the segments of each slab and may touch memory only where p is set (the
+// offset is then inside the volume).  Must be called by all 32 lanes of the
+// warp.  Every lane walks its own lines; the loop runs over the slabs any
+// lane's ray may touch.  In the interior (slabs wholly inside the volume and
+// the source..pixel part for every ray of the warp) a slab holds the lane's
+// current voxel, the next one along whichever line crosses first and, where
+// both cross, the diagonal one, all in range; the other slabs check each
+// segment's indices and clip to the source..pixel part.  A lane without a
+// ray (ok false) keeps offset 0 with zero steps and sets no p.
 template <class Fn>
-__device__ __forceinline__ void walk(const Ray &r, bool valid, Fn &&fn) {
+__device__ __forceinline__ void walk(const Ray &r, bool ok, Fn &&fn) {
     const unsigned full = 0xffffffffu;
-    const int kb = __reduce_min_sync(full, valid ? r.k_first : INT_MAX);
-    const int ke = __reduce_max_sync(full, valid ? r.k_last : -1);
+    const int kb = __reduce_min_sync(full, ok ? r.k_lo : INT_MAX);
+    const int ke = __reduce_max_sync(full, ok ? r.k_hi : -1);
     if (kb > ke) return;
-    // interior slabs [k_mid0, k_mid1]: after every lane's entry slab and
-    // before every lane's exit slab, only when all 32 lanes hold a ray
-    int k_mid0 = __reduce_max_sync(full, valid ? r.k_first : INT_MAX) + 1;
-    int k_mid1 = __reduce_min_sync(full, valid ? r.k_last : -1) - 1;
-    if (!__all_sync(full, valid) || k_mid0 > k_mid1) {
-        k_mid0 = ke + 1;
-        k_mid1 = ke;
-    }
-    const float w_in = valid ? r.w_in : 0.f, w_out = valid ? r.w_out : 0.f;
-    const float fi = fminf(fmaxf(floorf(fmaf(w_in, r.A, r.xi0)), r.fa_lo), r.fa_hi);
-    const float fk = fminf(fmaxf(floorf(fmaf(w_in, r.C, r.ze0)), r.fb_lo), r.fb_hi);
-    const bool neg_a = r.A < 0.f, neg_b = r.C < 0.f;
-    const float sa = neg_a ? -1.f : 1.f, sb = neg_b ? -1.f : 1.f;
-    const int da = neg_a ? -1 : 1, db = neg_b ? -r.bstride : r.bstride;
-    const float xi0 = r.xi0, ze0 = r.ze0, invA = r.invA, invC = r.invC;
-    float px = neg_a ? fi : fi + 1.f;  // next lateral planes in the direction of travel
-    float pz = neg_b ? fk : fk + 1.f;
-    float w_nx = (valid && r.A != 0.f) ? (px - xi0) * invA : INFINITY;
-    float w_nz = (valid && r.C != 0.f) ? (pz - ze0) * invC : INFINITY;
-    int off = valid ? r.soff0 + kb * r.sstep + (int)fi + (int)fk * r.bstride : 0;
-    const int sstep = r.sstep;
-    float wk = (float)(kb - r.cs);
-    float w_lo = fminf(fmaxf(wk, w_in), w_out);
-    auto slab = [&](auto clamp) {
-        wk += 1.f;
-        const float w_hi = decltype(clamp)::value ? fminf(fmaxf(wk, w_in), w_out) : wk;
-        const bool cx = w_nx < w_hi;
-        const float sx = fminf(w_nx, w_hi);
-        const int dax = cx ? da : 0;
-        if (!__any_sync(full, w_nz < w_hi)) {
-            // interior slabs: every lane is inside its range, so its first
-            // segment is always a real voxel; the second exists iff cx
-            fn(off, sx - w_lo, decltype(clamp)::value ? (sx - w_lo > 0.f) : true);
-            off += dax;
-            fn(off, w_hi - sx, cx);
-        } else {
-            const bool cz = w_nz < w_hi;
-            const float sz = fminf(w_nz, w_hi);
-            const float s1 = fminf(sx, sz), s2 = fmaxf(sx, sz);
-            const int dbz = cz ? db : 0;
-            fn(off, s1 - w_lo, s1 - w_lo > 0.f);
-            fn(off + (sx <= sz ? dax : dbz), s2 - s1, s2 - s1 > 0.f);
-            off += dax + dbz;
-            fn(off, w_hi - s2, w_hi - s2 > 0.f);
-            if (cz) {
-                pz += sb;
-                w_nz = (pz - ze0) * invC;
-            }
-        }
+    const int k_mid0 = max(kb, __reduce_max_sync(full, ok ? r.k_in0 : INT_MIN));
+    const int k_mid1 = min(ke, __reduce_min_sync(full, ok ? r.k_in1 : INT_MAX));
+    const long long X = r.X0 + (r.x_up ? (long long)kb * r.dX : -(long long)kb * r.dX);
+    const long long Y = r.Y0 + (r.y_up ? (long long)kb * r.dY : -(long long)kb * r.dY);
+    int ai = (int)((r.x_up ? X - 1 : X) >> 32) + r.ca;   // lateral indices (may lie outside)
+    int bi = (int)((r.y_up ? Y - 1 : Y) >> 32) + r.cb;
+    unsigned phi = r.x_up ? (unsigned)(-X) : (unsigned)X;
+    unsigned psi = r.y_up ? (unsigned)(-Y) : (unsigned)Y;
+    const unsigned dX = ok ? r.dX : 0u, dY = ok ? r.dY : 0u;
+    const float kx = r.kx, ky = r.ky;
+    const int Na = r.Na, Nb = r.Nb;
+    const unsigned sstep = !ok ? 0u : r.rev ? 0u - (unsigned)r.sstride : (unsigned)r.sstride;
+    const unsigned astep = !ok ? 0u : r.x_up ? (unsigned)r.astride : 0u - (unsigned)r.astride;
+    const unsigned bstep = !ok ? 0u : r.y_up ? (unsigned)r.bstride : 0u - (unsigned)r.bstride;
+    const int da = r.x_up ? 1 : -1, db = r.y_up ? 1 : -1;
+    unsigned o = !ok ? 0u
+                     : (r.rev ? (unsigned)(r.Ns - 1) * (unsigned)r.sstride : 0u) +
+                           (unsigned)kb * sstep + (unsigned)ai * (unsigned)r.astride +
+                           (unsigned)bi * (unsigned)r.bstride;
+    const float ksrc = ok ? r.ksrc : 0.f, kpix = ok ? r.kpix : 0.f;
+    // the lanes of a warp may walk different axes: the loop runs over the
+    // union of their slabs, and a lane's own slab index must be checked too
+    const unsigned Nsl = ok ? (unsigned)r.Ns : 0u;
+    auto clamped = [&](int k) {
+        const bool cx = phi < dX, cy = psi < dY;
+        const float sx = cx ? fmaf(one_plus_frac(phi), kx, -kx) : 1.f;
+        const float sy = cy ? fmaf(one_plus_frac(psi), ky, -ky) : 1.f;
+        const float s1 = fminf(sx, sy), s2 = fmaxf(sx, sy);
+        const float kf = (float)k;
+        const float c_lo = fminf(fmaxf(ksrc - kf, 0.f), 1.f);
+        const float c_hi = fminf(fmaxf(kpix - kf, 0.f), 1.f);
+        const float b1 = fminf(fmaxf(s1, c_lo), c_hi), b2 = fminf(fmaxf(s2, c_lo), c_hi);
+        const float l1 = b1 - c_lo, l2 = b2 - b1, l3 = c_hi - b2;
+        const bool sk = (unsigned)k < Nsl;
+        const bool a0 = sk && (unsigned)ai < (unsigned)Na;
+        const bool a1 = sk && (unsigned)(ai + da) < (unsigned)Na;
+        const bool z0 = (unsigned)bi < (unsigned)Nb, z1 = (unsigned)(bi + db) < (unsigned)Nb;
+        const bool mx = sx <= sy;   // the middle segment is past the crossing of line a
+        fn((int)o, l1, a0 && z0 && l1 > 0.f);
+        fn((int)(o + (mx ? astep : bstep)), l2, (mx ? (a1 && z0) : (a0 && z1)) && l2 > 0.f);
+        fn((int)(o + (cx ? astep : 0u) + (cy ? bstep : 0u)), l3,
+           (cx ? a1 : a0) && (cy ? z1 : z0) && l3 > 0.f);
+        phi -= dX;
+        psi -= dY;
         if (cx) {
-            px += sa;
-            w_nx = (px - xi0) * invA;
+            ai += da;
+            o += astep;
         }
-        w_lo = w_hi;
-        off += sstep;
+        if (cy) {
+            bi += db;
+            o += bstep;
+        }
+        o += sstep;
     };
-    using clamped = std::integral_constant<bool, true>;
-    using interior = std::integral_constant<bool, false>;
+    // In the interior every offset handed to fn with p set is in range.
+    auto interior = [&]() {
+        const bool cx = phi < dX, cy = psi < dY;
+        const float sx = cx ? fmaf(one_plus_frac(phi), kx, -kx) : 1.f;
+        const float sy = cy ? fmaf(one_plus_frac(psi), ky, -ky) : 1.f;
+        const float s1 = fminf(sx, sy), s2 = fmaxf(sx, sy);
+        const unsigned ax = cx ? astep : 0u, by = cy ? bstep : 0u;
+        fn((int)o, s1, ok);
+        fn((int)(o + (sx <= sy ? astep : bstep)), s2 - s1, cx || cy);
+        fn((int)(o + ax + by), 1.f - s2, cx && cy);
+        phi -= dX;
+        psi -= dY;
+        o += sstep + ax + by;
+    };
     int k = kb;
-    for (; k < k_mid0; ++k) slab(clamped{});
+    const int k_entry_end = min(k_mid0, ke + 1);
+    for (; k < k_entry_end; ++k) clamped(k);
+    if (k <= k_mid1) {
 #pragma unroll 2
-    for (; k <= k_mid1; ++k) slab(interior{});
-    for (; k <= ke; ++k) slab(clamped{});
+        for (; k <= k_mid1; ++k) interior();
+        // the lateral indices, tracked only by the clamped slabs, from the offset
+        if (k <= ke && ok) {
+            const unsigned rem = o - (r.rev ? (unsigned)(r.Ns - 1) * (unsigned)r.sstride : 0u) -
+                                 (unsigned)k * sstep;
+            bi = (int)(rem / (unsigned)r.bstride);
+            ai = (int)((rem - (unsigned)bi * (unsigned)r.bstride) / (unsigned)r.astride);
+        }
+    }
+    for (; k <= ke; ++k) clamped(k);
 }
 
 // Predicated float reduction into global memory (no branch around it): the
@@ -544,18 +577,6 @@ struct CmRay {
     int k_in0 = INT_MIN, k_in1 = INT_MAX;  // slabs wholly inside the volume
     float lsig = 0.f;                // mm of ray per slab
 };
-
-// Slab coordinate at which the Q.32 line X(k) = X0 + k s reaches the integer
-// plane P (s: signed slope per slab, in units of 2^-32).
-__device__ __forceinline__ float plane_k(int P, long long X0, float s) {
-    return __ll2float_rn(((long long)P << 32) - X0) / s;
-}
-
-// 1 + q 2^-32 truncated to a float in [1, 2): the exponent bits of 1.0f
-// (0x7f << 23) funnel-shifted in above the top 23 bits of q.
-__device__ __forceinline__ float one_plus_frac(unsigned q) {
-    return __uint_as_float(__funnelshift_r(q, 0x7fu, 9));
-}
 
 // A load the compiler may not merge with an earlier load of the same address
 // (so that values re-derived from it need no register in between).

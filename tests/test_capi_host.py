@@ -65,6 +65,10 @@ def test_bad_geometry_rejected_before_cuda(built_lib):
     assert b"nv" in L.ct_last_error()
     d = ct._Desc(8, 8, 8, 1, 1, 1, 0, 0, 0, 8, 8, 1, 1, 0, 0, 750, 1200, 65536, None)
     assert L.ct_geometry_create(ctypes.byref(d), ctypes.byref(h)) == 1
+    # the walks' integer lines: nx and ny <= 65535 as well
+    d = ct._Desc(65536, 2, 2, 1, 1, 1, 0, 0, 0, 8, 8, 1, 1, 0, 0, 750, 1200, 4, None)
+    assert L.ct_geometry_create(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert b"nx, ny, nz" in L.ct_last_error()
 
 
 def test_solver_options_rejected_before_cuda(built_lib):

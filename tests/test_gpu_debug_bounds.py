@@ -17,6 +17,7 @@ pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 CHILD = r'''
+import ctypes
 import numpy as np, torch
 import paper_2110_13526_gb300 as ct
 import oracle, synth
@@ -36,6 +37,12 @@ cases = {
                   sid=80.0, sdd=140.0, nviews=5),
     "source_inside": dict(nx=16, ny=16, nz=8, vx=2.0, vy=2.0, vz=1.0, nu=16, nv=12, du=2.0,
                           dv=1.5, sid=12.0, sdd=40.0, nviews=6),
+    # steep rays advancing along z through a tall, narrow, off-centre volume
+    # with a far-shifted detector (ray-major kernels, both setups)
+    "steep": dict(nx=4, ny=5, nz=27, vx=1.37, vy=0.84, vz=1.31, ox=0.21, oy=-0.81, oz=7.27,
+                  nu=54, nv=11, du=0.2, dv=8.54, sid=12.34, sdd=16.52, nviews=8,
+                  det_off_u=-0.04, det_off_v=-28.28,
+                  angles=[1.436, 2.112, 3.517, 3.806, 3.985, 5.232, 5.249, 6.111]),
 }
 for name, cfg in cases.items():
     g, og = ct.Geometry(**cfg), oracle.OGeom(**cfg)
@@ -50,6 +57,15 @@ for name, cfg in cases.items():
     xb = torch.from_numpy(synth.random_field((2,) + g.vol_shape, seed=3)).cuda()
     yb = ct.project_batch(g, xb); ct.backproject_batch(g, yb); ct.debug_status()
     ct.count_nnz(g); ct.project_norm2(g, torch.from_numpy(x).cuda()); ct.debug_status()
+    xd = torch.from_numpy(x).cuda()
+    sd = torch.empty(g.sino_shape, device="cuda")
+    nd = torch.zeros((), dtype=torch.float64, device="cuda")
+    assert ct.lib().ct_project_norm2_noalloc(g.handle, ctypes.c_void_p(xd.data_ptr()),
+                                             ctypes.c_void_p(sd.data_ptr()), ctypes.c_float(1.0),
+                                             ctypes.c_float(0.0), ctypes.c_void_p(nd.data_ptr()),
+                                             None) == 0
+    assert rel(sd, oracle.project(og, x.astype(np.float64))) < 1e-5, name
+    ct.debug_status()
     b = torch.from_numpy(oracle.project(og, np.abs(x).astype(np.float64)).astype(np.float32)).cuda()
     for pc in ("none", "jacobi", "rowcol"):
         ct.cgls(g, b, max_iter=4, precond=pc); ct.debug_status()
