@@ -27,7 +27,10 @@
 // footprint into shared memory, so every voxel is written once, without
 // reductions; the transaxial footprint of a column and the u-weighted sums
 // of the detector rows under the segment are computed once per view and
-// segment.  Ramp reciprocals are taken once per trapezoid, not per cell.
+// segment.  Neighbouring voxels of a segment share their common z face: a
+// voxel's axial trapezoid is the difference of its two faces' ramps, so the
+// cells under each face are integrated once, not once per voxel.  Ramp
+// reciprocals are taken once per trapezoid or face, not per cell.
 // Coordinates are relative to the volume centre (per-view constants computed
 // in FP64 on the host), which keeps the FP32 breakpoints accurate.
 #include "ct_debug.cuh"
@@ -92,6 +95,20 @@ __device__ __forceinline__ float trap_cell(float t0, float t1, float t2, float t
     x2 = fminf(b, t3);
     if (x2 > x1) r += (x2 - x1) * (2.f * t3 - x1 - x2) * r23;
     return r;
+}
+
+// Integral over [a, b] of the ramp that rises from 0 at lo to 1 at hi and
+// stays 1 above (r = half_rcp(hi - lo)); RAMP false: a step at lo == hi.
+template <bool RAMP>
+__device__ __forceinline__ float ramp_cell(float lo, float hi, float r, float a, float b) {
+    float s = 0.f;
+    if (RAMP) {
+        const float x1 = fmaxf(a, lo), x2 = fminf(b, hi);
+        if (x2 > x1) s = (x2 - x1) * (x2 + x1 - 2.f * lo) * r;
+    }
+    const float x1 = fmaxf(a, hi);
+    if (b > x1) s += b - x1;
+    return s;
 }
 
 // Column (i, j) of view `view`: transaxial footprint, axial depths, amplitude.
@@ -233,7 +250,8 @@ __global__ void __launch_bounds__(256) k_sf_forward(ProjGeom g, const float *__r
 // the transaxial footprint of a column and view is computed once for the
 // whole segment, in passes of kSfKUF cells kept in registers, and so is the
 // u-weighted sum of each detector row under the segment (up to kSfRows rows
-// in shared memory; a segment spanning more rows sums them per voxel).
+// in shared memory; a segment spanning more rows sums them per voxel), and
+// the cell integrals under each z face of the segment (power 1).
 template <bool HAS_RHO, int POWER, bool TT>
 __global__ void __launch_bounds__(256) k_sf_backward(ProjGeom g, const float *__restrict__ e,
                                                      const float *__restrict__ rho, Coef cf,
@@ -275,17 +293,50 @@ __global__ void __launch_bounds__(256) k_sf_backward(ProjGeom g, const float *__
                     }
                     return su;
                 };
+                // The faces of the segment: face f is the bottom of voxel
+                // kz0 + f, seen as the ramp from lo (its lower projection)
+                // to hi (its upper one; TR: lo == hi, a step).  Both grow
+                // with z (every depth is positive), so voxel k's axial
+                // footprint is ramp_k - ramp_{k+1} wherever the two ramps
+                // do not overlap (hi_k <= lo_{k+1}), and its sum over the
+                // rows is W_k - W_{k+1} plus the rows wholly above ramp k
+                // and not above ramp k+1 (W_f: the ramp's cells weighted
+                // by the rows' sums).  Voxels whose ramps overlap sum their
+                // own trapezoid.  POWER 2 squares every cell and sums
+                // trapezoids throughout.
+                const bool faces = POWER == 1 && c.qb > 0.f;
+                auto face = [&](int f, float &lo, float &hi, int &a, int &b) {
+                    const float z = fmaf((float)(kz0 + f) - 0.5f * (float)g.nz, g.hz, g.sf_oz);
+                    const float p = fmaf(z, c.qa, g.sf_cv);
+                    const float q = TT ? fmaf(z, c.qb, g.sf_cv) : p;
+                    lo = fminf(p, q);
+                    hi = fmaxf(p, q);
+                    a = max(0, (int)floorf(lo + 0.5f));
+                    b = min(max((int)floorf(hi + 0.5f), -1), g.nv - 1);
+                };
                 // rows under the segment (v grows with z): their u-weighted
                 // sums once each, shared by the voxels above them
                 float vb[4], amp, vr01, vr23;
-                sf_axial<TT>(g, c, kz0, vb, amp, vr01, vr23);
-                const int lf = max(0, (int)floorf(vb[0] + 0.5f));
-                sf_axial<TT>(g, c, kz0 + nzs - 1, vb, amp, vr01, vr23);
-                const int ll = min(g.nv - 1, (int)floorf(vb[3] + 0.5f));
-                const bool cached = ll - lf < kSfRows;
-                if (cached)
-                    for (int l = lf; l <= ll; ++l) srow[l - lf][tid] = row_sum(l);
-                for (int dz = 0; dz < nzs; ++dz) {
+                int lf, ll;
+                if (faces) {
+                    float lo, hi;
+                    int a, b;
+                    face(0, lo, hi, lf, b);
+                    face(nzs, lo, hi, a, ll);
+                } else {
+                    sf_axial<TT>(g, c, kz0, vb, amp, vr01, vr23);
+                    lf = max(0, (int)floorf(vb[0] + 0.5f));
+                    sf_axial<TT>(g, c, kz0 + nzs - 1, vb, amp, vr01, vr23);
+                    ll = min(g.nv - 1, (int)floorf(vb[3] + 0.5f));
+                }
+                const unsigned ncached = ll - lf < kSfRows ? (unsigned)max(ll - lf + 1, 0) : 0u;
+                for (int l = lf; l < lf + (int)ncached; ++l) srow[l - lf][tid] = row_sum(l);
+                auto su_of = [&](int l) -> float {
+                    const unsigned r = (unsigned)(l - lf);
+                    return r < ncached ? srow[r][tid] : row_sum(l);
+                };
+                // voxel kz0 + dz from its own trapezoid
+                auto voxel_trap = [&](int dz) -> float {
                     sf_axial<TT>(g, c, kz0 + dz, vb, amp, vr01, vr23);
                     const int kv0 = max(0, (int)floorf(vb[0] + 0.5f));
                     const int kv1 = min(g.nv - 1, (int)floorf(vb[3] + 0.5f));
@@ -294,14 +345,52 @@ __global__ void __launch_bounds__(256) k_sf_backward(ProjGeom g, const float *__
                         const float fv = trap_cell(vb[0], vb[1], vb[2], vb[3], vr01, vr23,
                                                    (float)l - 0.5f, (float)l + 0.5f);
                         if (fv == 0.f) continue;
-                        const unsigned r = (unsigned)(l - lf);
-                        const float su =
-                            cached && r < (unsigned)kSfRows ? srow[r][tid] : row_sum(l);
-                        s = POWER == 1 ? fmaf(fv, su, s) : fmaf(fv * fv, su, s);
+                        s = POWER == 1 ? fmaf(fv, su_of(l), s) : fmaf(fv * fv, su_of(l), s);
                     }
-                    if (s != 0.f)
-                        sacc[dz][tid] = POWER == 1 ? fmaf(amp, s, sacc[dz][tid])
-                                                   : fmaf(amp * amp, s, sacc[dz][tid]);
+                    return s;
+                };
+                if (faces) {
+                    auto ramp_sum = [&](float lo, float hi, int a, int b) -> float {
+                        const float r = TT ? half_rcp(hi - lo) : 0.f;
+                        float w = 0.f;
+                        for (int l = a; l <= b; ++l)
+                            w = fmaf(ramp_cell<TT>(lo, hi, r, (float)l - 0.5f, (float)l + 0.5f),
+                                     su_of(l), w);
+                        return w;
+                    };
+                    float lo0, hi0, w0;
+                    int a0, b0;
+                    face(0, lo0, hi0, a0, b0);
+                    w0 = ramp_sum(lo0, hi0, a0, b0);
+                    for (int dz = 0; dz < nzs; ++dz) {
+                        float lo1, hi1;
+                        int a1, b1;
+                        face(dz + 1, lo1, hi1, a1, b1);
+                        const float w1 = ramp_sum(lo1, hi1, a1, b1);
+                        float s;
+                        if (hi0 <= lo1) {
+                            s = w0 - w1;
+                            for (int l = max(b0 + 1, 0); l <= b1; ++l) s += su_of(l);
+                        } else {
+                            s = voxel_trap(dz);
+                        }
+                        if (s != 0.f) {
+                            const float z = g.sf_oz + ((float)(kz0 + dz) - 0.5f * (float)(g.nz - 1)) * g.hz;
+                            amp = c.m * sqrtf(fmaf(z, z, c.dxy2));
+                            sacc[dz][tid] = fmaf(amp, s, sacc[dz][tid]);
+                        }
+                        lo0 = lo1;
+                        hi0 = hi1;
+                        w0 = w1;
+                        b0 = b1;
+                    }
+                } else {
+                    for (int dz = 0; dz < nzs; ++dz) {
+                        const float s = voxel_trap(dz);
+                        if (s != 0.f)
+                            sacc[dz][tid] = POWER == 1 ? fmaf(amp, s, sacc[dz][tid])
+                                                       : fmaf(amp * amp, s, sacc[dz][tid]);
+                    }
                 }
             }
         }

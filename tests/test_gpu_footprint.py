@@ -30,6 +30,11 @@ CASES = {
                    sid=150.0, sdd=250.0, nviews=7),
     "fine": dict(nx=10, ny=9, nz=8, vx=3.0, vy=3.0, vz=3.0, nu=150, nv=120, du=0.25, dv=0.3,
                  sid=100.0, sdd=180.0, nviews=5),
+    # source 2.7 mm from the nearest voxel corner: in TT the projections of a
+    # z face at the nearest and farthest depth spread wider than the voxel's
+    # height, so neighbouring faces overlap (about half the voxel-views)
+    "steep": dict(nx=8, ny=8, nz=24, vx=2.0, vy=2.0, vz=1.0, nu=40, nv=40, du=3.0, dv=3.0,
+                  sid=14.0, sdd=30.0, nviews=5, det_off_u=0.7, det_off_v=-1.1),
 }
 
 
