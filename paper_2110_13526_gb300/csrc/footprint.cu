@@ -212,9 +212,15 @@ __global__ void __launch_bounds__(256) k_sf_forward(ProjGeom g, const float *__r
             fu[q] = q < nk ? trap_cell(c.tau[0], c.tau[1], c.tau[2], c.tau[3], c.r01, c.r23,
                                        (float)(k0 + q) - 0.5f, (float)(k0 + q) + 0.5f)
                            : 0.f;
+        const size_t col = (size_t)j * g.nx + i;
+        auto load = [&](int k) -> float {
+            const size_t vi = (size_t)k * plane + col;
+            return UNIT_VOL || !CT_IN_BOUNDS(vi, plane * g.nz) ? 1.f : vol[vi];
+        };
+        float xn = load(0);  // each voxel's value is loaded one voxel ahead
         for (int k = 0; k < g.nz; ++k) {
-            const size_t vi = (size_t)k * plane + (size_t)j * g.nx + i;
-            const float xv = UNIT_VOL || !CT_IN_BOUNDS(vi, plane * g.nz) ? 1.f : vol[vi];
+            const float xv = xn;
+            if (k + 1 < g.nz) xn = load(k + 1);
             if (xv == 0.f) continue;
             float vb[4], amp, vr01, vr23;
             sf_axial<TT>(g, c, k, vb, amp, vr01, vr23);
