@@ -89,6 +89,34 @@ def test_forward_backward_parity(ct, name, kind):
     assert rel(vo.cpu().numpy(), 0.25 * ofp.backproject(og, y, k) - v0) < TOL
 
 
+# degenerate sizes: one voxel, one slice (a single segment with one face pair
+# per column), one detector row (most faces' ramps clipped off the detector)
+DEGENERATE = {
+    "single_voxel": dict(nx=1, ny=1, nz=1, vx=3.0, vy=3.0, vz=3.0, nu=5, nv=3, du=1.0, dv=1.0,
+                         sid=50.0, sdd=90.0, nviews=4, angles=[0.1, 1.3, 2.9, 4.4]),
+    "one_slice": dict(nx=12, ny=9, nz=1, vx=1.0, vy=1.1, vz=2.0, nu=20, nv=4, du=1.0, dv=1.0,
+                      sid=60.0, sdd=100.0, nviews=5, det_off_v=0.3),
+    "one_row": dict(nx=10, ny=10, nz=6, vx=1.0, vy=1.0, vz=1.0, nu=18, nv=1, du=1.2, dv=3.0,
+                    sid=60.0, sdd=100.0, nviews=5, det_off_v=0.4),
+}
+
+
+@pytest.mark.parametrize("kind", ["sf_tr", "sf_tt"])
+@pytest.mark.parametrize("name", sorted(DEGENERATE))
+def test_degenerate_sizes(ct, name, kind):
+    cfg = DEGENERATE[name]
+    og = oracle.OGeom(**cfg)
+    k = kind[3:]
+    x = np.abs(synth.random_field((cfg["nz"], cfg["ny"], cfg["nx"]), seed=70))
+    want = ofp.project(og, x, k)
+    y = synth.random_field(want.shape, seed=71)
+    want_r = ofp.backproject(og, y, k)
+    for det in (False, True):
+        g = ct.Geometry(**cfg, projector=kind, deterministic=det)
+        assert rel(ct.project(g, torch.from_numpy(x).cuda()).cpu().numpy(), want) < TOL
+        assert rel(ct.backproject(g, torch.from_numpy(y).cuda()).cpu().numpy(), want_r) < TOL
+
+
 @pytest.mark.parametrize("kind", ["sf_tr", "sf_tt"])
 def test_adjoint_nnz_and_norm(ct, kind):
     cfg = CASES["ragged"]

@@ -54,6 +54,13 @@ CASES = {
     # single voxel and a one-pixel detector
     "tiny": dict(nx=1, ny=1, nz=1, vx=3.0, vy=3.0, vz=3.0, nu=5, nv=3, du=1.0, dv=1.0,
                  sid=50.0, sdd=90.0, nviews=4, angles=[0.1, 1.3, 2.9, 4.4]),
+    # one slice and one detector row: column-major warps with a single ray
+    "slice_row": dict(nx=24, ny=17, nz=1, vx=1.0, vy=1.2, vz=2.0, nu=40, nv=1, du=1.0, dv=1.5,
+                      sid=80.0, sdd=140.0, nviews=7),
+    # one slice under a cone whose outer rows advance mostly along z (the
+    # ray-major kernels): only the rows near the source's height reach it
+    "slice_cone": dict(nx=20, ny=18, nz=1, vx=1.0, vy=1.0, vz=3.0, nu=30, nv=60, du=1.5,
+                       dv=2.5, sid=30.0, sdd=60.0, nviews=5, det_off_v=0.37),
 }
 
 
@@ -259,7 +266,7 @@ def test_host_tensors_round_trip(ct):
     assert torch.equal(p_host, p_dev)
 
 
-@pytest.mark.parametrize("name", ["ragged", "offcentre", "bigcone", "pairs"])
+@pytest.mark.parametrize("name", ["ragged", "offcentre", "bigcone", "pairs", "slice_row", "slice_cone"])
 def test_deterministic_backprojection(ct, name):
     """Fixed-point accumulation: bitwise repeatable, same parity bar."""
     cfg = CASES[name]
