@@ -191,6 +191,26 @@ def traffic_for(kernel: str):
     return float(ent["dram_bytes_per_launch"]) if ent else None
 
 
+def issue_roofline(ent: dict, seconds: float, clk: dict):
+    """The instruction-issue roofline of a projector kernel: its warp
+    instructions per launch (committed ncu count for the same source) over the
+    live launch time, against 4 warp instructions per clock on each of the
+    152 SMs at the median SM clock sampled under load (the maximum clock when
+    no sample was taken).  None when the source changed since the count."""
+    n = ent.get("warp_inst_per_launch") if ent else None
+    if not n:
+        return None
+    mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = 4.0 * 152 * mhz * 1e6
+    out = {"bound": "alu", "achieved": n / seconds, "peak": peak, "unit": "warp-inst/s",
+           "frac": n / seconds / peak, "warp_inst_per_launch": n,
+           "peak_meaning": "4 warp instructions per clock per SM x 152 SMs x %.0f MHz" % mhz}
+    sec = ent.get("red_sectors_per_launch")
+    if sec:
+        out["l2_reduction_sectors_per_s"] = sec / seconds
+    return out
+
+
 def kernel_report(kernel: str, seconds: float, nnz: int, algo_bytes: float) -> dict:
     """Per-kernel figures: live CUDA-event time, ray-voxel updates per second
     and effective gather bandwidth; DRAM bandwidth (ncu bytes over the live
@@ -377,7 +397,8 @@ def run_ours(a):
             "issue_busy": ent.get("issue_active"),
             "kernel": kname, "peak_source": peak_kind,
             "ms_per_launch": t_dom * 1e3,
-            "algorithmic_bytes_per_launch": by_dom}
+            "algorithmic_bytes_per_launch": by_dom,
+            "issue": issue_roofline(ent, t_dom, clk)}
     value = whole_job_rate(a.steps * K, world, ms)
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
