@@ -44,9 +44,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--iters", type=int, default=50, help="CGLS x updates per step")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="cgls", choices=["cgls", "ops", "serve", "precision"],
+    ap.add_argument("--mode", default="cgls", choices=["cgls", "ops", "serve", "precision", "pr1"],
                     help="ops: time ct_project and ct_backproject alone (profiling aid); "
-                         "serve: the continuous-batching request stream alone")
+                         "serve: the continuous-batching request stream alone; pr1: A, A^T "
+                         "and CGLS-20 on the 64^3 PR1 case, GPU beside the oracle")
     ap.add_argument("--requests", type=int, default=128, help="serve mode: requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serve mode: arrivals per second")
     ap.add_argument("--slots", type=int, default=8, help="serve mode: concurrent jobs")
@@ -630,6 +631,82 @@ def run_serve(a):
     return 0
 
 
+def run_pr1(a):
+    """The 64^3, 90-view PR1 case on both sides: the GPU's A and A^T
+    (CUDA events, median of 20) and ct_cgls with 20 updates (wall time with a
+    device sync, median of 5), beside the oracle's full A and A^T and its
+    CGLS-20 (FP64, OpenMP, on the host cores).  Each side projects its own b
+    from the same phantom and adds the same seeded 1 % noise."""
+    import numpy as np
+    import torch
+
+    import paper_2110_13526_gb300 as ct
+    import synth
+
+    torch.cuda.set_device(0)
+    cfg = synth.CONFIGS["PR1"]
+    g = ct.Geometry(**cfg)
+    x_true = synth.voxelize(synth.nested_phantom(64.0, seed=0), cfg)
+    xd = torch.from_numpy(x_true).cuda()
+    b_gpu = synth.gaussian_noise(ct.project(g, xd).cpu().numpy(), 0.01, seed=0)
+    bd = torch.from_numpy(b_gpu.astype(np.float32)).cuda()
+    y = torch.randn(g.sino_shape, device="cuda", generator=torch.Generator("cuda").manual_seed(7))
+    p = torch.empty(g.sino_shape, device="cuda")
+    r = torch.empty(g.vol_shape, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def ev(fn, n):
+        ts = []
+        for _ in range(n):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    for _ in range(max(a.warmup, 3)):
+        ct.project(g, xd, out=p)
+        ct.backproject(g, y, out=r)
+        ct.cgls(g, bd, max_iter=20)
+    ms_a = ev(lambda: ct.project(g, xd, out=p), 20)
+    ms_at = ev(lambda: ct.backproject(g, y, out=r), 20)
+    walls = []
+    for _ in range(5):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, rep = ct.cgls(g, bd, max_iter=20)
+        torch.cuda.synchronize()
+        walls.append(time.perf_counter() - t0)
+    gpu = {"A_ms": ms_a, "AT_ms": ms_at, "cgls20_s": statistics.median(walls),
+           "cgls20_nb_over_nb0": rep.history[-1]}
+
+    import oracle
+    from oracle.solvers import cgls as ocgls
+    oracle.build()
+    og = oracle.OGeom(**cfg)
+    th = oracle.default_threads()
+    x64 = x_true.astype(np.float64)
+    t0 = time.perf_counter()
+    p64 = oracle.project(og, x64, th)
+    t1 = time.perf_counter()
+    oracle.backproject(og, p64, th)
+    t2 = time.perf_counter()
+    b_or = synth.gaussian_noise(p64, 0.01, seed=0)
+    t3 = time.perf_counter()
+    res = ocgls(oracle.Operator(og, th), b_or, K=20)
+    t4 = time.perf_counter()
+    orc = {"A_s": t1 - t0, "AT_s": t2 - t1, "cgls20_s": t4 - t3,
+           "cgls20_nb_over_nb0": float(res.history[-1]), "cores": th}
+    print(json.dumps({"mode": "pr1", "config": {"workload": "PR1: 64^3 nested phantom (1 mm), "
+                                                 "128x96 detector (1 mm), 90 views, 1 % noise"},
+                      "gpu": gpu, "oracle": orc,
+                      "ratio": {"A": orc["A_s"] * 1e3 / ms_a, "AT": orc["AT_s"] * 1e3 / ms_at,
+                                "cgls20": orc["cgls20_s"] / gpu["cgls20_s"]}}))
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -640,6 +717,8 @@ def main():
         return run_serve(a)
     if a.mode == "precision":
         return run_precision(a)
+    if a.mode == "pr1":
+        return run_pr1(a)
     return run_ours(a)
 
 
