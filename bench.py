@@ -44,10 +44,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--iters", type=int, default=50, help="CGLS x updates per step")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="cgls", choices=["cgls", "ops", "serve", "precision", "pr1"],
+    ap.add_argument("--mode", default="cgls", choices=["cgls", "ops", "serve", "precision", "pr1",
+                                                     "diff"],
                     help="ops: time ct_project and ct_backproject alone (profiling aid); "
                          "serve: the continuous-batching request stream alone; pr1: A, A^T "
-                         "and CGLS-20 on the 64^3 PR1 case, GPU beside the oracle")
+                         "and CGLS-20 on the 64^3 PR1 case, GPU beside the oracle; diff: the batched "
+                         "autograd operators on 8 x 128^3 volumes")
     ap.add_argument("--requests", type=int, default=128, help="serve mode: requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serve mode: arrivals per second")
     ap.add_argument("--slots", type=int, default=8, help="serve mode: concurrent jobs")
@@ -707,6 +709,69 @@ def run_pr1(a):
     return 0
 
 
+def run_diff(a):
+    """The differentiation workload: a batch of 8 volumes of 128^3 (192 x 144
+    detector, 180 views) through the autograd operators.  CUDA events, median
+    of 10 after warm-up: batched A and A^T (one persistent projector launch
+    per batch), the loss ||A x - b||^2 with its gradient (one A and one A^T),
+    and the checkpointed unrolled CGLS with 10 updates, forward and backward."""
+    import numpy as np
+    import torch
+
+    import paper_2110_13526_gb300 as ct
+    from paper_2110_13526_gb300.autograd import A, AT, unrolled_cgls
+    import synth
+
+    torch.cuda.set_device(0)
+    cfg = synth.CONFIGS["DIFF"]
+    g = ct.Geometry(**cfg)
+    lo, hi = synth.box_of(cfg)
+    xs = [synth.voxelize(synth.random_ellipsoids(20, 100 + i, lo, hi, axis_scale=0.5), cfg)
+          for i in range(8)]
+    x_true = torch.from_numpy(np.stack(xs)).cuda()
+    gen = torch.Generator("cuda").manual_seed(4)
+    with torch.no_grad():
+        b = A(g, x_true) + 0.01 * torch.randn(8, *g.sino_shape, device="cuda", generator=gen)
+    x = (x_true + 0.05 * torch.randn(x_true.shape, device="cuda",
+                                     generator=torch.Generator("cuda").manual_seed(5)))
+    stream = torch.cuda.current_stream()
+
+    def ev(fn, n=10):
+        for _ in range(max(a.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(n):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    def grad_step():
+        xg = x.clone().requires_grad_(True)
+        ((A(g, xg) - b).double() ** 2).sum().backward()
+
+    def cgls_step():
+        bg = b.clone().requires_grad_(True)
+        unrolled_cgls(g, bg, K=10).sum().backward()
+
+    with torch.no_grad():
+        ms_a = ev(lambda: A(g, x))
+        ms_at = ev(lambda: AT(g, b))
+    ms_grad = ev(grad_step)
+    ms_cgls = ev(cgls_step, n=5)
+    print(json.dumps({"mode": "diff",
+                      "config": {"workload": "DIFF: 8 x 128^3 volumes (1 mm, 20-ellipsoid "
+                                             "phantoms), 192x144 detector (1.6 mm), 180 views"},
+                      "batch": 8, "A_ms": ms_a, "AT_ms": ms_at,
+                      "A_ms_per_volume": ms_a / 8, "AT_ms_per_volume": ms_at / 8,
+                      "loss_grad_ms": ms_grad, "unrolled_cgls10_fwd_bwd_ms": ms_cgls}))
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -719,6 +784,8 @@ def main():
         return run_precision(a)
     if a.mode == "pr1":
         return run_pr1(a)
+    if a.mode == "diff":
+        return run_diff(a)
     return run_ours(a)
 
 

@@ -28,6 +28,9 @@ CONFIGS: Dict[str, dict] = {
                  dv=1.0, sid=750.0, sdd=1200.0, nviews=360),
     "P512": dict(nx=512, ny=512, nz=512, vx=0.5, vy=0.5, vz=0.5, nu=768, nv=576, du=0.75,
                  dv=0.75, sid=750.0, sdd=1200.0, nviews=720),
+    # the differentiation workload: one geometry for a batch of 8 volumes
+    "DIFF": dict(nx=128, ny=128, nz=128, vx=1.0, vy=1.0, vz=1.0, nu=192, nv=144, du=1.6,
+                 dv=1.6, sid=750.0, sdd=1200.0, nviews=180),
 }
 
 
