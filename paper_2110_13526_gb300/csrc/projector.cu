@@ -116,7 +116,11 @@ __device__ __forceinline__ void ray_line(long long a, long long xi, int cs, long
     up = a > 0 && dX != 0u;
 }
 
-// Ray (u, v) of one view; returns false if it misses the volume box.
+// Ray (u, v) of one view; returns false if it misses the volume box.  With
+// DIRECT every ray's offsets index the caller's layout [z][y][x] (a ray
+// advancing along x then steps by 1 per slab and by nx along its lateral
+// line), for the kernel that reads the volume in place.
+template <bool DIRECT = false>
 __device__ __forceinline__ bool ray_setup(const ProjGeom &g, int view, int u, int v, Ray &r) {
     const longlong2 *q = reinterpret_cast<const longlong2 *>(g.col_q + ((size_t)view * g.nu + u));
     const longlong2 qa = __ldg(q), qc = __ldg(q + 1), qz = __ldg(q + 2);
@@ -128,15 +132,17 @@ __device__ __forceinline__ bool ray_setup(const ProjGeom &g, int view, int u, in
     int cs;
     if (!(fl & 4) && llabs(c) <= (1LL << 44)) {
         // advancing along x or y: line a = the column's lateral line, b = z
-        if (fl & 1) {   // slabs along x, lateral y: [z][x][y]
-            r.Ns = g.nx; r.Na = g.ny; r.sstride = g.ny; hs = g.hx; ha = g.hy;
-            r.transposed = true;
+        if (fl & 1) {   // slabs along x, lateral y: [z][x][y] (DIRECT: [z][y][x])
+            r.Ns = g.nx; r.Na = g.ny; hs = g.hx; ha = g.hy;
+            r.sstride = DIRECT ? 1 : g.ny;
+            r.astride = DIRECT ? g.nx : 1;
+            r.transposed = !DIRECT;
         } else {        // slabs along y, lateral x: [z][y][x]
             r.Ns = g.ny; r.Na = g.nx; r.sstride = g.nx; hs = g.hy; ha = g.hx;
+            r.astride = 1;
             r.transposed = false;
         }
         r.Nb = g.nz;
-        r.astride = 1;
         r.bstride = g.nx * g.ny;
         hb = g.hz;
         r.rev = (fl & 2) != 0;
@@ -473,10 +479,10 @@ __global__ void __launch_bounds__(kTU *kTV) k_count(ProjGeom g,
 }
 
 // Variant of k_forward with the FP64 norm partials that reads only the
-// caller's volume in its own layout [nz][ny][nx]: the walk of a ray that
-// advances along x yields offsets of the transposed layout [z][x][y], mapped
-// back here.  Those rays gather with a stride of nx, so this is slower, but it
-// needs no transposed copy.
+// caller's volume in its own layout [nz][ny][nx]: every ray walks offsets of
+// that layout.  The lanes of a warp holding rays that advance along x
+// gather with a stride of nx (adjacent lanes are adjacent in y), so this is
+// slower, but it needs no transposed copy.
 __global__ void __launch_bounds__(kTU *kTV) k_forward_direct(ProjGeom g,
                                                              const float *__restrict__ vol,
                                                              float *__restrict__ out, float alpha,
@@ -487,19 +493,11 @@ __global__ void __launch_bounds__(kTU *kTV) k_forward_direct(ProjGeom g,
     tile_of(g, u, v, view);
     const bool inb = (u < g.nu) && (v < g.nv) && (view < g.nviews);
     Ray r;
-    const bool valid = inb && ray_setup(g, view, u, v, r);
-    const int nxy = g.nx * g.ny;
+    const bool valid = inb && ray_setup<true>(g, view, u, v, r);
+    const int64_t nvox = (int64_t)g.nx * g.ny * g.nz;
     float acc = 0.f;
     walk(r, valid, [&](int o, float l, bool p) {
-        if (p && l > 0.f) {
-            int oo = o;
-            if (r.transposed) {  // o = z nx ny + x ny + y  ->  z nx ny + y nx + x
-                const int z = o / nxy, rem = o - z * nxy;
-                const int x = rem / g.ny, y = rem - x * g.ny;
-                oo = z * nxy + y * g.nx + x;
-            }
-            if (CT_IN_BOUNDS(oo, nxy * (int64_t)g.nz)) acc = fmaf(l, __ldg(vol + oo), acc);
-        }
+        if (p && l > 0.f && CT_IN_BOUNDS(o, nvox)) acc = fmaf(l, __ldg(vol + o), acc);
     });
     double sq = 0.0;
     const size_t idx = ((size_t)view * g.nv + v) * g.nu + u;
