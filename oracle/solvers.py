@@ -33,8 +33,8 @@ algorithm it follows.
   The Discussion also says PSIRT keeps no column-sum vector; the variant that
   drops C for one scalar step lam / sigma_max (sigma_max the largest
   eigenvalue of A^T R^-1 A, power iteration) is ``variant="scalar"``.  It too
-  converges slower than SIRT.  Parity of PSIRT with the paper's own numbers
-  is unpinned.
+  converges slower than SIRT.  PSIRT against the paper's own numbers: parity
+  unpinned (its fixed point, the weighted normal equations, is pinned).
 * ``inv_sqrt_guarded`` / ``jacobi_weights`` / ``rowcol_weights`` -- the
   preconditioners of the Software and Discussion sections (Jacobi = diagonal
   of A^T A; row/column sums), with tiny sums (cone boundary) mapped to 0.
