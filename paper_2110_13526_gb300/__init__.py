@@ -338,10 +338,14 @@ def project_norm2(g: Geometry, vol: torch.Tensor, out: Optional[torch.Tensor] = 
                   alpha: float = 1.0, beta: float = 0.0, stream=None):
     """(out, ||out||^2 as a 0-d cuda float64 tensor) (ct_project_norm2)."""
     v = _dev(vol, g.vol_shape, "vol", g.device)
-    o = torch.empty(g.sino_shape, dtype=torch.float32, device=g.device) if out is None else out
+    o = (torch.empty(g.sino_shape, dtype=torch.float32, device=g.device) if out is None
+         else _dev(out, g.sino_shape, "out", g.device))
     nrm = torch.empty((), dtype=torch.float64, device=g.device)
     _check(lib().ct_project_norm2(g.handle, _ptr(v), _ptr(o), float(alpha), float(beta),
                                   _ptr(nrm), _stream(stream)))
+    if out is not None and o.data_ptr() != out.data_ptr():
+        out.copy_(o)
+        o = out
     return o, nrm
 
 
@@ -380,15 +384,17 @@ def _batched(fn, g: Geometry, t: torch.Tensor, in_shape, out_shape, name, alpha,
     x = t.reshape((-1,) + tuple(in_shape))
     if x.dtype != torch.float32:
         raise ValueError("%s: FP32 only" % name)
-    x = x.to(g.device).contiguous()
     nb = x.shape[0]
+    # out is checked before anything moves to the device
+    if out is not None and (out.dtype != torch.float32 or not out.is_cuda
+                            or not out.is_contiguous()
+                            or out.numel() != nb * out_shape[0] * out_shape[1] * out_shape[2]):
+        raise ValueError("%s: out must be a contiguous FP32 cuda tensor of %d items"
+                         % (name, nb))
+    x = x.to(g.device).contiguous()
     if out is None:
         o = torch.empty((nb,) + tuple(out_shape), dtype=torch.float32, device=g.device)
     else:
-        if out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous() \
-                or out.numel() != nb * out_shape[0] * out_shape[1] * out_shape[2]:
-            raise ValueError("%s: out must be a contiguous FP32 cuda tensor of %d items"
-                             % (name, nb))
         o = out
     _check(fn(g.handle, _ptr(x), _ptr(o), int(nb), float(alpha), float(beta), _stream(stream)))
     if out is not None:
