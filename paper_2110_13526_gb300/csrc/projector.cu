@@ -35,9 +35,9 @@
 //    counter and the allocation-free projection): the lanes are 32 adjacent
 //    columns of one row and differ along the lateral axis that varies with
 //    u: x for rays advancing along y or z (the caller's layout [z][y][x])
-//    and y for rays advancing along x, which read a copy laid out [z][x][y].
-// Either way the warp's gathers (and the backprojector's reductions) fall on
-// one or two 128-byte lines.
+//    and y for rays advancing along x, which read a copy laid out [z][x][y]
+//    (the allocation-free projection reads [z][y][x] in place, strided).
+// Otherwise the warp's gathers (and the reductions) fall on 1-2 lines.
 #include <algorithm>
 #include <atomic>
 #include <climits>
@@ -89,9 +89,9 @@ __device__ __forceinline__ float one_plus_frac(unsigned q) {
 // the host table) and z (the row's line, an exact integer sum); for a ray
 // advancing along z, x and y, rounded to Q.44 from an FP64 setup of the ray.
 // A slab holds at most three segments.  Offsets index the kernel's copy of
-// the volume: [z][y][x] for rays advancing along y or z, [z][x][y]
-// (transposed) for rays advancing along x, so adjacent lanes (adjacent
-// columns of one row) touch adjacent words along their in-plane lateral axis.
+// the volume: [z][y][x] for rays advancing along y or z, [z][x][y] (except
+// in ray_setup<true>: [z][y][x]) for rays advancing along x, so adjacent
+// lanes touch adjacent words along their in-plane lateral axis.
 struct Ray {
     long long X0 = 0, Y0 = 0;        // lines a and b at the start of slab 0 (Q.32)
     unsigned dX = 0u, dY = 0u;       // |slope| per slab (Q.32)
